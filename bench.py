@@ -1,0 +1,406 @@
+"""Benchmark: aggregate risk analysis on one GB300 (or N independent ranks).
+
+One step = one pass of the hot path over the workload: the YLT forward
+(lookup, financial terms, ELT sum, occurrence terms, FP64 aggregate and
+aggregate terms for every layer and trial) and the metrics (mean, PML and
+TVaR per layer). Default workload: 1,000,000 trials x 1,000 events over a
+2,000,000-event catalogue, one layer of 16 ELTs with 20,000 non-zero
+lognormal(12, 2) losses each (synthetic, seeded).
+
+Metric: trial-events x ELTs per second (sum_t K_t * sum_j |E_j| per step /
+step time), plus ms per 1M-trial YLT and the roofline fraction of the
+forward kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1]
+                  [--variant auto|plain|batched|fp64] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+CONFIG_TEXT = {
+    "c1": "1,000,000 trials x 1,000 events, catalogue 2,000,000, 1 layer x 16 ELTs (20,000 non-zero lognormal(12,2) "
+          "losses each), occR 1e5 occL 5e6 aggR 1e6 aggL 2e7, PML/TVaR at 0.99",
+    "c1u": "config c1 with aggR 9e7 aggL 5e7 (aggregate terms straddle the median aggregate)",
+    "c0": "10,000 trials x 1,000 events, catalogue 100,000, 1 layer x 3 ELTs",
+    "c2": "1,000,000 trials of clamp(Poisson(1000),200,2000) events (CSR), 64 layers x U{1..32} ELTs from a pool of 256",
+    "c4": "1,000,000 trials x 1,000 events, 128 layers x U{4..32} ELTs from a pool of 512, lognormal(13,2.5)",
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1308_2572_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1308_2572_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (profiles/<kernel>_<workload>.txt lines
+    'dram_bytes_per_launch: N' and 'source_hash: H')."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def algorithmic_bytes(w, variant: str):
+    """Algorithmic bytes of one forward launch set.
+
+    hbm: compulsory DRAM traffic -- every YET id (4 B) and CSR offset read
+    once, every event-major table row a pass can touch read once from DRAM
+    (the distinct rows, bounded by the table), the YLT (8 B) and branch-free
+    output written once.
+    l2: the sectors the gathers touch -- 32 * ceil(4 n_pad / 32) bytes per
+    (event, layer) for the per-layer tables, 32 * ceil(4 n_pool / 32) per
+    event for the pool table -- plus the id stream.
+    """
+    port, yet = w.portfolio, w.yet
+    n_events = yet.n_events
+    ids = 4 * n_events + (8 * (yet.n_trials + 1) if yet.trial_off is not None else 0)
+    ylt = 8 * yet.n_trials * port.n_layers
+    C = port.catalogue_size
+    sizes = port.elts_per_layer()
+    pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
+    if variant == "plain":
+        row = np.array([4 * pad(int(n)) for n in sizes])
+        sectors = int(sum(32 * -(-r // 32) for r in row)) * n_events
+        table = int(row.sum()) * C
+    else:
+        epl = 1
+        while 32 * epl < port.n_elt:
+            epl *= 2
+        rowb = 32 * epl * (8 if variant == "fp64" else 4)
+        sectors = rowb * n_events
+        table = rowb * C
+    # distinct rows touched by a pass: every catalogue row with probability 1 - exp(-n_events / C)
+    touched = table * (1.0 - np.exp(-n_events / C))
+    return {"hbm": ids + ylt + touched, "l2": ids + sectors, "ids": ids, "ylt": ylt, "table": table}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores, on a
+    bounded sample of the workload per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1308_2572_gb300 import workloads
+    sample_trials = args.ref_trials
+    w = workloads.make(args.config, n_trials=sample_trials)
+    prob = w.oracle_problem()
+    lookups = w.lookups()
+    for _ in range(args.warmup):
+        oracle.ylt(prob, want_gross=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y, _, _ = oracle.ylt(prob, want_gross=False)
+        oracle.metrics(y, w.probs)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = lookups / dt
+    cores = oracle.num_threads()
+    sample = f"first {sample_trials} trials of workload {args.config} (all layers), YLT + metrics per step"
+    line = {"impl": "reference", "metric": "trial-events x ELTs per second", "value": value,
+            "unit": "trial-events*ELTs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
+                       "sample_trials": sample_trials},
+            "cpu_baseline": {"value": value, "unit": "trial-events*ELTs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "trial-events*ELTs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args, w_full):
+    """Oracle timed on the host cores on a bounded sample (about 10-20 s)."""
+    import oracle
+    from paper_1308_2572_gb300 import workloads
+    T = w_full.yet.n_trials
+    probe = min(T, 500)
+    trials = np.arange(probe, dtype=np.int64)
+    prob = w_full.oracle_problem()
+    per_trial = w_full.lookups() / T
+    t0 = time.perf_counter()
+    oracle.ylt(prob, trials=trials, want_gross=False)
+    rate = probe * per_trial / (time.perf_counter() - t0)
+    n = int(min(T, max(probe, args.cpu_seconds * rate / per_trial)))
+    trials = np.arange(n, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.ylt(prob, trials=trials, want_gross=False)
+    dt = time.perf_counter() - t0
+    return {"value": n * per_trial / dt, "unit": "trial-events*ELTs/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"YLT of the first {n} of {T} trials, all layers ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--config", default="c1")
+    ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-trials", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1308_2572_gb300 import art, workloads
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    t_gen = time.perf_counter()
+    w = workloads.make(args.config)
+    log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
+    port, yet = w.portfolio, w.yet
+    L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
+    layouts = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | (art.ART_LAYOUT_POOL64 if args.variant == "fp64" else 0)
+    p = art.portfolio_from_workload(w, device=dev, layouts=layouts)
+    ids = torch.from_numpy(yet.event_ids).to(dev)
+    off = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).to(dev)
+    ylt = torch.empty((L, T), dtype=torch.float64, device=dev)
+    probs = list(w.probs)
+    n_p = len(probs)
+    mean = torch.empty(L, dtype=torch.float64, device=dev)
+    pml = torch.empty((L, n_p), dtype=torch.float64, device=dev)
+    tvar = torch.empty((L, n_p), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64}
+
+    def step():
+        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+
+    # variant choice: time each candidate forward (untimed for the result)
+    cands = [args.variant] if args.variant != "auto" else ["plain", "batched"]
+    fwd_ms = {}
+    for v in cands:
+        art.art_set_variant(p, vmap[v])
+        for _ in range(2):
+            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms[v] = e0.elapsed_time(e1) / 3
+    variant = min(fwd_ms, key=fwd_ms.get)
+    art.art_set_variant(p, vmap[variant])
+    log(f"[bench] forward ms per variant: {fwd_ms}; using {variant}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    assert art.art_get_device_status(p, stream) == art.ART_OK
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        ev[i][1].record(stream)
+        art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    fwd = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_step = total_ms / args.steps
+    lookups = w.lookups()
+    value = world * lookups * args.steps / (total_ms / 1e3)
+    fwd_mean = float(np.mean(fwd))
+
+    # roofline of the dominant kernel (the forward)
+    peak, peak_kind = measured_peaks()
+    ab = algorithmic_bytes(w, variant)
+    achieved = ab["hbm"] / (fwd_mean / 1e3) / 1e9
+    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_batched_fp64"}[variant]
+    traffic = recorded_traffic(kernel_name, args.config)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+            "kernel": kernel_name, "algorithmic_bytes_per_launch": ab["hbm"],
+            "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": ab["l2"] / (fwd_mean / 1e3) / 1e9}
+
+    # end to end: host buffers through the C ABI (ids H2D in chunks, YLT D2H),
+    # then the metrics on a device copy of the YLT and their D2H
+    e2e = None
+    if args.e2e_steps > 0:
+        ids_h = torch.from_numpy(yet.event_ids).pin_memory()
+        off_h = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).pin_memory()
+        ylt_h = torch.empty((L, T), dtype=torch.float64).pin_memory()
+        ylt_d = torch.empty((L, T), dtype=torch.float64, device=dev)
+        out_h = torch.empty((L * (1 + 2 * n_p),), dtype=torch.float64).pin_memory()
+        art.art_run_ylt_host(p, T, ids_h, off_h, K, ylt_h, stream)  # warm staging buffers
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            art.art_run_ylt_host(p, T, ids_h, off_h, K, ylt_h, stream)
+            ylt_d.copy_(ylt_h, non_blocking=True)
+            art.art_metrics(ylt_d, T, L, probs, mean, pml, tvar, stream)
+            out_h[:L].copy_(mean, non_blocking=True)
+            out_h[L:L + L * n_p].copy_(pml.reshape(-1), non_blocking=True)
+            out_h[L + L * n_p:].copy_(tvar.reshape(-1), non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = yet.event_ids.nbytes + (0 if yet.trial_off is None else yet.trial_off.nbytes) + 8 * L * T
+        d2h = 8 * L * T + 8 * L * (1 + 2 * n_p)
+        e2e = {"value": world * lookups / e2e_s, "unit": "trial-events*ELTs/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "path": "art_run_ylt_host (pinned host YET, chunked H2D overlapped with compute) + art_metrics"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, w)
+
+    # kernels of ours launched per step: forward (one per layer for the plain
+    # variant, one persistent launch otherwise) + metrics (state init, 6 x
+    # (histogram + select), tail sums, finalize)
+    launches = (L if variant == "plain" else 1) + 15
+    if rank == 0:
+        line = {
+            "metric": "trial-events x ELTs per second", "value": value, "unit": "trial-events*ELTs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
+                       "variant": variant, "layers": L, "trials": T, "events": yet.n_events,
+                       "lookups_per_step": lookups,
+                       "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
+                       "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"},
+            "ms_per_1M_trial_ylt": fwd_mean * 1e6 / T,
+            "forward_ms": fwd_mean, "forward_ms_by_variant": fwd_ms,
+            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    p.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

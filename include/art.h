@@ -1,0 +1,268 @@
+/*
+ * art.h -- C ABI of libart, GB300-native aggregate risk analysis.
+ *
+ * Method: Bahl, Baltzer, Rau-Chaplin, Varghese, Whiteway, "Achieving Speedup
+ * in Aggregate Risk Analysis using Multiple GPUs" (arXiv:1308.2572).
+ * A Year Event Table (YET: per trial, a list of event ids), a set of Event
+ * Loss Tables (ELTs: event id -> loss, plus per-ELT financial terms) and a
+ * set of excess-of-loss layers (each covering some ELTs, with occurrence and
+ * aggregate retentions and limits) give a Year Loss Table YLT[layer][trial]
+ * (Section II, Algorithm 1). From the YLT come the expected loss, PML and
+ * TVaR (Section I).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are device pointers on the current CUDA device;
+ *    pointers named *_host are host pointers. Caller buffers stay owned by
+ *    the caller; the library never frees them and keeps no reference to them
+ *    after the call returns, except where a call says so.
+ *  - Calls that take a stream are stream-ordered and asynchronous: they
+ *    enqueue work and return. A NULL stream is the legacy default stream.
+ *  - Host-side validation errors return at once (ART_EINVAL) and enqueue
+ *    nothing. Errors found on the device (an event id outside the catalogue)
+ *    never trap: the offending event counts as zero loss, a device flag is
+ *    set, and art_get_device_status reports ART_EID_RANGE.
+ *  - Every piecewise-linear term is XL(v; R, L) = min(max(v - R, 0), L);
+ *    limits may be +INFINITY (an unlimited cover).
+ *  - No entry point waits on other CTAs or other GPUs; there are no spin
+ *    waits in any kernel of this library.
+ */
+#ifndef ART_H
+#define ART_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define ART_API __attribute__((visibility("default")))
+#else
+#define ART_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ART_OK = 0,
+    ART_EINVAL = 1,        /* an argument failed host-side validation        */
+    ART_ENOMEM = 2,        /* a device allocation failed                      */
+    ART_ECUDA = 3,         /* a CUDA runtime call failed                      */
+    ART_EID_RANGE = 4,     /* the device saw an event id outside [0, C)       */
+    ART_ETIMEOUT = 5,      /* reserved: a bounded wait gave up                */
+    ART_EUNSUPPORTED = 6   /* the portfolio lacks the layout this call needs  */
+} art_status;
+
+/* Opaque portfolio: the library's own device copies of the ELTs in the
+ * layouts its kernels read, plus the FP32-rounded terms. */
+typedef struct art_portfolio art_portfolio;
+
+/* Layer terms T = (OccR, OccL, AggR, AggL) of Section II. Retentions must be
+ * finite and >= 0; limits > 0 or +INFINITY. OccR and OccL are rounded to
+ * FP32 (the precision the occurrence test runs in); AggR and AggL stay FP64. */
+typedef struct {
+    double occ_ret;
+    double occ_lim;
+    double agg_ret;
+    double agg_lim;
+} art_layer_terms;
+
+/* Kernel variants for art_run_ylt. */
+enum {
+    ART_VARIANT_AUTO = 0,     /* batched when the pool layout exists, else plain          */
+    ART_VARIANT_PLAIN = 1,    /* one launch per layer over a per-layer event-major table  */
+    ART_VARIANT_BATCHED = 2,  /* one persistent launch over all layers (pool table)       */
+    ART_VARIANT_FP64 = 3      /* batched, with FP64 tables and FP64 per-event arithmetic  */
+};
+
+/* Layouts built by art_create_portfolio (bit mask). */
+enum {
+    ART_LAYOUT_LAYER = 1,     /* per layer: [C][n_pad] FP32, the layer's ELTs side by side */
+    ART_LAYOUT_POOL = 2,      /* all ELTs:  [C][n_elt_pad] FP32, shared by every layer     */
+    ART_LAYOUT_POOL64 = 4     /* all ELTs:  [C][n_elt_pad] FP64 (precision study)          */
+};
+
+/* Flags. */
+enum {
+    ART_FLAG_L2_PERSIST = 1,  /* set a persisting L2 access-policy window over the hot
+                                 table on the stream passed to each run call          */
+    ART_FLAG_GRAPH = 2        /* batched runs replay a cached CUDA graph of the launch */
+};
+
+typedef struct {
+    int32_t layouts;          /* ART_LAYOUT_* mask; 0 means ART_LAYOUT_LAYER | ART_LAYOUT_POOL */
+    int32_t variant;          /* ART_VARIANT_*                                                */
+    int32_t flags;            /* ART_FLAG_*                                                   */
+    int32_t trial_tile;       /* batched: trials per work unit (0 = autotune / default)       */
+    int32_t cta_threads;      /* batched: threads per CTA (0 = default)                       */
+    int32_t reserved[3];
+} art_options;
+
+/*
+ * art_create_portfolio -- the preprocessing stage (Section II: YET, ELT and
+ * layers loaded into memory; Section III: ELTs as direct-access tables).
+ *
+ *  catalogue_size     C, number of event ids; ids are 0..C-1. 1 <= C < 2^31.
+ *  n_elt              number of ELTs, 1..4096.
+ *  elt_losses_dev     [n_elt][C] FP32 direct-access tables (row e is ELT e,
+ *                     zero where the ELT has no loss); device memory, read
+ *                     during this call only. Values must be finite, >= 0.
+ *  elt_mult_host,     [n_elt] FP32 financial terms of each ELT: the loss
+ *  elt_ded_host,      becomes F_e(y) = XL(m_e y; D_e, Lim_e) (the paper names
+ *  elt_lim_host       per-ELT terms but not their form; this is the reading).
+ *                     m_e, D_e finite >= 0; Lim_e > 0 or +INFINITY.
+ *                     elt_mult_host may be NULL (all 1).
+ *  n_layers           1..65536.
+ *  layer_elt_off_host [n_layers + 1], starts at 0, non-decreasing; layer j
+ *                     covers layer_elt_ids_host[off[j] .. off[j+1]), 1..32
+ *                     distinct ELT ids per layer.
+ *  terms_host         [n_layers] layer terms.
+ *  opt                NULL for defaults.
+ *  stream             stream the table builds run on; the call returns after
+ *                     they complete (the caller's buffer may be reused).
+ *  out                receives the portfolio; destroy with art_destroy_portfolio.
+ * Errors: ART_EINVAL (validation), ART_ENOMEM, ART_ECUDA.
+ */
+ART_API art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const float* elt_losses_dev,
+                                const float* elt_mult_host, const float* elt_ded_host,
+                                const float* elt_lim_host, int32_t n_layers,
+                                const int32_t* layer_elt_off_host, const int32_t* layer_elt_ids_host,
+                                const art_layer_terms* terms_host, const art_options* opt,
+                                cudaStream_t stream, art_portfolio** out);
+
+/* Replace the terms without rebuilding tables (pricing loops, finite
+ * differences). Any pointer may be NULL to keep those terms. Same validation
+ * and rounding as art_create_portfolio. Takes effect for calls enqueued
+ * afterwards on any stream; the caller orders it against calls in flight. */
+ART_API art_status art_update_terms(art_portfolio* p, const float* elt_mult_host, const float* elt_ded_host,
+                            const float* elt_lim_host, const art_layer_terms* terms_host);
+
+/* Read back the terms as the kernels apply them (after FP32 rounding).
+ * Any pointer may be NULL. */
+ART_API art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* elt_ded_host,
+                         float* elt_lim_host, art_layer_terms* terms_host);
+
+/* Select the kernel variant (ART_VARIANT_*) and batched tile shape; 0 keeps
+ * the current value of a tile parameter. */
+ART_API art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads);
+
+/*
+ * art_run_ylt -- the simulation stage (Section II, Algorithm 1, steps 1-4):
+ * for every layer j and trial t,
+ *     x_d = sum_{e in E_j} F_e(l_e[E_{t,d}])   FP32, ELT order
+ *     o_d = XL(x_d; OccR_j, OccL_j)            FP32
+ *     S   = sum_d o_d                          FP64
+ *     Y   = XL(S; AggR_j, AggL_j)              FP64
+ * Y equals the trial loss lr of Algorithm 1: its per-event differences of the
+ * aggregate terms telescope to XL(S; AggR, AggL) because AggR >= 0, so event
+ * order (and the timestamps) does not change Y.
+ *
+ *  n_trials           T >= 0 (0 is a no-op).
+ *  event_ids_dev      int32 event ids. Dense: [T][K]. CSR: trial t is
+ *                     event_ids_dev[off[t] .. off[t+1]).
+ *  trial_off_dev      NULL for a dense YET, else [T+1] int64, off[0] = 0,
+ *                     non-decreasing (checked on the device: a decreasing pair
+ *                     is treated as an empty trial and flags ART_EINVAL via
+ *                     art_get_device_status).
+ *  events_per_trial   K for a dense YET (>= 0), ignored for CSR.
+ *  ylt_dev            [n_layers][T] FP64 output.
+ *  branch_dev         NULL, or [n_layers][T] uint8 output: 0 when S <= AggR,
+ *                     1 when AggR < S < AggR + AggL, 2 above (the aggregate
+ *                     branch art_run_ylt_backward needs).
+ * Errors: ART_EINVAL, ART_EUNSUPPORTED (variant's layout not built), ART_ECUDA.
+ */
+ART_API art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
+                       const int64_t* trial_off_dev, int32_t events_per_trial, double* ylt_dev,
+                       uint8_t* branch_dev, cudaStream_t stream);
+
+/*
+ * art_run_ylt_host -- art_run_ylt from host buffers: the YET is copied to the
+ * device in chunks of trials on the given stream, each chunk's YLT rows are
+ * computed and copied back into ylt_host ([n_layers][T] FP64). The portfolio
+ * owns the staging buffers (grown on demand, freed with the portfolio).
+ * Blocks until the result is in ylt_host. Dense YETs only (trial_off NULL)
+ * or CSR with host offsets. Pinned host memory gives full copy bandwidth.
+ */
+ART_API art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
+                            const int64_t* trial_off_host, int32_t events_per_trial,
+                            double* ylt_host, cudaStream_t stream);
+
+/*
+ * art_metrics -- financial functions on the YLT (Section I: PML and TVaR;
+ * Section II: "financial functions or filters" on the trial losses).
+ * Per layer j: mean_j = (1/T) sum_t Y_{j,t}; with k = ceil((1 - p) T)
+ * (at least 1; a (1-p)T within 1e-9 T of an integer is taken as that
+ * integer), PML_p = the k-th largest Y_{j,.} and TVaR_p = the mean of the k
+ * largest. Exact selection (radix select on the FP64 bit patterns), FP64 sums.
+ *
+ *  ylt_dev     [n_layers][n_trials] FP64, values >= 0 (the YLT).
+ *  probs_host  [n_p] probabilities in (0, 1); 1 <= n_p <= 8.
+ *  mean_dev    [n_layers] FP64 output (may be NULL).
+ *  pml_dev     [n_layers][n_p] FP64 output (may be NULL).
+ *  tvar_dev    [n_layers][n_p] FP64 output (may be NULL).
+ * Scratch is taken from the stream-ordered allocator and released on the
+ * stream. Errors: ART_EINVAL, ART_ENOMEM, ART_ECUDA.
+ */
+ART_API art_status art_metrics(const double* ylt_dev, int64_t n_trials, int32_t n_layers, const double* probs_host,
+                       int32_t n_p, double* mean_dev, double* pml_dev, double* tvar_dev, cudaStream_t stream);
+
+/*
+ * art_metrics_backward -- gradient of sum_j (gm_j mean_j + sum_q gt_{j,q}
+ * TVaR_{j,q}) with respect to the YLT: grad_ylt[j][t] = gm_j / T
+ * + sum_q gt_{j,q} w_{j,q}(t), where w = 1/k for Y > PML, (k - #greater) /
+ * (k #equal) for Y == PML (ties share the boundary weight), 0 below.
+ *  pml_dev           [n_layers][n_p] from art_metrics on the same YLT.
+ *  grad_mean_dev     [n_layers] or NULL; grad_tvar_dev [n_layers][n_p] or NULL.
+ *  grad_ylt_dev      [n_layers][n_trials] FP64 output.
+ */
+ART_API art_status art_metrics_backward(const double* ylt_dev, int64_t n_trials, int32_t n_layers,
+                                const double* probs_host, int32_t n_p, const double* pml_dev,
+                                const double* grad_mean_dev, const double* grad_tvar_dev,
+                                double* grad_ylt_dev, cudaStream_t stream);
+
+/*
+ * art_run_ylt_backward -- adjoint of art_run_ylt (the paper has no
+ * gradients; this is the pricing sensitivity). Given G = sum g_{j,t} Y_{j,t}:
+ *   dG/dAggR_j = -sum_t g a,  dG/dAggL_j = sum_t g c,
+ *   dG/dOccR_j = -sum_t g a #{d: OccR < x_d < OccR + OccL},
+ *   dG/dOccL_j =  sum_t g a #{d: x_d > OccR + OccL},
+ *   dG/dm_e    =  sum_j sum_t g a sum_d [o_d mid][D_e < m_e l < D_e + Lim_e] l,
+ * with a = [branch == 1], c = [branch == 2] and l = l_e[E_{t,d}]; at a kink
+ * the strict-inequality branch is taken. Trials whose branch is not 1 are not
+ * re-read. The per-event branches are recomputed in the forward's FP32
+ * arithmetic; sums are FP64 and deterministic.
+ *  branch_dev        [n_layers][T] from art_run_ylt on the same YET and terms.
+ *  grad_ylt_dev      [n_layers][T] FP64.
+ *  grad_terms_dev    [n_layers][4] FP64 output (OccR, OccL, AggR, AggL).
+ *  grad_mult_dev     [n_elt] FP64 output.
+ * Needs the ART_LAYOUT_LAYER tables. Scratch from the stream-ordered allocator.
+ */
+ART_API art_status art_run_ylt_backward(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
+                                const int64_t* trial_off_dev, int32_t events_per_trial,
+                                const uint8_t* branch_dev, const double* grad_ylt_dev,
+                                double* grad_terms_dev, double* grad_mult_dev, cudaStream_t stream);
+
+/* Synchronise the stream, then read and clear the portfolio's device error
+ * flags: ART_OK, ART_EID_RANGE (an id outside [0, C) was seen; it counted as
+ * zero loss) or ART_EINVAL (decreasing CSR offsets were seen). */
+ART_API art_status art_get_device_status(art_portfolio* p, cudaStream_t stream);
+
+/* Bytes of device memory the portfolio holds, per layout (NULL to skip). */
+ART_API art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes,
+                             int64_t* pool64_bytes);
+
+/* Free the portfolio (synchronises the device first). NULL is a no-op. */
+ART_API void art_destroy_portfolio(art_portfolio* p);
+
+/* Static, human-readable name of a status. */
+ART_API const char* art_status_string(art_status s);
+
+/* Text of the last CUDA error this thread saw inside the library. */
+ART_API const char* art_last_cuda_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+ART_API int32_t art_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ART_H */

@@ -1,0 +1,628 @@
+// art_api.cu -- the C ABI of include/art.h: validation, the preprocessing
+// stage (building the direct-access tables in the kernels' layouts), dispatch
+// to the kernels, host-buffer staging, CUDA-graph replay and status.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "art_internal.cuh"
+
+namespace art {
+
+static thread_local std::string g_last_cuda_error;
+
+void set_last_error(cudaError_t e) {
+    if (e != cudaSuccess) g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+}
+
+// Set (or clear, bytes == 0) a persisting access-policy window on a stream.
+cudaError_t set_window(cudaStream_t s, const void* base, size_t bytes) {
+    cudaStreamAttrValue v;
+    std::memset(&v, 0, sizeof(v));
+    if (bytes) {
+        int dev = 0, max_win = 0, persist_max = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+        cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, dev);
+        const size_t win = std::min(bytes, (size_t)max_win);
+        v.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+        v.accessPolicyWindow.num_bytes = win;
+        v.accessPolicyWindow.hitRatio = win ? (float)std::min(1.0, (double)persist_max / (double)win) : 0.0f;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    }
+    return cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &v);
+}
+
+}  // namespace art
+
+using namespace art;
+
+namespace {
+
+__global__ void check_losses_kernel(const float* __restrict__ v, int64_t n, int* __restrict__ bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        if (!(x >= 0.0f) || !(x <= 3.4028234663852886e38f)) {  // negative, NaN or inf
+            atomicOr(bad, 1);
+            return;
+        }
+    }
+}
+
+art_status fail(cudaError_t e) {
+    set_last_error(e);
+    if (e == cudaErrorMemoryAllocation) return ART_ENOMEM;
+    return ART_ECUDA;
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+bool valid_limit(double x) { return !std::isnan(x) && x > 0.0; }  // +inf allowed
+
+int pad_np(int n) {
+    if (n <= 4) return 4;
+    if (n <= 8) return 8;
+    if (n <= 16) return 16;
+    if (n <= 24) return 24;
+    return 32;
+}
+
+// Round ELT and layer terms as the kernels apply them; false when invalid.
+bool round_terms(int32_t n_elt, const float* m, const float* d, const float* l, int32_t n_layers,
+                 const art_layer_terms* t, std::vector<float>& om, std::vector<float>& od, std::vector<float>& ol,
+                 std::vector<float>& orr, std::vector<float>& orl, std::vector<double>& oar,
+                 std::vector<double>& oal) {
+    // NULL arrays keep the current values (partial updates)
+    if (m) {
+        om.assign(m, m + n_elt);
+        for (float x : om)
+            if (!finite_nonneg(x)) return false;
+    }
+    if (d) {
+        od.assign(d, d + n_elt);
+        for (float x : od)
+            if (!finite_nonneg(x)) return false;
+    }
+    if (l) {
+        ol.assign(l, l + n_elt);
+        for (float x : ol)
+            if (!valid_limit(x)) return false;
+    }
+    if (t) {
+        orr.resize(n_layers);
+        orl.resize(n_layers);
+        oar.resize(n_layers);
+        oal.resize(n_layers);
+        for (int32_t j = 0; j < n_layers; ++j) {
+            const art_layer_terms& x = t[j];
+            if (!finite_nonneg(x.occ_ret) || !valid_limit(x.occ_lim) || !finite_nonneg(x.agg_ret) ||
+                !valid_limit(x.agg_lim))
+                return false;
+            orr[j] = (float)x.occ_ret;
+            orl[j] = (float)x.occ_lim;
+            if (!std::isfinite(orr[j]) || !(orl[j] > 0.0f)) return false;  // overflow on rounding
+            oar[j] = x.agg_ret;
+            oal[j] = x.agg_lim;
+        }
+    }
+    return true;
+}
+
+// Batched metadata: terms per pool column, (lane, slot) -> layer, and per
+// (ELT, lane) the bit mask of the lane's slots whose layer covers the ELT.
+cudaError_t upload_batched_terms(art_portfolio* p) {
+    const int np = p->pool_np;
+    std::vector<float> t32(3 * (size_t)np);
+    std::vector<double> t64(3 * (size_t)np);
+    for (int e = 0; e < np; ++e) {
+        const bool real = e < p->n_elt;
+        t32[e] = real ? p->mult[e] : 1.0f;
+        t32[np + e] = real ? p->ded[e] : 0.0f;
+        t32[2 * np + e] = real ? p->lim[e] : std::numeric_limits<float>::infinity();
+        for (int k = 0; k < 3; ++k) t64[k * np + e] = (double)t32[k * np + e];
+    }
+    std::vector<float> occ(2 * (size_t)p->n_layers);
+    std::vector<double> agg(2 * (size_t)p->n_layers);
+    for (int j = 0; j < p->n_layers; ++j) {
+        occ[2 * j] = p->occ_ret[j];
+        occ[2 * j + 1] = p->occ_lim[j];
+        agg[2 * j] = p->agg_ret[j];
+        agg[2 * j + 1] = p->agg_lim[j];
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpy(p->d_elt_terms, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMemcpy(p->d_elt_terms64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMemcpy(p->d_occ, occ.data(), sizeof(float) * occ.size(), cudaMemcpyHostToDevice))) return e;
+    return cudaMemcpy(p->d_agg, agg.data(), sizeof(double) * agg.size(), cudaMemcpyHostToDevice);
+}
+
+cudaError_t build_batched_meta(art_portfolio* p) {
+    const int L = p->n_layers;
+    p->slots = L <= 64 ? 2 : (L <= 128 ? 4 : 8);
+    const int per_tile = 32 * p->slots;
+    p->n_tiles = (L + per_tile - 1) / per_tile;
+    const int np = p->pool_np;
+    std::vector<int32_t> slot_layer((size_t)p->n_tiles * p->slots * 32, -1);
+    std::vector<uint8_t> memb((size_t)p->n_tiles * np * 32, 0);
+    for (int j = 0; j < L; ++j) {
+        const int tile = j / per_tile, r = j % per_tile, slot = r / 32, lane = r % 32;
+        slot_layer[((size_t)tile * p->slots + slot) * 32 + lane] = j;
+        for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
+            memb[((size_t)tile * np + p->lids[c]) * 32 + lane] |= (uint8_t)(1u << slot);
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_elt_terms, sizeof(float) * 3 * np))) return e;
+    if ((e = cudaMalloc(&p->d_elt_terms64, sizeof(double) * 3 * np))) return e;
+    if ((e = cudaMalloc(&p->d_occ, sizeof(float) * 2 * L))) return e;
+    if ((e = cudaMalloc(&p->d_agg, sizeof(double) * 2 * L))) return e;
+    if ((e = cudaMalloc(&p->d_slot_layer, sizeof(int32_t) * slot_layer.size()))) return e;
+    if ((e = cudaMalloc(&p->d_memb, memb.size()))) return e;
+    if ((e = cudaMalloc(&p->d_work_counter, sizeof(unsigned int)))) return e;
+    if ((e = cudaMemcpy(p->d_slot_layer, slot_layer.data(), sizeof(int32_t) * slot_layer.size(), cudaMemcpyHostToDevice)))
+        return e;
+    if ((e = cudaMemcpy(p->d_memb, memb.data(), memb.size(), cudaMemcpyHostToDevice))) return e;
+    return upload_batched_terms(p);
+}
+
+size_t batched_smem(const art_portfolio* p, bool fp64) {
+    return 3 * (size_t)p->pool_np * (fp64 ? 8 : 4) + (size_t)p->n_tiles * p->pool_np * 32;
+}
+
+void free_portfolio(art_portfolio* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    for (float* t : p->layer_tab) cudaFree(t);
+    cudaFree(p->pool);
+    cudaFree(p->pool64);
+    cudaFree(p->d_elt_terms);
+    cudaFree(p->d_elt_terms64);
+    cudaFree(p->d_memb);
+    cudaFree(p->d_slot_layer);
+    cudaFree(p->d_occ);
+    cudaFree(p->d_agg);
+    cudaFree(p->d_work_counter);
+    cudaFree(p->d_flags);
+    cudaFree(p->d_loff);
+    cudaFree(p->d_lids);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(p->stage_ids[i]);
+        cudaFree(p->stage_off[i]);
+        cudaFree(p->stage_ylt[i]);
+        if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
+        if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    delete p;
+}
+
+int resolve_variant(const art_portfolio* p) {
+    if (p->variant != ART_VARIANT_AUTO) return p->variant;
+    if (p->pool && p->n_tiles > 0) return ART_VARIANT_BATCHED;
+    return ART_VARIANT_PLAIN;
+}
+
+bool variant_available(const art_portfolio* p, int v) {
+    if (v == ART_VARIANT_PLAIN) return (p->layouts & ART_LAYOUT_LAYER) != 0;
+    if (v == ART_VARIANT_BATCHED) return p->pool != nullptr && p->n_tiles > 0 && batched_smem(p, false) <= 200 * 1024;
+    if (v == ART_VARIANT_FP64) return p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024;
+    return false;
+}
+
+art_status validate_yet(int64_t n_trials, const int32_t* ids, const int64_t* off, int32_t k) {
+    if (n_trials < 0 || n_trials > (int64_t)1 << 40) return ART_EINVAL;
+    if (!off && k < 0) return ART_EINVAL;
+    if (!off && n_trials > 0 && k > 0 && n_trials > ((int64_t)1 << 62) / k) return ART_EINVAL;
+    if (n_trials > 0 && !ids && (off || k > 0)) return ART_EINVAL;
+    return ART_OK;
+}
+
+cudaError_t run_forward(art_portfolio* p, int variant, const YetArgs& y, double* ylt, uint8_t* branch,
+                        cudaStream_t s) {
+    if (variant == ART_VARIANT_PLAIN) return launch_plain(p, y, ylt, branch, s);
+    return launch_batched(p, y, ylt, branch, variant == ART_VARIANT_FP64, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* art_status_string(art_status s) {
+    switch (s) {
+        case ART_OK: return "ART_OK";
+        case ART_EINVAL: return "ART_EINVAL: invalid argument";
+        case ART_ENOMEM: return "ART_ENOMEM: device allocation failed";
+        case ART_ECUDA: return "ART_ECUDA: CUDA runtime error";
+        case ART_EID_RANGE: return "ART_EID_RANGE: event id outside the catalogue";
+        case ART_ETIMEOUT: return "ART_ETIMEOUT: bounded wait gave up";
+        case ART_EUNSUPPORTED: return "ART_EUNSUPPORTED: layout not built for this call";
+    }
+    return "unknown art_status";
+}
+
+const char* art_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int32_t art_version(void) { return 10000; }
+
+art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const float* elt_losses_dev,
+                                const float* elt_mult_host, const float* elt_ded_host, const float* elt_lim_host,
+                                int32_t n_layers, const int32_t* layer_elt_off_host,
+                                const int32_t* layer_elt_ids_host, const art_layer_terms* terms_host,
+                                const art_options* opt, cudaStream_t stream, art_portfolio** out) {
+    if (!out) return ART_EINVAL;
+    *out = nullptr;
+    if (catalogue_size < 1 || n_elt < 1 || n_elt > 4096 || n_layers < 1 || n_layers > 65536) return ART_EINVAL;
+    if (!elt_losses_dev || !elt_ded_host || !elt_lim_host || !layer_elt_off_host || !layer_elt_ids_host ||
+        !terms_host)
+        return ART_EINVAL;
+    if (layer_elt_off_host[0] != 0) return ART_EINVAL;
+    for (int32_t j = 0; j < n_layers; ++j) {
+        const int32_t b = layer_elt_off_host[j], e = layer_elt_off_host[j + 1];
+        if (e - b < 1 || e - b > kMaxLayerElts) return ART_EINVAL;
+        for (int32_t c = b; c < e; ++c) {
+            const int32_t id = layer_elt_ids_host[c];
+            if (id < 0 || id >= n_elt) return ART_EINVAL;
+            for (int32_t c2 = b; c2 < c; ++c2)
+                if (layer_elt_ids_host[c2] == id) return ART_EINVAL;
+        }
+    }
+    auto* p = new art_portfolio();
+    p->catalogue = catalogue_size;
+    p->n_elt = n_elt;
+    p->n_layers = n_layers;
+    std::vector<float> ones(n_elt, 1.0f);
+    if (!round_terms(n_elt, elt_mult_host ? elt_mult_host : ones.data(), elt_ded_host, elt_lim_host, n_layers,
+                     terms_host, p->mult, p->ded, p->lim, p->occ_ret, p->occ_lim, p->agg_ret, p->agg_lim)) {
+        delete p;
+        return ART_EINVAL;
+    }
+    p->loff.assign(layer_elt_off_host, layer_elt_off_host + n_layers + 1);
+    p->lids.assign(layer_elt_ids_host, layer_elt_ids_host + p->loff.back());
+    p->layouts = (opt && opt->layouts) ? opt->layouts : (ART_LAYOUT_LAYER | ART_LAYOUT_POOL);
+    p->variant = opt ? opt->variant : ART_VARIANT_AUTO;
+    p->flags = opt ? opt->flags : 0;
+    p->trial_tile = opt ? opt->trial_tile : 0;
+    p->cta_threads = opt ? opt->cta_threads : 0;
+    if (p->variant < ART_VARIANT_AUTO || p->variant > ART_VARIANT_FP64 || p->trial_tile < 0 ||
+        (p->cta_threads != 0 && (p->cta_threads % 32 != 0 || p->cta_threads > 1024))) {
+        delete p;
+        return ART_EINVAL;
+    }
+
+    cudaError_t e;
+    art_status st = ART_OK;
+    do {
+        if ((e = cudaGetDevice(&p->device))) break;
+        if ((e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device))) break;
+        if ((e = cudaMalloc(&p->d_flags, sizeof(int) * kNumFlags))) break;
+        if ((e = cudaMemsetAsync(p->d_flags, 0, sizeof(int) * kNumFlags, stream))) break;
+        // losses must be finite and >= 0 (zero where an ELT has no loss)
+        const int64_t n_vals = (int64_t)n_elt * catalogue_size;
+        check_losses_kernel<<<(unsigned)std::min<int64_t>((n_vals + 255) / 256, 4096), 256, 0, stream>>>(
+            elt_losses_dev, n_vals, p->d_flags);
+        if ((e = cudaGetLastError())) break;
+        int bad = 0;
+        if ((e = cudaMemcpyAsync(&bad, p->d_flags, sizeof(int), cudaMemcpyDeviceToHost, stream))) break;
+        if ((e = cudaStreamSynchronize(stream))) break;
+        if (bad) {
+            st = ART_EINVAL;
+            break;
+        }
+        if ((e = cudaMalloc(&p->d_loff, sizeof(int32_t) * p->loff.size()))) break;
+        if ((e = cudaMalloc(&p->d_lids, sizeof(int32_t) * p->lids.size()))) break;
+        if ((e = cudaMemcpy(p->d_loff, p->loff.data(), sizeof(int32_t) * p->loff.size(), cudaMemcpyHostToDevice))) break;
+        if ((e = cudaMemcpy(p->d_lids, p->lids.data(), sizeof(int32_t) * p->lids.size(), cudaMemcpyHostToDevice))) break;
+        if (p->layouts & ART_LAYOUT_LAYER) {
+            p->layer_tab.assign(n_layers, nullptr);
+            p->layer_np.assign(n_layers, 0);
+            for (int32_t j = 0; j < n_layers && !e; ++j) {
+                const int32_t n = p->loff[j + 1] - p->loff[j];
+                const int32_t np = pad_np(n);
+                p->layer_np[j] = np;
+                const size_t bytes = sizeof(float) * (size_t)catalogue_size * np;
+                if ((e = cudaMalloc(&p->layer_tab[j], bytes))) break;
+                p->layer_bytes += (int64_t)bytes;
+                e = build_layer_table(elt_losses_dev, catalogue_size, p->d_lids + p->loff[j], n, np, p->layer_tab[j],
+                                      stream);
+            }
+            if (e) break;
+        }
+        if ((p->layouts & (ART_LAYOUT_POOL | ART_LAYOUT_POOL64)) && n_elt <= kMaxPoolElts) {
+            int epl = 1;
+            while (32 * epl < n_elt) epl *= 2;
+            p->pool_np = 32 * epl;
+            if (p->layouts & ART_LAYOUT_POOL) {
+                const size_t bytes = sizeof(float) * (size_t)catalogue_size * p->pool_np;
+                if ((e = cudaMalloc(&p->pool, bytes))) break;
+                p->pool_bytes = (int64_t)bytes;
+            }
+            if (p->layouts & ART_LAYOUT_POOL64) {
+                const size_t bytes = sizeof(double) * (size_t)catalogue_size * p->pool_np;
+                if ((e = cudaMalloc(&p->pool64, bytes))) break;
+                p->pool64_bytes = (int64_t)bytes;
+            }
+            if ((e = build_pool_table(elt_losses_dev, catalogue_size, n_elt, p->pool_np, p->pool, p->pool64, stream)))
+                break;
+            if ((e = build_batched_meta(p))) break;
+        }
+        if (p->flags & ART_FLAG_L2_PERSIST) {
+            int persist_max = 0;
+            cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, p->device);
+            if (persist_max > 0 && (e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max))) break;
+        }
+        e = cudaStreamSynchronize(stream);
+    } while (0);
+    if (e != cudaSuccess || st != ART_OK) {
+        const art_status r = e != cudaSuccess ? fail(e) : st;
+        free_portfolio(p);
+        return r;
+    }
+    if (p->variant != ART_VARIANT_AUTO && !variant_available(p, p->variant)) {
+        free_portfolio(p);
+        return ART_EUNSUPPORTED;
+    }
+    *out = p;
+    return ART_OK;
+}
+
+art_status art_update_terms(art_portfolio* p, const float* elt_mult_host, const float* elt_ded_host,
+                            const float* elt_lim_host, const art_layer_terms* terms_host) {
+    if (!p) return ART_EINVAL;
+    std::vector<float> m = p->mult, d = p->ded, l = p->lim, orr = p->occ_ret, orl = p->occ_lim;
+    std::vector<double> oar = p->agg_ret, oal = p->agg_lim;
+    if (!round_terms(p->n_elt, elt_mult_host, elt_ded_host, elt_lim_host, p->n_layers, terms_host, m, d, l, orr, orl,
+                     oar, oal))
+        return ART_EINVAL;
+    p->mult.swap(m);
+    p->ded.swap(d);
+    p->lim.swap(l);
+    p->occ_ret.swap(orr);
+    p->occ_lim.swap(orl);
+    p->agg_ret.swap(oar);
+    p->agg_lim.swap(oal);
+    if (p->d_elt_terms) {
+        const cudaError_t e = upload_batched_terms(p);
+        if (e) return fail(e);
+    }
+    if (p->graph_exec) {  // the plain variant bakes terms into launch parameters
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    return ART_OK;
+}
+
+art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* elt_ded_host, float* elt_lim_host,
+                         art_layer_terms* terms_host) {
+    if (!p) return ART_EINVAL;
+    if (elt_mult_host) std::copy(p->mult.begin(), p->mult.end(), elt_mult_host);
+    if (elt_ded_host) std::copy(p->ded.begin(), p->ded.end(), elt_ded_host);
+    if (elt_lim_host) std::copy(p->lim.begin(), p->lim.end(), elt_lim_host);
+    if (terms_host)
+        for (int32_t j = 0; j < p->n_layers; ++j)
+            terms_host[j] = art_layer_terms{p->occ_ret[j], p->occ_lim[j], p->agg_ret[j], p->agg_lim[j]};
+    return ART_OK;
+}
+
+art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads) {
+    if (!p || variant < ART_VARIANT_AUTO || variant > ART_VARIANT_FP64 || trial_tile < 0 || cta_threads < 0 ||
+        cta_threads % 32 != 0 || cta_threads > 1024)
+        return ART_EINVAL;
+    if (variant != ART_VARIANT_AUTO && !variant_available(p, variant)) return ART_EUNSUPPORTED;
+    p->variant = variant;
+    if (trial_tile) p->trial_tile = trial_tile;
+    if (cta_threads) p->cta_threads = cta_threads;
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    return ART_OK;
+}
+
+art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
+                       const int64_t* trial_off_dev, int32_t events_per_trial, double* ylt_dev, uint8_t* branch_dev,
+                       cudaStream_t stream) {
+    if (!p) return ART_EINVAL;
+    art_status st = validate_yet(n_trials, event_ids_dev, trial_off_dev, events_per_trial);
+    if (st) return st;
+    if (n_trials == 0) return ART_OK;
+    if (!ylt_dev) return ART_EINVAL;
+    const int variant = resolve_variant(p);
+    if (!variant_available(p, variant)) return ART_EUNSUPPORTED;
+    YetArgs y{event_ids_dev, trial_off_dev, n_trials, trial_off_dev ? 0 : events_per_trial, p->catalogue};
+    cudaError_t e;
+    const bool use_graph = (p->flags & ART_FLAG_GRAPH) != 0;
+    if (use_graph) {
+        const void* key[4] = {event_ids_dev, trial_off_dev, ylt_dev, branch_dev};
+        const bool hit = p->graph_exec && std::equal(key, key + 4, p->graph_key) && p->graph_key_n[0] == n_trials &&
+                         p->graph_key_n[1] == ((int64_t)events_per_trial << 4 | variant);
+        if (!hit) {
+            if (p->graph_exec) {
+                cudaGraphExecDestroy(p->graph_exec);
+                p->graph_exec = nullptr;
+            }
+            cudaStream_t cap;
+            if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return fail(e);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (!e) {
+                const cudaError_t le = run_forward(p, variant, y, ylt_dev, branch_dev, cap);
+                e = cudaStreamEndCapture(cap, &g);
+                if (!e) e = le;
+            }
+            if (!e) e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            if (e) {
+                p->graph_exec = nullptr;
+                return fail(e);
+            }
+            std::copy(key, key + 4, p->graph_key);
+            p->graph_key_n[0] = n_trials;
+            p->graph_key_n[1] = ((int64_t)events_per_trial << 4 | variant);
+        }
+        e = cudaGraphLaunch(p->graph_exec, stream);
+        return e ? fail(e) : ART_OK;
+    }
+    const bool window = (p->flags & ART_FLAG_L2_PERSIST) != 0 && variant != ART_VARIANT_PLAIN;
+    if (window) set_window(stream, variant == ART_VARIANT_FP64 ? (const void*)p->pool64 : (const void*)p->pool,
+                           variant == ART_VARIANT_FP64 ? p->pool64_bytes : p->pool_bytes);
+    e = run_forward(p, variant, y, ylt_dev, branch_dev, stream);
+    if (window) set_window(stream, nullptr, 0);
+    return e ? fail(e) : ART_OK;
+}
+
+art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
+                            const int64_t* trial_off_host, int32_t events_per_trial, double* ylt_host,
+                            cudaStream_t stream) {
+    if (!p) return ART_EINVAL;
+    art_status st = validate_yet(n_trials, event_ids_host, trial_off_host, events_per_trial);
+    if (st) return st;
+    if (n_trials == 0) return ART_OK;
+    if (!ylt_host) return ART_EINVAL;
+    if (trial_off_host) {
+        if (trial_off_host[0] != 0) return ART_EINVAL;
+        for (int64_t t = 0; t < n_trials; ++t)
+            if (trial_off_host[t + 1] < trial_off_host[t]) return ART_EINVAL;
+    }
+    const int variant = resolve_variant(p);
+    if (!variant_available(p, variant)) return ART_EUNSUPPORTED;
+    // chunk of trials per stage: about 64 MiB of ids
+    const int64_t avg = trial_off_host ? std::max<int64_t>(1, trial_off_host[n_trials] / std::max<int64_t>(1, n_trials))
+                                       : std::max<int64_t>(1, events_per_trial);
+    int64_t chunk = std::max<int64_t>(1024, ((int64_t)16 << 20) / avg);
+    chunk = std::min(chunk, n_trials);
+    // largest id span of any chunk
+    int64_t max_ids = 0;
+    for (int64_t t0 = 0; t0 < n_trials; t0 += chunk) {
+        const int64_t t1 = std::min(n_trials, t0 + chunk);
+        const int64_t span = trial_off_host ? trial_off_host[t1] - trial_off_host[t0] : (t1 - t0) * events_per_trial;
+        max_ids = std::max(max_ids, span);
+    }
+    cudaError_t e = cudaSuccess;
+    if (max_ids > p->stage_ids_cap || chunk > p->stage_trials_cap) {
+        cudaStreamSynchronize(stream);
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(p->stage_ids[i]);
+            cudaFree(p->stage_off[i]);
+            cudaFree(p->stage_ylt[i]);
+            p->stage_ids[i] = nullptr;
+            p->stage_off[i] = nullptr;
+            p->stage_ylt[i] = nullptr;
+        }
+        p->stage_ids_cap = p->stage_trials_cap = 0;
+        for (int i = 0; i < 2 && !e; ++i) {
+            if ((e = cudaMalloc(&p->stage_ids[i], sizeof(int32_t) * std::max<int64_t>(1, max_ids)))) break;
+            if ((e = cudaMalloc(&p->stage_off[i], sizeof(int64_t) * (chunk + 1)))) break;
+            e = cudaMalloc(&p->stage_ylt[i], sizeof(double) * (size_t)chunk * p->n_layers);
+        }
+        if (e) return fail(e);
+        p->stage_ids_cap = max_ids;
+        p->stage_trials_cap = chunk;
+    }
+    if (!p->copy_stream) {
+        if ((e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking))) return fail(e);
+        for (int i = 0; i < 2 && !e; ++i) {
+            if ((e = cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming))) break;
+            e = cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming);
+        }
+        if (e) return fail(e);
+    }
+    // the copy stream must not run ahead of work already queued on `stream`
+    if ((e = cudaEventRecord(p->ev_done[0], stream))) return fail(e);
+    if ((e = cudaEventRecord(p->ev_done[1], stream))) return fail(e);
+    int64_t c = 0;
+    for (int64_t t0 = 0; t0 < n_trials && !e; t0 += chunk, ++c) {
+        const int slot = (int)(c & 1);
+        const int64_t t1 = std::min(n_trials, t0 + chunk), nt = t1 - t0;
+        const int64_t i0 = trial_off_host ? trial_off_host[t0] : t0 * events_per_trial;
+        const int64_t i1 = trial_off_host ? trial_off_host[t1] : t1 * events_per_trial;
+        if ((e = cudaStreamWaitEvent(p->copy_stream, p->ev_done[slot], 0))) break;
+        if (i1 > i0 && (e = cudaMemcpyAsync(p->stage_ids[slot], event_ids_host + i0, sizeof(int32_t) * (i1 - i0),
+                                            cudaMemcpyHostToDevice, p->copy_stream)))
+            break;
+        if (trial_off_host && (e = cudaMemcpyAsync(p->stage_off[slot], trial_off_host + t0, sizeof(int64_t) * (nt + 1),
+                                                   cudaMemcpyHostToDevice, p->copy_stream)))
+            break;
+        if ((e = cudaEventRecord(p->ev_copied[slot], p->copy_stream))) break;
+        if ((e = cudaStreamWaitEvent(stream, p->ev_copied[slot], 0))) break;
+        // offsets stay absolute: the ids pointer is shifted so that ids[off[t]]
+        // lands in the staging buffer
+        YetArgs y{p->stage_ids[slot] - i0, trial_off_host ? p->stage_off[slot] : nullptr, nt,
+                  trial_off_host ? 0 : events_per_trial, p->catalogue};
+        if (!trial_off_host) y.ids = p->stage_ids[slot];
+        if ((e = run_forward(p, variant, y, p->stage_ylt[slot], nullptr, stream))) break;
+        if ((e = cudaMemcpy2DAsync(ylt_host + t0, sizeof(double) * n_trials, p->stage_ylt[slot], sizeof(double) * nt,
+                                   sizeof(double) * nt, p->n_layers, cudaMemcpyDeviceToHost, stream)))
+            break;
+        e = cudaEventRecord(p->ev_done[slot], stream);
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(stream);
+    if (e || e2) return fail(e ? e : e2);
+    return ART_OK;
+}
+
+art_status art_metrics(const double* ylt_dev, int64_t n_trials, int32_t n_layers, const double* probs_host,
+                       int32_t n_p, double* mean_dev, double* pml_dev, double* tvar_dev, cudaStream_t stream) {
+    if (!ylt_dev || n_trials < 1 || n_trials > 0x7fffffffLL || n_layers < 1 || n_layers > 65535 || !probs_host ||
+        n_p < 1 || n_p > kMaxProbs)
+        return ART_EINVAL;
+    for (int q = 0; q < n_p; ++q)
+        if (!(probs_host[q] > 0.0 && probs_host[q] < 1.0)) return ART_EINVAL;
+    const cudaError_t e = metrics_run(ylt_dev, n_trials, n_layers, probs_host, n_p, mean_dev, pml_dev, tvar_dev, stream);
+    return e ? fail(e) : ART_OK;
+}
+
+art_status art_metrics_backward(const double* ylt_dev, int64_t n_trials, int32_t n_layers, const double* probs_host,
+                                int32_t n_p, const double* pml_dev, const double* grad_mean_dev,
+                                const double* grad_tvar_dev, double* grad_ylt_dev, cudaStream_t stream) {
+    if (!ylt_dev || !grad_ylt_dev || n_trials < 1 || n_trials > 0x7fffffffLL || n_layers < 1 || n_layers > 65535 ||
+        n_p < 0 || n_p > kMaxProbs)
+        return ART_EINVAL;
+    if (grad_tvar_dev && (!pml_dev || !probs_host || n_p < 1)) return ART_EINVAL;
+    for (int q = 0; q < n_p && probs_host; ++q)
+        if (!(probs_host[q] > 0.0 && probs_host[q] < 1.0)) return ART_EINVAL;
+    const cudaError_t e = metrics_backward_run(ylt_dev, n_trials, n_layers, probs_host, n_p, pml_dev, grad_mean_dev,
+                                               grad_tvar_dev, grad_ylt_dev, stream);
+    return e ? fail(e) : ART_OK;
+}
+
+art_status art_run_ylt_backward(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
+                                const int64_t* trial_off_dev, int32_t events_per_trial, const uint8_t* branch_dev,
+                                const double* grad_ylt_dev, double* grad_terms_dev, double* grad_mult_dev,
+                                cudaStream_t stream) {
+    if (!p) return ART_EINVAL;
+    art_status st = validate_yet(n_trials, event_ids_dev, trial_off_dev, events_per_trial);
+    if (st) return st;
+    if (!grad_terms_dev || !grad_mult_dev || (n_trials > 0 && (!branch_dev || !grad_ylt_dev))) return ART_EINVAL;
+    if (!(p->layouts & ART_LAYOUT_LAYER)) return ART_EUNSUPPORTED;
+    YetArgs y{event_ids_dev, trial_off_dev, n_trials, trial_off_dev ? 0 : events_per_trial, p->catalogue};
+    const cudaError_t e = launch_adjoint(p, y, branch_dev, grad_ylt_dev, grad_terms_dev, grad_mult_dev, stream);
+    return e ? fail(e) : ART_OK;
+}
+
+art_status art_get_device_status(art_portfolio* p, cudaStream_t stream) {
+    if (!p) return ART_EINVAL;
+    int flags[kNumFlags] = {0, 0, 0, 0};
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (!e) e = cudaMemcpy(flags, p->d_flags, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemset(p->d_flags, 0, sizeof(flags));
+    if (e) return fail(e);
+    if (flags[kFlagIdRange]) return ART_EID_RANGE;
+    if (flags[kFlagBadOffsets]) return ART_EINVAL;
+    return ART_OK;
+}
+
+art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes, int64_t* pool64_bytes) {
+    if (!p) return ART_EINVAL;
+    if (layer_bytes) *layer_bytes = p->layer_bytes;
+    if (pool_bytes) *pool_bytes = p->pool_bytes;
+    if (pool64_bytes) *pool64_bytes = p->pool64_bytes;
+    return ART_OK;
+}
+
+void art_destroy_portfolio(art_portfolio* p) { free_portfolio(p); }
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// art_internal.cuh -- internal types and device helpers of libart.
+//
+// Everything here serves the kernels behind include/art.h. The method is
+// Section II / Algorithm 1 of Bahl et al. (arXiv:1308.2572); the layouts are
+// the direct-access tables of Section III, re-laid out event-major so that one
+// event's losses across a layer's (or the pool's) ELTs are contiguous.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "art.h"
+
+namespace art {
+
+constexpr int kMaxLayerElts = 32;   // ELTs per layer (the paper: 3-30)
+constexpr int kMaxPoolElts = 512;   // widest pool row the batched kernel reads
+constexpr int kMaxProbs = 8;        // probabilities per art_metrics call
+
+// Error flag slots in the portfolio's device flag array.
+enum { kFlagIdRange = 0, kFlagBadOffsets = 1, kNumFlags = 4 };
+
+// XL(v; R, L) = min(max(v - R, 0), L), the excess-of-loss form of the
+// occurrence (Algorithm 1 step 3) and aggregate (step 4) terms.
+__device__ __forceinline__ float xl_f32(float v, float r, float l) { return fminf(fmaxf(v - r, 0.0f), l); }
+__device__ __forceinline__ double xl_f64(double v, double r, double l) { return fmin(fmax(v - r, 0.0), l); }
+
+// Per-ELT financial terms (step 2), read as F(y) = XL(m y; D, Lim) with the
+// product and the deductible in one FMA rounding.
+__device__ __forceinline__ float fin_f32(float y, float m, float d, float lim) {
+    return fminf(fmaxf(__fmaf_rn(m, y, -d), 0.0f), lim);
+}
+__device__ __forceinline__ double fin_f64(double y, double m, double d, double lim) {
+    return fmin(fmax(fma(m, y, -d), 0.0), lim);
+}
+
+// Aggregate branch code stored for the adjoint: 1 strictly between the
+// retention and retention + limit, 2 strictly above, 0 otherwise.
+__device__ __forceinline__ uint8_t agg_branch(double s, double r, double l) {
+    double w = s - r;
+    if (!(w > 0.0)) return 0;
+    if (w > l) return 2;
+    if (w < l) return 1;
+    return 0;
+}
+
+// Terms of one layer as the plain kernel reads them: passed by value, so they
+// sit in the kernel-parameter constant bank and unrolled loops use them as
+// constant operands. Padding ELTs (index >= n) have m = 1, D = 0, Lim = inf
+// and zero table entries, so they add exactly 0.
+struct LayerArgs {
+    const float* table;   // [C][np] event-major direct-access table of the layer
+    float m[kMaxLayerElts];
+    float d[kMaxLayerElts];
+    float lim[kMaxLayerElts];
+    float occ_ret, occ_lim;
+    double agg_ret, agg_lim;
+    int32_t layer;        // layer index (row of the YLT)
+};
+
+struct YetArgs {
+    const int32_t* ids;
+    const int64_t* off;   // NULL: dense
+    int64_t n_trials;
+    int32_t k;            // events per trial when dense
+    int32_t catalogue;
+};
+
+__device__ __forceinline__ void trial_range(const YetArgs& y, int64_t t, int64_t& b, int64_t& e, bool& bad) {
+    if (y.off) {
+        b = y.off[t];
+        e = y.off[t + 1];
+        bad = e < b;
+        if (bad) e = b;
+    } else {
+        b = t * (int64_t)y.k;
+        e = b + y.k;
+        bad = false;
+    }
+}
+
+// Streaming loads (evict-first) for the YET, read exactly once per pass.
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+
+// Batched layout description shared by the host and the batched kernels.
+struct BatchedArgs {
+    const void* pool;          // [C][pool_np] FP32 or FP64
+    const float* elt_terms;    // [3][pool_np]  m, D, Lim (FP32)
+    const double* elt_terms64; // [3][pool_np]  same values in FP64
+    const uint8_t* memb;       // [n_tiles][pool_np][32] slot bits per (ELT, lane)
+    const int32_t* slot_layer; // [n_tiles][slots][32] layer of (slot, lane), -1 if empty
+    const float* occ;          // [n_layers][2] OccR, OccL (FP32)
+    const double* agg;         // [n_layers][2] AggR, AggL
+    int32_t pool_np;
+    int32_t n_layers;
+    int32_t n_tiles;
+    int32_t slots;
+};
+
+}  // namespace art
+
+// The opaque portfolio.
+struct art_portfolio {
+    int device = 0;
+    int32_t catalogue = 0, n_elt = 0, n_layers = 0;
+    int32_t layouts = 0, variant = ART_VARIANT_AUTO, flags = 0;
+    int32_t trial_tile = 0, cta_threads = 0;
+    int num_sms = 0;
+
+    // terms as applied (after rounding)
+    std::vector<float> mult, ded, lim, occ_ret, occ_lim;
+    std::vector<double> agg_ret, agg_lim;
+    std::vector<int32_t> loff, lids;
+
+    // ART_LAYOUT_LAYER: per layer [C][np_j]
+    std::vector<float*> layer_tab;
+    std::vector<int32_t> layer_np;
+    int64_t layer_bytes = 0;
+
+    // ART_LAYOUT_POOL / POOL64: [C][pool_np]
+    float* pool = nullptr;
+    double* pool64 = nullptr;
+    int32_t pool_np = 0;
+    int64_t pool_bytes = 0, pool64_bytes = 0;
+
+    // batched metadata (device)
+    float* d_elt_terms = nullptr;      // [3][pool_np]
+    double* d_elt_terms64 = nullptr;   // [3][pool_np]
+    uint8_t* d_memb = nullptr;
+    int32_t* d_slot_layer = nullptr;
+    float* d_occ = nullptr;
+    double* d_agg = nullptr;
+    int32_t slots = 0, n_tiles = 0;
+    unsigned int* d_work_counter = nullptr;
+
+    int* d_flags = nullptr;            // [kNumFlags]
+    int32_t* d_loff = nullptr;         // device copies of the layer lists
+    int32_t* d_lids = nullptr;
+
+    // host-run staging
+    int32_t* stage_ids[2] = {nullptr, nullptr};
+    int64_t* stage_off[2] = {nullptr, nullptr};
+    double* stage_ylt[2] = {nullptr, nullptr};
+    int64_t stage_ids_cap = 0, stage_trials_cap = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+
+    // cached graph of one batched launch
+    cudaGraphExec_t graph_exec = nullptr;
+    const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t graph_key_n[2] = {0, 0};
+};
+
+namespace art {
+
+// Host-side launchers (each returns a CUDA error code).
+cudaError_t launch_plain(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t launch_batched(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, bool fp64,
+                           cudaStream_t s);
+cudaError_t launch_adjoint(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,
+                           double* grad_terms, double* grad_mult, cudaStream_t s);
+cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
+                        double* mean, double* pml, double* tvar, cudaStream_t s);
+cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs,
+                                 int32_t n_p, const double* pml, const double* gmean, const double* gtvar,
+                                 double* gylt, cudaStream_t s);
+cudaError_t build_layer_table(const float* src, int32_t catalogue, const int32_t* elts_dev, int32_t n,
+                              int32_t np, float* dst, cudaStream_t s);
+cudaError_t build_pool_table(const float* src, int32_t catalogue, int32_t n_elt, int32_t np, float* dst32,
+                             double* dst64, cudaStream_t s);
+
+// k = ceil((1 - p) N) with the integer guard; at least 1, at most N.
+int64_t tail_count(double p, int64_t n);
+
+void set_last_error(cudaError_t e);
+
+// Set (bytes > 0) or clear (bytes == 0) a persisting L2 access-policy window
+// over a hot table on a stream.
+cudaError_t set_window(cudaStream_t s, const void* base, size_t bytes);
+
+}  // namespace art

@@ -1,0 +1,427 @@
+// metrics.cu -- expected loss, PML and TVaR from the YLT (Section I names PML
+// and TVaR as the risk metrics derived from a YLT; Section II applies
+// "financial functions or filters" to the trial losses).
+//
+// Reading: per layer, with k = ceil((1-p) N) (at least 1), PML_p is the k-th
+// largest trial loss and TVaR_p the mean of the k largest.
+//
+// Exact selection without a sort: trial losses are >= 0, so the FP64 bit
+// pattern (sign cleared, which also folds -0 onto +0) orders like the value.
+// A most-significant-digit radix select over 63 bits in six passes (digits of
+// 11, 11, 11, 11, 11 and 8 bits) narrows, for every (layer, probability)
+// problem at once, the prefix of the k-th largest key: each pass histograms
+// the keys that match the prefix found so far (shared-memory histograms,
+// flushed to global with atomics), and a one-CTA-per-problem kernel picks the
+// digit where the count from the top crosses the remaining rank. A last pass
+// sums the values strictly above the k-th largest; TVaR adds the tied
+// remainder: (sum_gt + (k - count_gt) * PML) / k. Sums are FP64 and
+// deterministic (per-thread, per-block, then per-problem in a fixed order).
+#include <algorithm>
+#include <cmath>
+
+#include "art_internal.cuh"
+
+namespace art {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBins = 2048;
+constexpr int kPasses = 6;
+__host__ __device__ constexpr int pass_shift(int i) { return i < 5 ? 52 - 11 * i : 0; }
+__host__ __device__ constexpr int pass_bits(int i) { return i < 5 ? 11 : 8; }
+
+struct KParams {
+    long long k[kMaxProbs];
+};
+
+struct SelState {
+    unsigned long long prefix;
+    unsigned long long mask;
+    long long krem;
+    long long k;
+};
+
+__device__ __forceinline__ unsigned long long key_of(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// Block-wide sum of a double in a fixed order (warp tree, then warps in order).
+__device__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    return r;  // valid in thread 0
+}
+
+__device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    return r;
+}
+
+__global__ void init_state_kernel(SelState* st, int n_problems, int n_p, const KParams kq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_problems) {
+        st[i].prefix = 0;
+        st[i].mask = 0;
+        st[i].k = kq.k[i % n_p];
+        st[i].krem = kq.k[i % n_p];
+    }
+}
+
+// One pass: grid (blocks_per_layer, n_layers). The first pass also writes
+// the block's partial sum of the layer's values (for the mean).
+__global__ void __launch_bounds__(kThreads) hist_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                        const SelState* __restrict__ st, int shift, int bits,
+                                                        unsigned int* __restrict__ ghist,
+                                                        double* __restrict__ part_sum) {
+    extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
+    __shared__ double sh_red[32];
+    const int nb = 1 << bits;
+    const int j = blockIdx.y;
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
+    unsigned long long pre[kMaxProbs], msk[kMaxProbs];
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) {
+        pre[q] = q < n_p ? st[j * n_p + q].prefix : 1ULL;  // unused slots never match
+        msk[q] = q < n_p ? st[j * n_p + q].mask : 0ULL;
+    }
+    __syncthreads();
+    const double* row = ylt + (size_t)j * (size_t)n;
+    double sum = 0.0;
+    const unsigned dmask = (unsigned)nb - 1u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = row[i];
+        if (part_sum) sum += v;
+        const unsigned long long key = key_of(v);
+        const unsigned dig = (unsigned)(key >> shift) & dmask;
+#pragma unroll
+        for (int q = 0; q < kMaxProbs; ++q)
+            if (q < n_p && (key & msk[q]) == pre[q]) atomicAdd(&sh_hist[q * nb + dig], 1u);
+    }
+    if (part_sum) {
+        const double r = block_sum(sum, sh_red);
+        if (threadIdx.x == 0) part_sum[(size_t)j * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
+        const unsigned c = sh_hist[i];
+        if (c) atomicAdd(&ghist[((size_t)j * n_p) * kMaxBins + (size_t)(i / nb) * kMaxBins + (i % nb)], c);
+    }
+}
+
+// One CTA per (layer, probability): find the digit where the count of keys
+// from the top reaches the remaining rank, extend the prefix, clear the bins.
+__global__ void __launch_bounds__(kThreads) select_kernel(SelState* st, unsigned int* ghist, int shift, int bits) {
+    __shared__ unsigned long long sh_scan[kThreads];
+    __shared__ int sh_bin;
+    __shared__ unsigned long long sh_above;
+    const int pidx = blockIdx.x;
+    const int nb = 1 << bits;
+    const int per = nb / kThreads > 0 ? nb / kThreads : 1;
+    unsigned int* h = ghist + (size_t)pidx * kMaxBins;
+    const long long krem = st[pidx].krem;
+    // thread i covers descending ranks [i*per, (i+1)*per): bins nb-1-i*per downwards
+    unsigned long long local = 0;
+    if (threadIdx.x * per < nb)
+        for (int r = 0; r < per; ++r) local += h[nb - 1 - (threadIdx.x * per + r)];
+    sh_scan[threadIdx.x] = local;
+    if (threadIdx.x == 0) sh_bin = -1;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele) over the 256 chunk counts, descending bins
+    for (int o = 1; o < kThreads; o <<= 1) {
+        const unsigned long long add = threadIdx.x >= (unsigned)o ? sh_scan[threadIdx.x - o] : 0ULL;
+        __syncthreads();
+        sh_scan[threadIdx.x] += add;
+        __syncthreads();
+    }
+    const unsigned long long incl = sh_scan[threadIdx.x];
+    const unsigned long long excl = incl - local;
+    if (threadIdx.x * per < nb && (long long)excl < krem && krem <= (long long)incl) {
+        unsigned long long run = excl;
+        for (int r = 0; r < per; ++r) {
+            const int bin = nb - 1 - (threadIdx.x * per + r);
+            const unsigned c = h[bin];
+            if ((long long)(run + c) >= krem) {
+                sh_bin = bin;
+                sh_above = run;
+                break;
+            }
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int bin = sh_bin < 0 ? 0 : sh_bin;  // unreachable when counts are consistent
+        st[pidx].prefix |= (unsigned long long)bin << shift;
+        st[pidx].mask |= (unsigned long long)(nb - 1) << shift;
+        st[pidx].krem = krem - (long long)(sh_bin < 0 ? 0 : sh_above);
+    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+}
+
+// Per block and problem: count and sum of values strictly above the k-th key.
+__global__ void __launch_bounds__(kThreads) tail_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                        const SelState* __restrict__ st,
+                                                        unsigned long long* __restrict__ part_cnt,
+                                                        double* __restrict__ part_sum) {
+    __shared__ double sh_red[32];
+    __shared__ unsigned long long sh_red_u[32];
+    const int j = blockIdx.y;
+    unsigned long long thr[kMaxProbs];
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
+    const double* row = ylt + (size_t)j * (size_t)n;
+    double s[kMaxProbs];
+    unsigned long long c[kMaxProbs];
+    for (int q = 0; q < kMaxProbs; ++q) {
+        s[q] = 0.0;
+        c[q] = 0;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = row[i];
+        const unsigned long long key = key_of(v);
+#pragma unroll
+        for (int q = 0; q < kMaxProbs; ++q)
+            if (q < n_p && key > thr[q]) {
+                s[q] += v;
+                c[q] += 1;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) {
+        if (q >= n_p) break;
+        const double rs = block_sum(s[q], sh_red);
+        const unsigned long long rc = block_sum_u64(c[q], sh_red_u);
+        if (threadIdx.x == 0) {
+            const size_t w = ((size_t)j * n_p + q) * gridDim.x + blockIdx.x;
+            part_sum[w] = rs;
+            part_cnt[w] = rc;
+        }
+    }
+}
+
+__global__ void finalize_kernel(const SelState* __restrict__ st, int n_layers, int n_p, int nblk, int64_t n,
+                                const double* __restrict__ mean_part, const unsigned long long* __restrict__ tail_cnt,
+                                const double* __restrict__ tail_sum, double* mean, double* pml, double* tvar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_layers * n_p) return;
+    const int j = i / n_p, q = i % n_p;
+    if (q == 0 && mean) {
+        double m = 0.0;
+        for (int b = 0; b < nblk; ++b) m += mean_part[(size_t)j * nblk + b];
+        mean[j] = m / (double)n;
+    }
+    double sgt = 0.0;
+    unsigned long long cgt = 0;
+    for (int b = 0; b < nblk; ++b) {
+        sgt += tail_sum[(size_t)i * nblk + b];
+        cgt += tail_cnt[(size_t)i * nblk + b];
+    }
+    const double v = __longlong_as_double((long long)st[i].prefix);
+    const long long k = st[i].k;
+    if (pml) pml[i] = v;
+    if (tvar) tvar[i] = (sgt + (double)(k - (long long)cgt) * v) / (double)k;
+}
+
+// Backward: counts of values above and equal to each PML, then the weights.
+__global__ void __launch_bounds__(kThreads) count_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                         const double* __restrict__ pml,
+                                                         unsigned long long* __restrict__ part_gt,
+                                                         unsigned long long* __restrict__ part_eq) {
+    __shared__ unsigned long long sh_red_u[32];
+    const int j = blockIdx.y;
+    unsigned long long thr[kMaxProbs], gt[kMaxProbs], eq[kMaxProbs];
+    for (int q = 0; q < kMaxProbs; ++q) {
+        thr[q] = q < n_p ? key_of(pml[j * n_p + q]) : 0;
+        gt[q] = 0;
+        eq[q] = 0;
+    }
+    const double* row = ylt + (size_t)j * (size_t)n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = key_of(row[i]);
+#pragma unroll
+        for (int q = 0; q < kMaxProbs; ++q) {
+            gt[q] += (q < n_p && key > thr[q]) ? 1 : 0;
+            eq[q] += (q < n_p && key == thr[q]) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) {
+        if (q >= n_p) break;
+        const unsigned long long a = block_sum_u64(gt[q], sh_red_u);
+        const unsigned long long b = block_sum_u64(eq[q], sh_red_u);
+        if (threadIdx.x == 0) {
+            const size_t w = ((size_t)j * n_p + q) * gridDim.x + blockIdx.x;
+            part_gt[w] = a;
+            part_eq[w] = b;
+        }
+    }
+}
+
+__global__ void weights_kernel(int n_layers, int n_p, int nblk, const KParams kq,
+                               const unsigned long long* __restrict__ part_gt,
+                               const unsigned long long* __restrict__ part_eq, double* __restrict__ w_gt,
+                               double* __restrict__ w_eq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_layers * n_p) return;
+    unsigned long long cg = 0, ce = 0;
+    for (int b = 0; b < nblk; ++b) {
+        cg += part_gt[(size_t)i * nblk + b];
+        ce += part_eq[(size_t)i * nblk + b];
+    }
+    const double k = (double)kq.k[i % n_p];
+    w_gt[i] = 1.0 / k;
+    w_eq[i] = ce ? ((k - (double)cg) / (k * (double)ce)) : 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) grad_ylt_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                            const double* __restrict__ pml,
+                                                            const double* __restrict__ gmean,
+                                                            const double* __restrict__ gtvar,
+                                                            const double* __restrict__ w_gt,
+                                                            const double* __restrict__ w_eq,
+                                                            double* __restrict__ gylt) {
+    const int j = blockIdx.y;
+    const double base = gmean ? gmean[j] / (double)n : 0.0;
+    unsigned long long thr[kMaxProbs];
+    double cg[kMaxProbs], ce[kMaxProbs];
+    for (int q = 0; q < kMaxProbs; ++q) {
+        const bool on = q < n_p && gtvar;
+        thr[q] = on ? key_of(pml[j * n_p + q]) : 0;
+        cg[q] = on ? gtvar[j * n_p + q] * w_gt[j * n_p + q] : 0.0;
+        ce[q] = on ? gtvar[j * n_p + q] * w_eq[j * n_p + q] : 0.0;
+    }
+    const double* row = ylt + (size_t)j * (size_t)n;
+    double* out = gylt + (size_t)j * (size_t)n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = key_of(row[i]);
+        double g = base;
+#pragma unroll
+        for (int q = 0; q < kMaxProbs; ++q) {
+            if (q < n_p) {
+                if (key > thr[q]) g += cg[q];
+                else if (key == thr[q]) g += ce[q];
+            }
+        }
+        out[i] = g;
+    }
+}
+
+int blocks_per_layer(int64_t n, int n_layers) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (n + (int64_t)kThreads * 16 - 1) / ((int64_t)kThreads * 16);
+    int64_t cap = std::max<int64_t>(1, (4LL * sms + n_layers - 1) / n_layers);
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int64_t tail_count(double p, int64_t n) {
+    if (n <= 0) return 0;
+    const double q = (1.0 - p) * (double)n;
+    const double r = std::nearbyint(q);
+    int64_t k = (std::fabs(q - r) <= 1e-9 * (double)n) ? (int64_t)r : (int64_t)std::ceil(q);
+    return std::min<int64_t>(n, std::max<int64_t>(1, k));
+}
+
+cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
+                        double* mean, double* pml, double* tvar, cudaStream_t s) {
+    const int nblk = blocks_per_layer(n, n_layers);
+    const int n_prob = n_layers * n_p;
+    // scratch: k values, state, histograms, partial sums
+    const size_t o_st = 0;
+    const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
+    const size_t o_ms = align256(o_h + sizeof(unsigned int) * kMaxBins * (size_t)n_prob);
+    const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
+    const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
+    const size_t total = align256(o_ts + sizeof(double) * (size_t)n_prob * nblk);
+    char* w = nullptr;
+    cudaError_t err = cudaMallocAsync((void**)&w, total, s);
+    if (err != cudaSuccess) return err;
+    KParams kq = {};
+    for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs[q], n);
+    auto* st = (SelState*)(w + o_st);
+    auto* hist = (unsigned int*)(w + o_h);
+    auto* msum = (double*)(w + o_ms);
+    auto* tcnt = (unsigned long long*)(w + o_tc);
+    auto* tsum = (double*)(w + o_ts);
+    do {
+        if ((err = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kMaxBins * (size_t)n_prob, s))) break;
+        init_state_kernel<<<(n_prob + 255) / 256, 256, 0, s>>>(st, n_prob, n_p, kq);
+        if ((err = cudaGetLastError())) break;
+        for (int i = 0; i < kPasses && !err; ++i) {
+            const int bits = pass_bits(i);
+            const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
+            if (shm > 48 * 1024) {
+                err = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+                if (err) break;
+            }
+            hist_kernel<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, hist,
+                                                                   i == 0 ? msum : nullptr);
+            if ((err = cudaGetLastError())) break;
+            select_kernel<<<n_prob, kThreads, 0, s>>>(st, hist, pass_shift(i), bits);
+            err = cudaGetLastError();
+        }
+        if (err) break;
+        tail_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_p, st, tcnt, tsum);
+        if ((err = cudaGetLastError())) break;
+        finalize_kernel<<<(n_prob + 127) / 128, 128, 0, s>>>(st, n_layers, n_p, nblk, n, msum, tcnt, tsum, mean,
+                                                             pml, tvar);
+        err = cudaGetLastError();
+    } while (0);
+    const cudaError_t e2 = cudaFreeAsync(w, s);
+    return err ? err : e2;
+}
+
+cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
+                                 const double* pml, const double* gmean, const double* gtvar, double* gylt,
+                                 cudaStream_t s) {
+    const int nblk = blocks_per_layer(n, n_layers);
+    const int n_prob = n_layers * n_p;
+    const size_t o_g = 0;
+    const size_t o_e = align256(o_g + sizeof(unsigned long long) * (size_t)n_prob * nblk);
+    const size_t o_wg = align256(o_e + sizeof(unsigned long long) * (size_t)n_prob * nblk);
+    const size_t o_we = align256(o_wg + sizeof(double) * n_prob);
+    const size_t total = align256(o_we + sizeof(double) * n_prob);
+    char* w = nullptr;
+    cudaError_t err = cudaMallocAsync((void**)&w, total, s);
+    if (err != cudaSuccess) return err;
+    KParams kq = {};
+    for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs[q], n);
+    auto* pg = (unsigned long long*)(w + o_g);
+    auto* pe = (unsigned long long*)(w + o_e);
+    auto* wg = (double*)(w + o_wg);
+    auto* we = (double*)(w + o_we);
+    do {
+        if (gtvar) {
+            count_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_p, pml, pg, pe);
+            if ((err = cudaGetLastError())) break;
+            weights_kernel<<<(n_prob + 127) / 128, 128, 0, s>>>(n_layers, n_p, nblk, kq, pg, pe, wg, we);
+            if ((err = cudaGetLastError())) break;
+        }
+        grad_ylt_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, gtvar ? n_p : 0, pml, gmean, gtvar, wg, we,
+                                                                 gylt);
+        err = cudaGetLastError();
+    } while (0);
+    const cudaError_t e2 = cudaFreeAsync(w, s);
+    return err ? err : e2;
+}
+
+}  // namespace art

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Small workloads are compared element by element in full; the paper-scale
+workloads run in the launch configuration the bench times and are compared
+on sampled trials the oracle computes one by one. Tolerance: |dY| <= 1e-6 x
+the trial's gross loss for every (layer, trial).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1308_2572_gb300 import art, workloads
+
+from gpu_util import assert_ylt_close, device_yet, gpu_metrics, oracle_sample, run_ylt, METRIC_RTOL
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_FP64]
+ALL_LAYOUTS = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_POOL64
+
+
+def _small_cases():
+    return {
+        "ragged_csr_with_empty_trials": dict(seed=101, n_trials=1000, min_len=0, max_len=130),
+        "dense_k37": dict(seed=102, n_trials=777, dense_k=37),
+        "dense_k1": dict(seed=103, n_trials=300, dense_k=1),
+        "single_trial": dict(seed=104, n_trials=1, min_len=250, max_len=250),
+        "inf_limits": dict(seed=105, n_trials=500, inf_limits=True),
+        "one_elt_layers": dict(seed=106, n_elt=9, n_layers=7, max_elts_per_layer=1, n_trials=400),
+        "thirty_two_elt_layers": dict(seed=107, catalogue=1001, n_elt=40, n_layers=5, n_trials=300,
+                                      max_elts_per_layer=32),
+        "many_layers_two_tiles": dict(seed=108, catalogue=333, n_elt=70, n_layers=300, n_trials=200, max_len=40,
+                                      max_elts_per_layer=32),
+        "multipliers": dict(seed=109, n_trials=400, mult_range=(0.3, 2.5)),
+        "wide_pool": dict(seed=110, catalogue=5003, n_elt=300, n_layers=20, n_trials=150, max_len=60,
+                          max_elts_per_layer=32, nnz_frac=0.05),
+    }
+
+
+@pytest.mark.parametrize("case", sorted(_small_cases()))
+def test_small_cases_all_variants(case):
+    kw = _small_cases()[case]
+    w = workloads.random_case(**kw)
+    ref, gross, _ = oracle.ylt(w.oracle_problem())
+    p = art.portfolio_from_workload(w, layouts=ALL_LAYOUTS)
+    try:
+        yet = device_yet(w)
+        for v in VARIANTS:
+            ylt, _ = run_ylt(p, w, v, yet=yet)
+            assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"{case} variant {v}")
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("name", ["c0", "c0u"])
+def test_config0_full(name):
+    w = workloads.make(name)
+    ref, gross, _ = oracle.ylt(w.oracle_problem())
+    if name == "c0":
+        assert np.all(ref == 2e7)  # the literal aggregate terms cap every trial
+    p = art.portfolio_from_workload(w, layouts=ALL_LAYOUTS)
+    try:
+        yet = device_yet(w)
+        for v in VARIANTS:
+            ylt, _ = run_ylt(p, w, v, yet=yet)
+            y = ylt.cpu().numpy()
+            assert_ylt_close(y, ref, gross, f"{name} variant {v}")
+            mean, pml, tvar = gpu_metrics(ylt, [0.99])
+            om, op, ot = oracle.metrics(ref, [0.99])
+            np.testing.assert_allclose(pml, op, rtol=METRIC_RTOL)
+            np.testing.assert_allclose(tvar, ot, rtol=METRIC_RTOL)
+            np.testing.assert_allclose(mean, om, rtol=METRIC_RTOL)
+    finally:
+        p.close()
+
+
+@pytest.fixture(scope="module")
+def c1u():
+    w = workloads.make("c1u")
+    p = art.portfolio_from_workload(w)
+    yet = device_yet(w)
+    yield w, p, yet
+    p.close()
+    del yet
+    torch.cuda.empty_cache()
+
+
+def test_config1_sampled_plain_and_batched(c1u):
+    """Paper scale (1e6 trials x 1000 events, 16 ELTs): the bench's launch,
+    checked on 3000 sampled trials plus the first and last trial."""
+    w, p, yet = c1u
+    rng = np.random.default_rng(0)
+    T = w.yet.n_trials
+    trials = np.unique(np.concatenate([[0, T - 1], rng.choice(T, 3000, replace=False)]))
+    ref, gross, _ = oracle_sample(w, trials)
+    for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED):
+        ylt, _ = run_ylt(p, w, v, yet=yet)
+        got = ylt[:, torch.from_numpy(trials).cuda()].cpu().numpy()
+        assert_ylt_close(got, ref, gross, f"c1u variant {v}")
+        assert torch.all(ylt >= 0) and torch.all(ylt <= w.portfolio.agg_lim[0])
+
+
+def test_config1_metrics_against_oracle_on_same_ylt(c1u):
+    """The metrics kernels against the oracle's full-sort metrics on the same
+    (GPU) YLT: the k-th largest is selected exactly."""
+    w, p, yet = c1u
+    ylt, _ = run_ylt(p, w, art.ART_VARIANT_BATCHED, yet=yet)
+    probs = [0.99, 0.996, 0.999]
+    mean, pml, tvar = gpu_metrics(ylt, probs)
+    om, op, ot = oracle.metrics(ylt.cpu().numpy(), probs)
+    np.testing.assert_array_equal(pml, op)
+    np.testing.assert_allclose(tvar, ot, rtol=1e-12)
+    np.testing.assert_allclose(mean, om, rtol=1e-12)
+
+
+def test_literal_config1_caps_every_trial():
+    w = workloads.make("c1", n_trials=20000)
+    p = art.portfolio_from_workload(w)
+    try:
+        ylt, _ = run_ylt(p, w, art.ART_VARIANT_PLAIN)
+        assert torch.all(ylt == 2e7)
+        ref, gross, _ = oracle_sample(w, np.arange(0, 20000, 97))
+        assert np.all(ref == 2e7)
+    finally:
+        p.close()
+
+
+def test_determinism_and_graph_replay():
+    w = workloads.random_case(201, catalogue=2000, n_elt=20, n_layers=40, n_trials=3000, max_len=90)
+    p = art.portfolio_from_workload(w)
+    try:
+        yet = device_yet(w)
+        a, _ = run_ylt(p, w, art.ART_VARIANT_BATCHED, yet=yet)
+        b, _ = run_ylt(p, w, art.ART_VARIANT_BATCHED, yet=yet)
+        assert torch.equal(a, b)
+        c, _ = run_ylt(p, w, art.ART_VARIANT_PLAIN, yet=yet)
+        d, _ = run_ylt(p, w, art.ART_VARIANT_PLAIN, yet=yet)
+        assert torch.equal(c, d)
+    finally:
+        p.close()
+    g = art.portfolio_from_workload(w, flags=art.ART_FLAG_GRAPH)
+    try:
+        ids, off, k, T = device_yet(w)
+        L = w.portfolio.n_layers
+        outs = []
+        for _ in range(3):
+            y = torch.zeros((L, T), dtype=torch.float64, device="cuda") if not outs else outs[0]
+            art.art_run_ylt(g, T, ids, off, k, y)
+            torch.cuda.synchronize()
+            outs.append(y.clone())
+        assert torch.equal(outs[0], a) and torch.equal(outs[1], a) and torch.equal(outs[2], a)
+    finally:
+        g.close()
+
+
+def test_host_buffers_match_device_path():
+    for w in (workloads.random_case(202, n_trials=5000, max_len=80), workloads.make("c0u")):
+        p = art.portfolio_from_workload(w)
+        try:
+            dev, _ = run_ylt(p, w, art.ART_VARIANT_BATCHED)
+            L, T = w.portfolio.n_layers, w.yet.n_trials
+            ids = torch.from_numpy(w.yet.event_ids).pin_memory()
+            off = None if w.yet.trial_off is None else torch.from_numpy(w.yet.trial_off)
+            out = torch.zeros((L, T), dtype=torch.float64).pin_memory()
+            art.art_run_ylt_host(p, T, ids, off, w.yet.events_per_trial, out)
+            assert torch.equal(out, dev.cpu())
+        finally:
+            p.close()
+
+
+def test_out_of_range_ids_flag_without_trapping():
+    w = workloads.random_case(203, n_trials=50, min_len=5, max_len=20)
+    ids = w.yet.event_ids.copy()
+    ids[3] = w.portfolio.catalogue_size + 5
+    ids[7] = -2
+    bad = workloads.Workload(w.name, w.portfolio, workloads.YET(w.yet.n_trials, ids, 0, w.yet.trial_off), w.probs)
+    p = art.portfolio_from_workload(w)
+    try:
+        for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED):
+            dids, off, k, T = device_yet(bad)
+            art.art_set_variant(p, v)
+            ylt = torch.zeros((w.portfolio.n_layers, T), dtype=torch.float64, device="cuda")
+            art.art_run_ylt(p, T, dids, off, k, ylt)
+            assert art.art_get_device_status(p) == art.ART_EID_RANGE
+            assert art.art_get_device_status(p) == art.ART_OK  # the flag was cleared
+            # bad events count as zero loss: same as the oracle with those ids on a zero row
+            fixed = ids.copy()
+            zero_ev = int(np.flatnonzero(w.portfolio.elt_losses.sum(axis=0) == 0)[0])
+            fixed[3] = zero_ev
+            fixed[7] = zero_ev
+            ref, gross, _ = oracle.ylt(dict(w.oracle_problem(), event_ids=fixed))
+            assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"bad ids variant {v}")
+    finally:
+        p.close()
+
+
+def test_decreasing_offsets_flag_einval():
+    w = workloads.random_case(204, n_trials=20, min_len=3, max_len=9)
+    off = w.yet.trial_off.copy()
+    off[5], off[6] = off[6], off[5]
+    p = art.portfolio_from_workload(w)
+    try:
+        ids = torch.from_numpy(w.yet.event_ids).cuda()
+        doff = torch.from_numpy(off).cuda()
+        ylt = torch.zeros((w.portfolio.n_layers, 20), dtype=torch.float64, device="cuda")
+        art.art_run_ylt(p, 20, ids, doff, 0, ylt)
+        assert art.art_get_device_status(p) == art.ART_EINVAL
+    finally:
+        p.close()
+
+
+def test_update_terms_and_rounding():
+    w = workloads.random_case(205, n_trials=300)
+    p = art.portfolio_from_workload(w)
+    try:
+        m, d, l, t = art.art_get_terms(p)
+        np.testing.assert_array_equal(m, w.portfolio.elt_mult)
+        terms = t.copy()
+        terms[:, 0] = terms[:, 0] * 1.7 + 0.1  # OccR: not FP32-representable in general
+        art.art_update_terms(p, terms=terms)
+        _, _, _, t2 = art.art_get_terms(p)
+        np.testing.assert_array_equal(t2[:, 0], terms[:, 0].astype(np.float32).astype(np.float64))
+        np.testing.assert_array_equal(t2[:, 2:], terms[:, 2:])
+        prob = dict(w.oracle_problem(), occ_ret=t2[:, 0])
+        ref, gross, _ = oracle.ylt(prob)
+        for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED):
+            ylt, _ = run_ylt(p, w, v)
+            assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"updated terms variant {v}")
+    finally:
+        p.close()
