@@ -121,9 +121,9 @@ def kernel_source_hash():
 
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (profiles/<kernel>_<workload>.txt lines
+    the current kernel sources (profiles/<kernel>_<workload>.md lines
     'dram_bytes_per_launch: N' and 'source_hash: H')."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -237,6 +237,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trials", type=int, default=0,
+                    help="keep only the first N trials (small cases for profiling; 0 = the full workload)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -254,7 +256,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     t_gen = time.perf_counter()
-    w = workloads.make(args.config)
+    w = workloads.make(args.config, n_trials=args.trials or None)
     log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
