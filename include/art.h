@@ -206,6 +206,40 @@ ART_API art_status art_metrics(const double* ylt_dev, int64_t n_trials, int32_t 
                        int32_t n_p, double* mean_dev, double* pml_dev, double* tvar_dev, cudaStream_t stream);
 
 /*
+ * art_metrics_noalloc -- art_metrics without any device allocation. The
+ * paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory while they run. Examples are pricing services
+ * that reserve all device memory up front under a fixed budget and treat
+ * any later allocation as a failure, hosts whose device memory belongs to
+ * another framework's allocator that must not be bypassed, and latency-
+ * critical paths where an allocation's implicit synchronisation or its
+ * failure modes are unacceptable.
+ *
+ * Same arguments, outputs and results as art_metrics. Instead of the
+ * stream-ordered allocator it uses one scratch array that the library
+ * defines in device memory at file scope, ART_METRICS_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) in size; every GPU that loads the library holds those 8 MiB until
+ * the process exits. The scratch needed is about
+ *   n_layers * n_p * (8 KiB + 32 B + 16 B * b) + n_layers * 8 B * b
+ * with b = min(ceil(n_trials / 4096), ceil(4 * SMs / n_layers)) blocks per
+ * layer; a call that needs more returns ART_EINVAL and enqueues nothing
+ * (in practice, n_layers * n_p above about 1000).
+ *
+ * The first call on each device looks up that device's address of the
+ * scratch array (cudaGetSymbolAddress, with the device current); make that
+ * first call before any stream capture. Every call on a device shares the
+ * one array, and the array keeps the previous call's contents (each call
+ * clears what must start at zero itself). Calls whose work overlaps on the
+ * GPU -- on different streams, or from different threads -- race on the
+ * scratch and give wrong results: order them on one stream or with events.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define ART_METRICS_NOALLOC_SCRATCH_BYTES (8u << 20)
+ART_API art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trials, int32_t n_layers,
+                                       const double* probs_host, int32_t n_p, double* mean_dev, double* pml_dev,
+                                       double* tvar_dev, cudaStream_t stream);
+
+/*
  * art_metrics_backward -- gradient of sum_j (gm_j mean_j + sum_q gt_{j,q}
  * TVaR_{j,q}) with respect to the YLT: grad_ylt[j][t] = gm_j / T
  * + sum_q gt_{j,q} w_{j,q}(t), where w = 1/k for Y > PML, (k - #greater) /

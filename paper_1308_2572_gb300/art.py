@@ -26,7 +26,7 @@ ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH = 1, 2
 EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set_variant", "art_run_ylt",
            "art_run_ylt_host", "art_metrics", "art_metrics_backward", "art_run_ylt_backward",
            "art_get_device_status", "art_get_footprint", "art_destroy_portfolio", "art_status_string",
-           "art_last_cuda_error", "art_version")
+           "art_last_cuda_error", "art_version", "art_metrics_noalloc")
 
 
 class LayerTerms(ctypes.Structure):
@@ -71,6 +71,7 @@ def lib():
         "art_run_ylt_host": ([P, i64, P, P, i32, P, P], st),
         "art_metrics": ([P, i64, i32, P, i32, P, P, P, P], st),
         "art_metrics_backward": ([P, i64, i32, P, i32, P, P, P, P, P], st),
+        "art_metrics_noalloc": ([P, i64, i32, P, i32, P, P, P, P], st),
         "art_run_ylt_backward": ([P, i64, P, P, i32, P, P, P, P, P], st),
         "art_get_device_status": ([P, P], st),
         "art_get_footprint": ([P, P, P, P], st),
@@ -223,6 +224,20 @@ def art_metrics(ylt, n_trials: int, n_layers: int, probs: Sequence[float], mean=
     rc = lib().art_metrics(_dptr(ylt), int(n_trials), int(n_layers), _hptr(pr), pr.size, _dptr(mean), _dptr(pml),
                            _dptr(tvar), _stream(stream))
     _check(rc, "art_metrics")
+
+
+def art_metrics_noalloc(ylt, n_trials: int, n_layers: int, probs: Sequence[float], mean=None, pml=None, tvar=None,
+                        stream=None) -> None:
+    """art_metrics for callers that cannot allocate device memory: the
+    library's fixed 8 MiB static scratch instead of the stream-ordered
+    allocator. Calls that overlap on the GPU race on that scratch."""
+    pr = np.ascontiguousarray(probs, dtype=np.float64)
+    rc = lib().art_metrics_noalloc(_dptr(ylt), int(n_trials), int(n_layers), _hptr(pr), pr.size, _dptr(mean),
+                                   _dptr(pml), _dptr(tvar), _stream(stream))
+    if rc == ART_EINVAL:
+        raise ArtError(rc, "art_metrics_noalloc (invalid arguments, or the layers x probabilities need more than "
+                           "the 8 MiB static scratch)")
+    _check(rc, "art_metrics_noalloc")
 
 
 def art_metrics_backward(ylt, n_trials: int, n_layers: int, probs, pml, grad_mean, grad_tvar, grad_ylt,

@@ -425,3 +425,105 @@ cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers,
 }
 
 }  // namespace art
+
+// ---------------------------------------------------------------------------
+// art_metrics_noalloc: the same kernels over a fixed scratch array that the
+// library defines at file scope, for callers that cannot allocate device
+// memory (see include/art.h). The array lives in every device's copy of this
+// module; host code never dereferences its name, it asks the runtime for the
+// device address once per device.
+#include <mutex>
+
+namespace art {
+
+static __device__ __align__(256) unsigned char g_metrics_noalloc_scratch[ART_METRICS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up on
+// the first call per device (with that device current) and cached.
+cudaError_t noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_metrics_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace art
+
+extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trials, int32_t n_layers,
+                                          const double* probs_host, int32_t n_p, double* mean_dev, double* pml_dev,
+                                          double* tvar_dev, cudaStream_t stream) {
+    using namespace art;
+    if (!ylt_dev || n_trials < 1 || n_trials > 0x7fffffffLL || n_layers < 1 || n_layers > 65535 || !probs_host ||
+        n_p < 1 || n_p > kMaxProbs)
+        return ART_EINVAL;
+    for (int q = 0; q < n_p; ++q)
+        if (!(probs_host[q] > 0.0 && probs_host[q] < 1.0)) return ART_EINVAL;
+    const int nblk = blocks_per_layer(n_trials, n_layers);
+    const int n_prob = n_layers * n_p;
+    const size_t o_st = 0;
+    const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
+    const size_t o_ms = align256(o_h + sizeof(unsigned int) * kMaxBins * (size_t)n_prob);
+    const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
+    const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
+    const size_t total = align256(o_ts + sizeof(double) * (size_t)n_prob * nblk);
+    if (total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
+    unsigned char* w = nullptr;
+    cudaError_t err = noalloc_scratch(&w);
+    if (err != cudaSuccess) {
+        set_last_error(err);
+        return ART_ECUDA;
+    }
+    KParams kq = {};
+    for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs_host[q], n_trials);
+    auto* st = (SelState*)(w + o_st);
+    auto* hist = (unsigned int*)(w + o_h);
+    auto* msum = (double*)(w + o_ms);
+    auto* tcnt = (unsigned long long*)(w + o_tc);
+    auto* tsum = (double*)(w + o_ts);
+    do {
+        // the scratch keeps the previous call's contents: the histograms must start at zero
+        if ((err = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kMaxBins * (size_t)n_prob, stream))) break;
+        init_state_kernel<<<(n_prob + 255) / 256, 256, 0, stream>>>(st, n_prob, n_p, kq);
+        if ((err = cudaGetLastError())) break;
+        for (int i = 0; i < kPasses && !err; ++i) {
+            const int bits = pass_bits(i);
+            const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
+            if (shm > 48 * 1024) {
+                err = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+                if (err) break;
+            }
+            hist_kernel<<<dim3(nblk, n_layers), kThreads, shm, stream>>>(ylt_dev, n_trials, n_p, st, pass_shift(i),
+                                                                        bits, hist, i == 0 ? msum : nullptr);
+            if ((err = cudaGetLastError())) break;
+            select_kernel<<<n_prob, kThreads, 0, stream>>>(st, hist, pass_shift(i), bits);
+            err = cudaGetLastError();
+        }
+        if (err) break;
+        tail_kernel<<<dim3(nblk, n_layers), kThreads, 0, stream>>>(ylt_dev, n_trials, n_p, st, tcnt, tsum);
+        if ((err = cudaGetLastError())) break;
+        finalize_kernel<<<(n_prob + 127) / 128, 128, 0, stream>>>(st, n_layers, n_p, nblk, n_trials, msum, tcnt, tsum,
+                                                                  mean_dev, pml_dev, tvar_dev);
+        err = cudaGetLastError();
+    } while (0);
+    if (err != cudaSuccess) {
+        set_last_error(err);
+        return ART_ECUDA;
+    }
+    return ART_OK;
+}
