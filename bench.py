@@ -135,6 +135,22 @@ def recorded_traffic(kernel: str, workload: str):
     return float(m.group(1))
 
 
+def layer_groups(port):
+    """The library's layer groups (consecutive layers while a group has at
+    most 8 layers and at most 32 distinct ELTs), as ELT-id lists."""
+    groups, uni, n = [], [], 0
+    for j in range(port.n_layers):
+        elts = [int(e) for e in port.layer_elt_ids[port.layer_elt_off[j]:port.layer_elt_off[j + 1]]]
+        merged = uni + [e for e in elts if e not in uni]
+        if n and (n >= 8 or len(merged) > 32):
+            groups.append(uni)
+            uni, n, merged = [], 0, list(elts)
+        uni, n = merged, n + 1
+    if n:
+        groups.append(uni)
+    return groups
+
+
 def algorithmic_bytes(w, variant: str):
     """Algorithmic bytes of one forward launch set.
 
@@ -153,6 +169,19 @@ def algorithmic_bytes(w, variant: str):
     C = port.catalogue_size
     sizes = port.elts_per_layer()
     pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
+    if variant == "skip":
+        # per group: the id stream, one bitmap word per event (L1/L2), and a
+        # row read only for events with a non-zero loss in the group's ELTs
+        hbm = 0.0
+        l2 = 0.0
+        frac_touched = 1.0 - np.exp(-n_events / C)
+        for g in layer_groups(port):
+            rowb = 4 * pad(len(g))
+            nz = np.any(port.elt_losses[g] != 0, axis=0)
+            p_nz = float(nz.mean())
+            hbm += ids + C / 8 + nz.sum() * rowb * frac_touched
+            l2 += ids + n_events * p_nz * 32 * -(-rowb // 32)
+        return {"hbm": hbm + ylt, "l2": l2, "ids": ids, "ylt": ylt, "table": None}
     if variant == "plain":
         row = np.array([4 * pad(int(n)) for n in sizes])
         sectors = int(sum(32 * -(-r // 32) for r in row)) * n_events
@@ -231,7 +260,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64", "skip"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -260,7 +289,8 @@ def main():
     log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
-    layouts = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | (art.ART_LAYOUT_POOL64 if args.variant == "fp64" else 0)
+    layouts = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP
+               | (art.ART_LAYOUT_POOL64 if args.variant == "fp64" else 0))
     p = art.portfolio_from_workload(w, device=dev, layouts=layouts)
     ids = torch.from_numpy(yet.event_ids).to(dev)
     off = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).to(dev)
@@ -271,14 +301,15 @@ def main():
     pml = torch.empty((L, n_p), dtype=torch.float64, device=dev)
     tvar = torch.empty((L, n_p), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64}
+    vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64,
+            "skip": art.ART_VARIANT_SKIP}
 
     def step():
         art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
         art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
 
     # variant choice: time each candidate forward (untimed for the result)
-    cands = [args.variant] if args.variant != "auto" else ["plain", "batched"]
+    cands = [args.variant] if args.variant != "auto" else ["plain", "batched", "skip"]
     fwd_ms = {}
     for v in cands:
         art.art_set_variant(p, vmap[v])
@@ -333,7 +364,7 @@ def main():
     peak, peak_kind = measured_peaks()
     ab = algorithmic_bytes(w, variant)
     achieved = ab["hbm"] / (fwd_mean / 1e3) / 1e9
-    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_batched_fp64"}[variant]
+    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_batched_fp64", "skip": "ylt_skip"}[variant]
     traffic = recorded_traffic(kernel_name, args.config)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
@@ -380,7 +411,8 @@ def main():
     # kernels of ours launched per step: forward (one per layer for the plain
     # variant, one persistent launch otherwise) + metrics (state init, 6 x
     # (histogram + select), tail sums, finalize)
-    launches = (L if variant == "plain" else 1) + 15
+    n_groups = len(layer_groups(port))
+    launches = {"plain": L, "skip": n_groups}.get(variant, 1) + 15
     if rank == 0:
         line = {
             "metric": "trial-events x ELTs per second", "value": value, "unit": "trial-events*ELTs/s",

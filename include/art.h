@@ -71,14 +71,18 @@ enum {
     ART_VARIANT_AUTO = 0,     /* batched when the pool layout exists, else plain          */
     ART_VARIANT_PLAIN = 1,    /* one launch per layer over a per-layer event-major table  */
     ART_VARIANT_BATCHED = 2,  /* one persistent launch over all layers (pool table)       */
-    ART_VARIANT_FP64 = 3      /* batched, with FP64 tables and FP64 per-event arithmetic  */
+    ART_VARIANT_FP64 = 3,     /* batched, with FP64 tables and FP64 per-event arithmetic  */
+    ART_VARIANT_SKIP = 4      /* one launch per layer group (<= 8 layers, <= 32 ELTs):
+                                 occupancy bitmap skips events whose losses are all zero  */
 };
 
 /* Layouts built by art_create_portfolio (bit mask). */
 enum {
     ART_LAYOUT_LAYER = 1,     /* per layer: [C][n_pad] FP32, the layer's ELTs side by side */
     ART_LAYOUT_POOL = 2,      /* all ELTs:  [C][n_elt_pad] FP32, shared by every layer     */
-    ART_LAYOUT_POOL64 = 4     /* all ELTs:  [C][n_elt_pad] FP64 (precision study)          */
+    ART_LAYOUT_POOL64 = 4,    /* all ELTs:  [C][n_elt_pad] FP64 (precision study)          */
+    ART_LAYOUT_GROUP = 8      /* per layer group: [C][n_pad] FP32 over the group's ELTs
+                                 plus a C-bit occupancy bitmap                             */
 };
 
 /* Flags. */
@@ -89,7 +93,7 @@ enum {
 };
 
 typedef struct {
-    int32_t layouts;          /* ART_LAYOUT_* mask; 0 means ART_LAYOUT_LAYER | ART_LAYOUT_POOL */
+    int32_t layouts;          /* ART_LAYOUT_* mask; 0 means LAYER | POOL | GROUP               */
     int32_t variant;          /* ART_VARIANT_*                                                */
     int32_t flags;            /* ART_FLAG_*                                                   */
     int32_t trial_tile;       /* batched: trials per work unit (0 = autotune / default)       */
@@ -282,7 +286,7 @@ ART_API art_status art_get_device_status(art_portfolio* p, cudaStream_t stream);
 
 /* Bytes of device memory the portfolio holds, per layout (NULL to skip). */
 ART_API art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes,
-                             int64_t* pool64_bytes);
+                                     int64_t* pool64_bytes, int64_t* group_bytes);
 
 /* Free the portfolio (synchronises the device first). NULL is a no-op. */
 ART_API void art_destroy_portfolio(art_portfolio* p);

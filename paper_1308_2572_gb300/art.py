@@ -18,8 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libart.so")
 
 ART_OK, ART_EINVAL, ART_ENOMEM, ART_ECUDA, ART_EID_RANGE, ART_ETIMEOUT, ART_EUNSUPPORTED = range(7)
-ART_VARIANT_AUTO, ART_VARIANT_PLAIN, ART_VARIANT_BATCHED, ART_VARIANT_FP64 = range(4)
-ART_LAYOUT_LAYER, ART_LAYOUT_POOL, ART_LAYOUT_POOL64 = 1, 2, 4
+ART_VARIANT_AUTO, ART_VARIANT_PLAIN, ART_VARIANT_BATCHED, ART_VARIANT_FP64, ART_VARIANT_SKIP = range(5)
+ART_LAYOUT_LAYER, ART_LAYOUT_POOL, ART_LAYOUT_POOL64, ART_LAYOUT_GROUP = 1, 2, 4, 8
 ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH = 1, 2
 
 # Every entry point declared in include/art.h.
@@ -74,7 +74,7 @@ def lib():
         "art_metrics_noalloc": ([P, i64, i32, P, i32, P, P, P, P], st),
         "art_run_ylt_backward": ([P, i64, P, P, i32, P, P, P, P, P], st),
         "art_get_device_status": ([P, P], st),
-        "art_get_footprint": ([P, P, P, P], st),
+        "art_get_footprint": ([P, P, P, P, P], st),
         "art_destroy_portfolio": ([P], None),
         "art_status_string": ([st], ctypes.c_char_p),
         "art_last_cuda_error": ([], ctypes.c_char_p),
@@ -262,9 +262,11 @@ def art_get_device_status(p, stream=None) -> int:
 
 
 def art_get_footprint(p):
-    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    _check(lib().art_get_footprint(_h(p), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "art_get_footprint")
-    return a.value, b.value, c.value
+    """Returns (layer, pool, pool64, group) bytes held on the device."""
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().art_get_footprint(_h(p), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "art_get_footprint")
+    return a.value, b.value, c.value, d.value
 
 
 def art_destroy_portfolio(p) -> None:

@@ -167,6 +167,100 @@ cudaError_t build_batched_meta(art_portfolio* p) {
     return upload_batched_terms(p);
 }
 
+// Layer groups for the bitmap-skip kernel: consecutive layers while the
+// group has at most 8 layers and the union of their ELTs at most 32.
+void form_groups(art_portfolio* p) {
+    p->group_elts.clear();
+    p->group_layers.clear();
+    std::vector<int32_t> uni, lay;
+    for (int32_t j = 0; j < p->n_layers; ++j) {
+        std::vector<int32_t> merged = uni;
+        for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
+            if (std::find(merged.begin(), merged.end(), p->lids[c]) == merged.end()) merged.push_back(p->lids[c]);
+        if (!lay.empty() && ((int)lay.size() >= kMaxGroupLayers || (int)merged.size() > kMaxLayerElts)) {
+            p->group_elts.push_back(uni);
+            p->group_layers.push_back(lay);
+            uni.clear();
+            lay.clear();
+            merged.clear();
+            for (int c = p->loff[j]; c < p->loff[j + 1]; ++c) merged.push_back(p->lids[c]);
+        }
+        uni = merged;
+        lay.push_back(j);
+    }
+    if (!lay.empty()) {
+        p->group_elts.push_back(uni);
+        p->group_layers.push_back(lay);
+    }
+}
+
+// Terms of every group as its kernel reads them (kernel parameters).
+void refresh_group_terms(art_portfolio* p) {
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        GroupArgs& g = p->groups[gi];
+        const std::vector<int32_t>& el = p->group_elts[gi];
+        const std::vector<int32_t>& ly = p->group_layers[gi];
+        for (int k = 0; k < kMaxLayerElts; ++k) {
+            const bool real = k < (int)el.size();
+            g.m[k] = real ? p->mult[el[k]] : 1.0f;
+            g.d[k] = real ? p->ded[el[k]] : 0.0f;
+            g.lim[k] = real ? p->lim[el[k]] : std::numeric_limits<float>::infinity();
+        }
+        g.n_layers = (int32_t)ly.size();
+        for (int s = 0; s < kMaxGroupLayers; ++s) {
+            const bool real = s < (int)ly.size();
+            const int32_t j = real ? ly[s] : 0;
+            uint32_t mem = 0;
+            if (real)
+                for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
+                    mem |= 1u << (std::find(el.begin(), el.end(), p->lids[c]) - el.begin());
+            g.member[s] = mem;
+            g.occ_ret[s] = real ? p->occ_ret[j] : 0.0f;
+            g.occ_lim[s] = real ? p->occ_lim[j] : 0.0f;
+            g.agg_ret[s] = real ? p->agg_ret[j] : 0.0;
+            g.agg_lim[s] = real ? p->agg_lim[j] : 0.0;
+            g.layer[s] = real ? j : 0;
+        }
+    }
+}
+
+cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t stream) {
+    form_groups(p);
+    const size_t ng = p->group_elts.size();
+    p->groups.assign(ng, GroupArgs{});
+    p->group_np.assign(ng, 0);
+    p->group_tab.assign(ng, nullptr);
+    p->group_bitmap.assign(ng, nullptr);
+    int32_t* d_el = nullptr;
+    cudaError_t e = cudaMalloc(&d_el, sizeof(int32_t) * kMaxLayerElts * ng);
+    if (e) return e;
+    for (size_t gi = 0; gi < ng && !e; ++gi) {
+        const std::vector<int32_t>& el = p->group_elts[gi];
+        const int np = pad_np((int)el.size());
+        p->group_np[gi] = np;
+        const size_t tb = sizeof(float) * (size_t)p->catalogue * np;
+        const size_t bb = sizeof(uint32_t) * (((size_t)p->catalogue + 31) / 32);
+        if ((e = cudaMalloc(&p->group_tab[gi], tb))) break;
+        if ((e = cudaMalloc(&p->group_bitmap[gi], bb))) break;
+        p->group_bytes += (int64_t)(tb + bb);
+        if ((e = cudaMemcpyAsync(d_el + gi * kMaxLayerElts, el.data(), sizeof(int32_t) * el.size(),
+                                 cudaMemcpyHostToDevice, stream)))
+            break;
+        if ((e = build_layer_table(losses, p->catalogue, d_el + gi * kMaxLayerElts, (int32_t)el.size(), np,
+                                   p->group_tab[gi], stream)))
+            break;
+        if ((e = build_group_bitmap(p->group_tab[gi], p->catalogue, np, p->group_bitmap[gi], stream))) break;
+        p->groups[gi].table = p->group_tab[gi];
+        p->groups[gi].bitmap = p->group_bitmap[gi];
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(stream);
+    cudaFree(d_el);
+    if (e) return e;
+    if (e2) return e2;
+    refresh_group_terms(p);
+    return cudaSuccess;
+}
+
 size_t batched_smem(const art_portfolio* p, bool fp64) {
     return 3 * (size_t)p->pool_np * (fp64 ? 8 : 4) + (size_t)p->n_tiles * p->pool_np * 32;
 }
@@ -175,6 +269,8 @@ void free_portfolio(art_portfolio* p) {
     if (!p) return;
     cudaDeviceSynchronize();
     for (float* t : p->layer_tab) cudaFree(t);
+    for (float* t : p->group_tab) cudaFree(t);
+    for (uint32_t* b : p->group_bitmap) cudaFree(b);
     cudaFree(p->pool);
     cudaFree(p->pool64);
     cudaFree(p->d_elt_terms);
@@ -201,12 +297,17 @@ void free_portfolio(art_portfolio* p) {
 
 int resolve_variant(const art_portfolio* p) {
     if (p->variant != ART_VARIANT_AUTO) return p->variant;
+    // few groups: the YET is streamed once per group, each event row read
+    // only when its bit is set; many groups: one pass over a pool table
+    if (!p->groups.empty() && p->groups.size() <= 2) return ART_VARIANT_SKIP;
     if (p->pool && p->n_tiles > 0) return ART_VARIANT_BATCHED;
+    if (!p->groups.empty()) return ART_VARIANT_SKIP;
     return ART_VARIANT_PLAIN;
 }
 
 bool variant_available(const art_portfolio* p, int v) {
     if (v == ART_VARIANT_PLAIN) return (p->layouts & ART_LAYOUT_LAYER) != 0;
+    if (v == ART_VARIANT_SKIP) return !p->groups.empty();
     if (v == ART_VARIANT_BATCHED) return p->pool != nullptr && p->n_tiles > 0 && batched_smem(p, false) <= 200 * 1024;
     if (v == ART_VARIANT_FP64) return p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024;
     return false;
@@ -223,6 +324,7 @@ art_status validate_yet(int64_t n_trials, const int32_t* ids, const int64_t* off
 cudaError_t run_forward(art_portfolio* p, int variant, const YetArgs& y, double* ylt, uint8_t* branch,
                         cudaStream_t s) {
     if (variant == ART_VARIANT_PLAIN) return launch_plain(p, y, ylt, branch, s);
+    if (variant == ART_VARIANT_SKIP) return launch_skip(p, y, ylt, branch, s);
     return launch_batched(p, y, ylt, branch, variant == ART_VARIANT_FP64, s);
 }
 
@@ -281,12 +383,12 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
     }
     p->loff.assign(layer_elt_off_host, layer_elt_off_host + n_layers + 1);
     p->lids.assign(layer_elt_ids_host, layer_elt_ids_host + p->loff.back());
-    p->layouts = (opt && opt->layouts) ? opt->layouts : (ART_LAYOUT_LAYER | ART_LAYOUT_POOL);
+    p->layouts = (opt && opt->layouts) ? opt->layouts : (ART_LAYOUT_LAYER | ART_LAYOUT_POOL | ART_LAYOUT_GROUP);
     p->variant = opt ? opt->variant : ART_VARIANT_AUTO;
     p->flags = opt ? opt->flags : 0;
     p->trial_tile = opt ? opt->trial_tile : 0;
     p->cta_threads = opt ? opt->cta_threads : 0;
-    if (p->variant < ART_VARIANT_AUTO || p->variant > ART_VARIANT_FP64 || p->trial_tile < 0 ||
+    if (p->variant < ART_VARIANT_AUTO || p->variant > ART_VARIANT_SKIP || p->trial_tile < 0 ||
         (p->cta_threads != 0 && (p->cta_threads % 32 != 0 || p->cta_threads > 1024))) {
         delete p;
         return ART_EINVAL;
@@ -348,6 +450,7 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
                 break;
             if ((e = build_batched_meta(p))) break;
         }
+        if ((p->layouts & ART_LAYOUT_GROUP) && (e = build_groups(p, elt_losses_dev, stream))) break;
         if (p->flags & ART_FLAG_L2_PERSIST) {
             int persist_max = 0;
             cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, p->device);
@@ -387,6 +490,7 @@ art_status art_update_terms(art_portfolio* p, const float* elt_mult_host, const 
         const cudaError_t e = upload_batched_terms(p);
         if (e) return fail(e);
     }
+    refresh_group_terms(p);
     if (p->graph_exec) {  // the plain variant bakes terms into launch parameters
         cudaGraphExecDestroy(p->graph_exec);
         p->graph_exec = nullptr;
@@ -407,7 +511,7 @@ art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* el
 }
 
 art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads) {
-    if (!p || variant < ART_VARIANT_AUTO || variant > ART_VARIANT_FP64 || trial_tile < 0 || cta_threads < 0 ||
+    if (!p || variant < ART_VARIANT_AUTO || variant > ART_VARIANT_SKIP || trial_tile < 0 || cta_threads < 0 ||
         cta_threads % 32 != 0 || cta_threads > 1024)
         return ART_EINVAL;
     if (variant != ART_VARIANT_AUTO && !variant_available(p, variant)) return ART_EUNSUPPORTED;
@@ -615,8 +719,10 @@ art_status art_get_device_status(art_portfolio* p, cudaStream_t stream) {
     return ART_OK;
 }
 
-art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes, int64_t* pool64_bytes) {
+art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes, int64_t* pool64_bytes,
+                             int64_t* group_bytes) {
     if (!p) return ART_EINVAL;
+    if (group_bytes) *group_bytes = p->group_bytes;
     if (layer_bytes) *layer_bytes = p->layer_bytes;
     if (pool_bytes) *pool_bytes = p->pool_bytes;
     if (pool64_bytes) *pool64_bytes = p->pool64_bytes;

@@ -100,6 +100,23 @@ struct BatchedArgs {
     int32_t slots;
 };
 
+// A layer group for the bitmap-skip kernel: up to 8 layers whose ELTs number
+// at most 32 together, with one event-major table over the union of those
+// ELTs and an occupancy bitmap over the catalogue. Passed by value.
+constexpr int kMaxGroupLayers = 8;
+struct GroupArgs {
+    const float* table;       // [C][np] FP32 over the group's ELTs (union order)
+    const uint32_t* bitmap;   // [ceil(C / 32)]: bit i set if row i is not all zero
+    float m[kMaxLayerElts];   // terms of the group's ELTs (padding: 1, 0, inf)
+    float d[kMaxLayerElts];
+    float lim[kMaxLayerElts];
+    uint32_t member[kMaxGroupLayers];  // bit k: the group's ELT k belongs to the layer
+    float occ_ret[kMaxGroupLayers], occ_lim[kMaxGroupLayers];
+    double agg_ret[kMaxGroupLayers], agg_lim[kMaxGroupLayers];
+    int32_t layer[kMaxGroupLayers];
+    int32_t n_layers;
+};
+
 }  // namespace art
 
 // The opaque portfolio.
@@ -125,6 +142,15 @@ struct art_portfolio {
     double* pool64 = nullptr;
     int32_t pool_np = 0;
     int64_t pool_bytes = 0, pool64_bytes = 0;
+
+    // ART_LAYOUT_GROUP: layer groups with union tables and occupancy bitmaps
+    std::vector<art::GroupArgs> groups;
+    std::vector<int32_t> group_np;
+    std::vector<std::vector<int32_t>> group_elts;   // union ELT ids per group
+    std::vector<std::vector<int32_t>> group_layers; // layer ids per group
+    std::vector<float*> group_tab;
+    std::vector<uint32_t*> group_bitmap;
+    int64_t group_bytes = 0;
 
     // batched metadata (device)
     float* d_elt_terms = nullptr;      // [3][pool_np]
@@ -158,6 +184,8 @@ namespace art {
 
 // Host-side launchers (each returns a CUDA error code).
 cudaError_t launch_plain(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np, uint32_t* bitmap, cudaStream_t s);
 cudaError_t launch_batched(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, bool fp64,
                            cudaStream_t s);
 cudaError_t launch_adjoint(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,
