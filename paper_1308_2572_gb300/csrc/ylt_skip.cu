@@ -9,18 +9,24 @@
 // zero to every layer of the group (absent losses are 0 and F_e(0) = 0 since
 // D_e >= 0), so it is skipped without reading its row.
 //
-// Mapping: one warp per trial. The warp streams the trial's ids (coalesced,
-// evict-first), tests each id's bit (the bitmap, C/8 bytes, stays in L1/L2),
-// and appends the ids whose bit is set to a per-warp queue in shared memory.
-// Each time 32 are queued, every lane takes one and evaluates it fully: one
-// row read (np * 4 contiguous bytes, not allocated in L1 so the bitmap stays
-// there), F_e per ELT in FP32, the per-layer ELT sums in the group's ELT
-// order, the occurrence terms, and the occurrence-net loss added to the
-// lane's per-layer aggregate. That aggregate is a compensated FP32 pair
-// (Knuth's two-sum: the pair holds the exact sum up to a second-order term
-// of order n u^2), folded into FP64 once per trial, so the FP64 pipe is used
-// per trial rather than per event; the warp then reduces the lanes' FP64
-// partials and applies the aggregate terms in FP64.
+// Mapping: a persistent grid of one CTA per SM. Each CTA copies the bitmap
+// into shared memory (as much of it as fits next to the queues: 1.79M events'
+// bits; the rest is read from global memory), so the per-event test is a
+// shared-memory load instead of a random L1 gather. Each warp walks a strided
+// sequence of trials as a stream of chunks of 32 * E events: the next chunk's
+// ids (from the same trial or the next one) are requested before the current
+// chunk is processed, hiding the DRAM latency of the id stream. The ids whose
+// bit is set go to a per-warp queue in shared memory; each time 32 are queued,
+// every lane takes one and evaluates it fully: one row read (np * 4
+// contiguous bytes in 256-bit loads, not allocated in L1), F_e per ELT in
+// FP32, the per-layer ELT sums in the group's ELT order, the occurrence
+// terms, and the occurrence-net loss added to the lane's per-layer aggregate.
+// That aggregate is a compensated FP32 pair (Knuth's two-sum: the pair holds
+// the exact sum up to a second-order term of order n u^2), folded into FP64
+// once per trial, so the FP64 pipe works per trial rather than per event; the
+// warp then reduces the lanes' FP64 partials and applies the aggregate terms
+// in FP64.
+#include <algorithm>
 #include <limits>
 
 #include "art_internal.cuh"
@@ -29,12 +35,16 @@ namespace art {
 
 namespace {
 
-constexpr int kSkipThreads = 256;
-constexpr int kSkipWarps = kSkipThreads / 32;
+#ifndef ART_SKIP_THREADS
+#define ART_SKIP_THREADS 1024
+#endif
 #ifndef ART_SKIP_IDS_PER_LANE
 #define ART_SKIP_IDS_PER_LANE 8
 #endif
+constexpr int kSkipThreads = ART_SKIP_THREADS;
+constexpr int kSkipWarps = kSkipThreads / 32;
 constexpr int kSkipIdsPerLane = ART_SKIP_IDS_PER_LANE;
+constexpr int kQueue = 64;  // per-warp queue entries
 
 __device__ __forceinline__ uint32_t ld_bitmap(const uint32_t* p) {
     uint32_t v;
@@ -42,12 +52,17 @@ __device__ __forceinline__ uint32_t ld_bitmap(const uint32_t* p) {
     return v;
 }
 
-__device__ __forceinline__ float4 ld_row_no_l1(const float4* p) {
-    float4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+// 32 contiguous bytes of a row in one 256-bit load (sm_100 and later).
+__device__ __forceinline__ void ld_row8(const float* p, float* v) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
         : "l"(p));
-    return v;
+}
+
+__device__ __forceinline__ void ld_row4(const float* p, float* v) {
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+        : "l"(p));
 }
 
 // s + e += v without losing the rounding error of the FP32 add (two-sum).
@@ -61,138 +76,209 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
 
 template <int NP, int LT>
 __device__ __forceinline__ void eval_event(const GroupArgs& g, int32_t id, float (&hi)[LT], float (&lo)[LT]) {
-    const float4* row = reinterpret_cast<const float4*>(g.table) + (size_t)id * (NP / 4);
+    const float* row = g.table + (size_t)id * NP;
     float f[NP];
+    if constexpr (NP % 8 == 0) {
 #pragma unroll
-    for (int q = 0; q < NP / 4; ++q) {
-        const float4 v = ld_row_no_l1(row + q);
-        f[4 * q + 0] = fin_f32(v.x, g.m[4 * q + 0], g.d[4 * q + 0], g.lim[4 * q + 0]);
-        f[4 * q + 1] = fin_f32(v.y, g.m[4 * q + 1], g.d[4 * q + 1], g.lim[4 * q + 1]);
-        f[4 * q + 2] = fin_f32(v.z, g.m[4 * q + 2], g.d[4 * q + 2], g.lim[4 * q + 2]);
-        f[4 * q + 3] = fin_f32(v.w, g.m[4 * q + 3], g.d[4 * q + 3], g.lim[4 * q + 3]);
+        for (int q = 0; q < NP / 8; ++q) ld_row8(row + 8 * q, f + 8 * q);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) ld_row4(row + 4 * q, f + 4 * q);
     }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) f[k] = fin_f32(f[k], g.m[k], g.d[k], g.lim[k]);
 #pragma unroll
     for (int j = 0; j < LT; ++j) {
         float x = 0.0f;
 #pragma unroll
-        for (int k = 0; k < NP; ++k)
-            if (g.member[j] & (1u << k)) x += f[k];
+        for (int k = 0; k < NP; ++k) {
+            // a one-layer group covers every real column; padding columns add 0
+            if (LT == 1 || (g.member[j] & (1u << k))) x += f[k];
+        }
         const float o = xl_f32(x, g.occ_ret[j], g.occ_lim[j]);
         if (o > 0.0f) two_sum_acc(hi[j], lo[j], o);
     }
 }
 
-template <int NP, int LT>
-__global__ void __launch_bounds__(kSkipThreads) ylt_skip_kernel(const GroupArgs g, const YetArgs y,
-                                                               double* __restrict__ ylt,
-                                                               uint8_t* __restrict__ branch,
-                                                               int* __restrict__ flags) {
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
+    return __ldcs(reinterpret_cast<const int4*>(p));
+}
+
+// Position of id slot k of a lane within a chunk of 32 * E events starting at
+// trial offset c0. Scalar layout: slot k is event c0 + 32 k + lane (each warp
+// load is 128 contiguous bytes). Vector layout (trial start and length
+// multiples of 4): slots 4h..4h+3 are events c0 + 128 h + 4 lane + 0..3, one
+// 16-byte load.
+template <bool VEC>
+__device__ __forceinline__ int32_t slot_pos(int32_t c0, int k, int lane) {
+    if constexpr (VEC) return c0 + 128 * (k >> 2) + 4 * lane + (k & 3);
+    else return c0 + 32 * k + lane;
+}
+
+template <int E, bool VEC>
+__device__ __forceinline__ void load_chunk(const int32_t* __restrict__ ids, int32_t c0, int32_t n, int lane,
+                                           int32_t (&v)[E]) {
+    if constexpr (VEC) {
+#pragma unroll
+        for (int h = 0; h < E / 4; ++h) {
+            const int32_t d = c0 + 128 * h + 4 * lane;
+            int4 w = make_int4(-1, -1, -1, -1);
+            if (d < n) w = ld_stream4(ids + d);  // n and d are multiples of 4
+            v[4 * h + 0] = w.x;
+            v[4 * h + 1] = w.y;
+            v[4 * h + 2] = w.z;
+            v[4 * h + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int32_t d = c0 + 32 * k + lane;
+            v[k] = d < n ? ld_stream(ids + d) : -1;
+        }
+    }
+}
+
+template <int NP, int LT, bool VEC>
+__global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupArgs g, const YetArgs y,
+                                                                  const int32_t smem_words,
+                                                                  double* __restrict__ ylt,
+                                                                  uint8_t* __restrict__ branch,
+                                                                  int* __restrict__ flags) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int E = kSkipIdsPerLane;  // ids per lane per chunk: a chunk is 32 * E events
-    __shared__ int32_t s_queue[kSkipWarps][64];
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    int32_t* s_queue = reinterpret_cast<int32_t*>(s_dyn);  // [kSkipWarps][kQueue]
+    uint32_t* s_bits = s_dyn + kSkipWarps * kQueue;          // the first smem_words words of the bitmap
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(g.bitmap);
+        uint4* dst = reinterpret_cast<uint4*>(s_bits);
+        for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= y.n_trials) return;  // whole warp
-    int32_t* q = s_queue[wib];
+    int32_t* q = s_queue + wib * kQueue;
     const unsigned lt_mask = (1u << lane) - 1u;
-    int64_t b, e;
-    bool bad_off;
-    trial_range(y, t, b, e, bad_off);
-    float hi[LT], lo[LT];
-#pragma unroll
-    for (int j = 0; j < LT; ++j) {
-        hi[j] = 0.0f;
-        lo[j] = 0.0f;
+    const int64_t n_warps = (int64_t)gridDim.x * kSkipWarps;
+    bool bad_id = false, bad_off_seen = false;
+
+    int64_t t = (int64_t)blockIdx.x * kSkipWarps + wib;
+    const int32_t* tid = y.ids;  // ids of the current trial
+    int32_t n = 0;               // its length
+    int32_t pre[E];
+    if (t < y.n_trials) {
+        int64_t b, e;
+        bool bo;
+        trial_range(y, t, b, e, bo);
+        bad_off_seen |= bo;
+        tid = y.ids + b;
+        n = (int32_t)(e - b);
+        load_chunk<E, VEC>(tid, 0, n, lane, pre);
     }
-    bool bad_id = false;
-    int qn = 0;  // warp-uniform queue length, < 32 between steps
-    // the chunk's ids are all requested before any is used, and the next
-    // chunk's ids are requested before this chunk's rows
-    int32_t nid[E];
+    while (t < y.n_trials) {
+        const int64_t tn = t + n_warps;
+        const int32_t* tidn = y.ids;
+        int32_t nn = 0;
+        if (tn < y.n_trials) {
+            int64_t bn, en;
+            bool bo;
+            trial_range(y, tn, bn, en, bo);
+            bad_off_seen |= bo;
+            tidn = y.ids + bn;
+            nn = (int32_t)(en - bn);
+        }
+        float hi[LT], lo[LT];
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const int64_t d = b + k * 32 + lane;
-        nid[k] = d < e ? ld_stream(y.ids + d) : -1;
-    }
-    for (int64_t d0 = b; d0 < e; d0 += 32 * E) {
-        int32_t id[E];
+        for (int j = 0; j < LT; ++j) {
+            hi[j] = 0.0f;
+            lo[j] = 0.0f;
+        }
+        int qn = 0;  // warp-uniform queue length, < 32 between steps
+        if (n == 0 && tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
+        for (int32_t c0 = 0; c0 < n; c0 += 32 * E) {
+            int32_t id[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) id[k] = nid[k];
-        const int64_t d1 = d0 + 32 * E;
-        if (d1 < e) {
+            for (int k = 0; k < E; ++k) id[k] = pre[k];
+            // request the next chunk (this trial's, or the next trial's first) now
+            if (c0 + 32 * E < n) load_chunk<E, VEC>(tid, c0 + 32 * E, n, lane, pre);
+            else if (tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
+            bool nz[E];
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const int64_t d = d1 + k * 32 + lane;
-                nid[k] = d < e ? ld_stream(y.ids + d) : -1;
+                const bool live = slot_pos<VEC>(c0, k, lane) < n;
+                const bool ok = live && (unsigned)id[k] < (unsigned)y.catalogue;
+                if (live && !ok) bad_id = true;
+                const int32_t wi = id[k] >> 5;
+                uint32_t w = 0u;
+                if (ok) w = wi < smem_words ? s_bits[wi] : ld_bitmap(g.bitmap + wi);
+                nz[k] = (w >> (id[k] & 31)) & 1u;
+            }
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const unsigned m = __ballot_sync(FULL, nz[k]);
+                if (nz[k]) q[qn + __popc(m & lt_mask)] = id[k];
+                qn += __popc(m);
+                if (qn >= 32) {
+                    __syncwarp();
+                    const int32_t mine = q[lane];
+                    const int32_t carry = q[32 + lane];
+                    __syncwarp();
+                    q[lane] = carry;  // entries 32 .. qn-1 move to the front
+                    qn -= 32;
+                    eval_event<NP, LT>(g, mine, hi, lo);
+                    __syncwarp();
+                }
             }
         }
-        uint32_t w[E];
+        __syncwarp();
+        if (lane < qn) eval_event<NP, LT>(g, q[lane], hi, lo);
+        __syncwarp();
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const bool live = d0 + k * 32 + lane < e;
-            const bool ok = live && (unsigned)id[k] < (unsigned)y.catalogue;
-            if (live && !ok) bad_id = true;
-            w[k] = ok ? ld_bitmap(g.bitmap + (id[k] >> 5)) : 0u;
-        }
+        for (int j = 0; j < LT; ++j) {
+            double sum = (double)hi[j] + (double)lo[j];
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const bool nz = (w[k] >> (id[k] & 31)) & 1u;
-            const unsigned m = __ballot_sync(FULL, nz);
-            if (nz) q[qn + __popc(m & lt_mask)] = id[k];
-            qn += __popc(m);
-            if (qn >= 32) {
-                __syncwarp();
-                const int32_t mine = q[lane];
-                const int32_t carry = q[32 + lane];
-                __syncwarp();
-                q[lane] = carry;  // entries 32 .. qn-1 move to the front
-                qn -= 32;
-                eval_event<NP, LT>(g, mine, hi, lo);
-                __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+            if (lane == 0 && j < g.n_layers) {
+                const size_t wi = (size_t)g.layer[j] * (size_t)y.n_trials + (size_t)t;
+                ylt[wi] = xl_f64(sum, g.agg_ret[j], g.agg_lim[j]);
+                if (branch) branch[wi] = agg_branch(sum, g.agg_ret[j], g.agg_lim[j]);
             }
         }
+        t = tn;
+        tid = tidn;
+        n = nn;
     }
-    __syncwarp();
-    if (lane < qn) eval_event<NP, LT>(g, q[lane], hi, lo);
     if (bad_id) atomicOr(flags + kFlagIdRange, 1);
-#pragma unroll
-    for (int j = 0; j < LT; ++j) {
-        double s = (double)hi[j] + (double)lo[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-        if (lane == 0 && j < g.n_layers) {
-            const size_t wi = (size_t)g.layer[j] * (size_t)y.n_trials + (size_t)t;
-            ylt[wi] = xl_f64(s, g.agg_ret[j], g.agg_lim[j]);
-            if (branch) branch[wi] = agg_branch(s, g.agg_ret[j], g.agg_lim[j]);
-        }
-    }
-    if (lane == 0 && bad_off) atomicOr(flags + kFlagBadOffsets, 1);
+    if (lane == 0 && bad_off_seen) atomicOr(flags + kFlagBadOffsets, 1);
 }
 
 template <int NP, int LT>
-cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, double* ylt, uint8_t* branch, int* flags,
-                         cudaStream_t s) {
-    auto kern = ylt_skip_kernel<NP, LT>;
-    static bool configured = false;
-    if (!configured) {
-        // shared memory for the queues of six resident CTAs, the rest L1
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 10);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    const int64_t blocks = (y.n_trials + kSkipWarps - 1) / kSkipWarps;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, kSkipThreads, 0, s>>>(g, y, ylt, branch, flags);
+cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, double* ylt,
+                         uint8_t* branch, int* flags, cudaStream_t s) {
+    // 16-byte id loads when every trial starts and ends on a multiple of 4 ids
+    const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
+    auto kern = vec ? ylt_skip_kernel<NP, LT, true> : ylt_skip_kernel<NP, LT, false>;
+    int dev = 0, max_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    const int queue_bytes = kSkipWarps * kQueue * 4;
+    const int words = (int)(((int64_t)catalogue + 31) / 32);
+    // whole 16-byte groups of words that fit next to the queues
+    const int smem_words = std::max(0, std::min(words, (max_optin - queue_bytes) / 4) & ~3);
+    const int smem = queue_bytes + smem_words * 4;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    const int64_t grid = std::min<int64_t>(num_sms, (y.n_trials + kSkipWarps - 1) / kSkipWarps);
+    kern<<<(unsigned)std::max<int64_t>(1, grid), kSkipThreads, smem, s>>>(g, y, smem_words, ylt, branch, flags);
     return cudaGetLastError();
 }
 
 template <int NP>
-cudaError_t launch_lt(const GroupArgs& g, const YetArgs& y, double* ylt, uint8_t* branch, int* flags,
-                      cudaStream_t s) {
-    if (g.n_layers <= 1) return launch_group<NP, 1>(g, y, ylt, branch, flags, s);
-    if (g.n_layers <= 2) return launch_group<NP, 2>(g, y, ylt, branch, flags, s);
-    if (g.n_layers <= 4) return launch_group<NP, 4>(g, y, ylt, branch, flags, s);
-    return launch_group<NP, 8>(g, y, ylt, branch, flags, s);
+cudaError_t launch_lt(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, double* ylt,
+                      uint8_t* branch, int* flags, cudaStream_t s) {
+    if (g.n_layers <= 1) return launch_group<NP, 1>(g, y, num_sms, catalogue, ylt, branch, flags, s);
+    if (g.n_layers <= 2) return launch_group<NP, 2>(g, y, num_sms, catalogue, ylt, branch, flags, s);
+    if (g.n_layers <= 4) return launch_group<NP, 4>(g, y, num_sms, catalogue, ylt, branch, flags, s);
+    return launch_group<NP, 8>(g, y, num_sms, catalogue, ylt, branch, flags, s);
 }
 
 // Bitmap of a group table: bit i set when row i has any non-zero entry.
@@ -219,11 +305,11 @@ cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t
         const GroupArgs& g = p->groups[gi];
         cudaError_t err;
         switch (p->group_np[gi]) {
-            case 4: err = launch_lt<4>(g, y, ylt, branch, p->d_flags, s); break;
-            case 8: err = launch_lt<8>(g, y, ylt, branch, p->d_flags, s); break;
-            case 16: err = launch_lt<16>(g, y, ylt, branch, p->d_flags, s); break;
-            case 24: err = launch_lt<24>(g, y, ylt, branch, p->d_flags, s); break;
-            case 32: err = launch_lt<32>(g, y, ylt, branch, p->d_flags, s); break;
+            case 4: err = launch_lt<4>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
+            case 8: err = launch_lt<8>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
+            case 16: err = launch_lt<16>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
+            case 24: err = launch_lt<24>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
+            case 32: err = launch_lt<32>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
             default: err = cudaErrorInvalidValue;
         }
         if (err != cudaSuccess) return err;
