@@ -1,0 +1,166 @@
+"""GPU parity for the adjoint (art_metrics_backward + art_run_ylt_backward)
+and the torch.autograd.Function around it.
+
+Workload: the 8-layer, 16-ELT portfolio over the paper-scale YET, first
+10,000 trials. The objective is sum_j (EL_j + TVaR_0.99,j). Checked against
+the FP64 oracle's analytic gradient (weights built here from the oracle's
+own YLT) and against central differences of the GPU forward.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1308_2572_gb300 import art, workloads
+from paper_1308_2572_gb300.autograd import layer_metrics
+
+from gpu_util import device_yet
+
+pytestmark = pytest.mark.gpu
+
+N_TRIALS = 10_000
+PROB = 0.99
+
+
+@pytest.fixture(scope="module")
+def c3():
+    w = workloads.make("c3", n_trials=N_TRIALS)
+    p = art.portfolio_from_workload(w)
+    yet = device_yet(w)
+    yield w, p, yet
+    p.close()
+
+
+def _oracle_weights(y_ref, k):
+    """dObjective/dY for sum_j (mean_j + TVaR_j) from the oracle's YLT: 1/N,
+    plus 1/k above the k-th largest, ties at it sharing the remainder."""
+    L, N = y_ref.shape
+    g = np.full((L, N), 1.0 / N)
+    for j in range(L):
+        s = np.sort(y_ref[j])[::-1]
+        pml = s[k - 1]
+        gt = y_ref[j] > pml
+        eq = y_ref[j] == pml
+        g[j, gt] += 1.0 / k
+        g[j, eq] += (k - gt.sum()) / (k * eq.sum())
+    return g
+
+
+def _gpu_grad(p, yet, L, n_elt):
+    ids, off, K, T = yet
+    ylt = torch.empty((L, T), dtype=torch.float64, device="cuda")
+    br = torch.empty((L, T), dtype=torch.uint8, device="cuda")
+    art.art_set_variant(p, art.ART_VARIANT_PLAIN)
+    art.art_run_ylt(p, T, ids, off, K, ylt, br)
+    mean = torch.empty(L, dtype=torch.float64, device="cuda")
+    pml = torch.empty((L, 1), dtype=torch.float64, device="cuda")
+    tvar = torch.empty((L, 1), dtype=torch.float64, device="cuda")
+    art.art_metrics(ylt, T, L, [PROB], mean, pml, tvar)
+    gy = torch.empty_like(ylt)
+    ones = torch.ones(L, dtype=torch.float64, device="cuda")
+    art.art_metrics_backward(ylt, T, L, [PROB], pml, ones, ones.reshape(L, 1).contiguous(), gy)
+    gt = torch.empty((L, 4), dtype=torch.float64, device="cuda")
+    gm = torch.empty(n_elt, dtype=torch.float64, device="cuda")
+    art.art_run_ylt_backward(p, T, ids, off, K, br, gy, gt, gm)
+    torch.cuda.synchronize()
+    return ylt.cpu().numpy(), br.cpu().numpy(), gy.cpu().numpy(), gt.cpu().numpy(), gm.cpu().numpy(), mean, tvar
+
+
+def test_branch_codes_match_oracle_aggregate(c3):
+    w, p, yet = c3
+    L = w.portfolio.n_layers
+    ylt, br, *_ = _gpu_grad(p, yet, L, w.portfolio.n_elt)
+    _, _, s = oracle.ylt(w.oracle_problem(), want_sum=True)
+    ar, al = w.portfolio.agg_ret[:, None], w.portfolio.agg_lim[:, None]
+    expect = np.where(s <= ar, 0, np.where(s - ar > al, 2, 1))
+    mism = br != expect
+    # a mismatch is only allowed where the FP64 aggregate sits within FP32
+    # rounding of a kink
+    near = (np.abs(s - ar) <= 1e-6 * s) | (np.abs(s - ar - al) <= 1e-6 * s)
+    assert not np.any(mism & ~near)
+    assert 0.05 < np.mean(expect == 1) < 0.95  # the portfolio exercises every branch
+    assert np.any(expect == 2) and np.any(expect == 0)
+
+
+def test_gradient_matches_oracle(c3):
+    w, p, yet = c3
+    L, E = w.portfolio.n_layers, w.portfolio.n_elt
+    k = oracle.tail_count(PROB, N_TRIALS)
+    _, _, _, gt, gm, _, _ = _gpu_grad(p, yet, L, E)
+    y_ref, gross, _ = oracle.ylt(w.oracle_problem())
+    g = _oracle_weights(y_ref, k)
+    ot, om, _, _ = oracle.grad(w.oracle_problem(), g)
+    np.testing.assert_allclose(gt, ot, rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(gm, om, rtol=1e-6, atol=1e-3)
+    assert np.all(gt[:, 2] <= 0) and np.all(gt[:, 0] <= 0)  # retentions lower the losses
+    assert np.all(gm >= 0)
+
+
+def test_gradient_matches_gpu_central_differences(c3):
+    """dObjective/dtheta against (Obj(theta + h) - Obj(theta - h)) / 2h of the
+    GPU forward, h = 1e-4 |theta| (the FP32-rounded step for FP32 terms)."""
+    w, p, yet = c3
+    L, E = w.portfolio.n_layers, w.portfolio.n_elt
+    _, _, _, gt, gm, _, _ = _gpu_grad(p, yet, L, E)
+    m0, d0, l0, t0 = art.art_get_terms(p)
+    ids, off, K, T = yet
+
+    def objective():
+        ylt = torch.empty((L, T), dtype=torch.float64, device="cuda")
+        art.art_run_ylt(p, T, ids, off, K, ylt)
+        mean = torch.empty(L, dtype=torch.float64, device="cuda")
+        pml = torch.empty((L, 1), dtype=torch.float64, device="cuda")
+        tvar = torch.empty((L, 1), dtype=torch.float64, device="cuda")
+        art.art_metrics(ylt, T, L, [PROB], mean, pml, tvar)
+        return float(mean.sum() + tvar.sum())
+
+    checked = 0
+    try:
+        for j in range(0, L, 3):
+            for c in range(4):
+                tp, tm = t0.copy(), t0.copy()
+                h = 1e-4 * abs(t0[j, c])
+                tp[j, c] += h
+                tm[j, c] -= h
+                art.art_update_terms(p, terms=tp)
+                _, _, _, tpr = art.art_get_terms(p)
+                fp = objective()
+                art.art_update_terms(p, terms=tm)
+                _, _, _, tmr = art.art_get_terms(p)
+                fm = objective()
+                fd = (fp - fm) / (tpr[j, c] - tmr[j, c])
+                assert fd == pytest.approx(gt[j, c], rel=2e-3, abs=1e-3 * max(1.0, abs(gt[j, c]))), (j, c)
+                checked += 1
+            art.art_update_terms(p, terms=t0)
+        for e in range(0, E, 5):
+            mp, mm = m0.copy(), m0.copy()
+            mp[e] *= 1 + 1e-4
+            mm[e] *= 1 - 1e-4
+            art.art_update_terms(p, elt_mult=mp)
+            mpr = art.art_get_terms(p)[0]
+            fp = objective()
+            art.art_update_terms(p, elt_mult=mm)
+            mmr = art.art_get_terms(p)[0]
+            fm = objective()
+            fd = (fp - fm) / (float(mpr[e]) - float(mmr[e]))
+            assert fd == pytest.approx(gm[e], rel=2e-3), e
+            checked += 1
+    finally:
+        art.art_update_terms(p, elt_mult=m0, terms=t0)
+    assert checked >= 12
+
+
+def test_autograd_function(c3):
+    w, p, yet = c3
+    L, E = w.portfolio.n_layers, w.portfolio.n_elt
+    art.art_set_variant(p, art.ART_VARIANT_PLAIN)
+    m0, _, _, t0 = art.art_get_terms(p)
+    params = [torch.tensor(t0[:, c], dtype=torch.float64, requires_grad=True) for c in range(4)]
+    mult = torch.tensor(m0.astype(np.float64), requires_grad=True)
+    mean, tvar = layer_metrics(p, yet, [PROB], *params, mult)
+    (mean.sum() + tvar.sum()).backward()
+    _, _, _, gt, gm, gmean, gtvar = _gpu_grad(p, yet, L, E)
+    np.testing.assert_allclose(mean.detach().numpy(), gmean.cpu().numpy(), rtol=0, atol=0)
+    for c in range(4):
+        np.testing.assert_allclose(params[c].grad.numpy(), gt[:, c], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(mult.grad.numpy(), gm, rtol=1e-12, atol=0)

@@ -232,3 +232,27 @@ def test_update_terms_and_rounding():
             assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"updated terms variant {v}")
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("name,n_sample", [("c2", 400), ("c4", 250)])
+def test_multilayer_workloads_sampled(name, n_sample):
+    """The batching (CSR, 64 layers over a 256-ELT pool) and precision
+    (128 layers over a 512-ELT pool) workloads at full size: every variant,
+    checked on sampled trials, and the invariant 0 <= Y <= AggL on all."""
+    w = workloads.make(name)
+    p = art.portfolio_from_workload(w, layouts=ALL_LAYOUTS)
+    try:
+        yet = device_yet(w)
+        T = w.yet.n_trials
+        rng = np.random.default_rng(1)
+        trials = np.unique(np.concatenate([[0, T - 1], rng.choice(T, n_sample, replace=False)]))
+        ref, gross, _ = oracle_sample(w, trials)
+        sel = torch.from_numpy(trials).cuda()
+        for v in VARIANTS:
+            ylt, _ = run_ylt(p, w, v, yet=yet)
+            assert_ylt_close(ylt[:, sel].cpu().numpy(), ref, gross, f"{name} variant {v}")
+            agg_lim = torch.from_numpy(w.portfolio.agg_lim).cuda()[:, None]
+            assert torch.all(ylt >= 0) and torch.all(ylt <= agg_lim)
+            del ylt
+    finally:
+        p.close()
