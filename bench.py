@@ -182,6 +182,14 @@ def algorithmic_bytes(w, variant: str):
             hbm += ids + C / 8 + nz.sum() * rowb * frac_touched
             l2 += ids + n_events * p_nz * 32 * -(-rowb // 32)
         return {"hbm": hbm + ylt, "l2": l2, "ids": ids, "ylt": ylt, "table": None}
+    if variant == "sparse":
+        # per event: the id, the CSR offsets (one sector) and 8 bytes per
+        # non-zero loss; the CSR (C + 1 offsets + entries) read once from DRAM
+        nnz_per_event = float((port.elt_losses != 0).sum(axis=0).mean())
+        nnz_total = float((port.elt_losses != 0).sum())
+        csr = 4 * (C + 1) + 8 * nnz_total
+        return {"hbm": ids + ylt + csr * (1.0 - np.exp(-n_events / C)),
+                "l2": ids + n_events * (32 + 8 * nnz_per_event), "ids": ids, "ylt": ylt, "table": csr}
     if variant == "plain":
         row = np.array([4 * pad(int(n)) for n in sizes])
         sectors = int(sum(32 * -(-r // 32) for r in row)) * n_events
@@ -260,7 +268,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64", "skip"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64", "skip", "sparse"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -289,7 +297,7 @@ def main():
     log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
-    layouts = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP
+    layouts = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE
                | (art.ART_LAYOUT_POOL64 if args.variant == "fp64" else 0))
     p = art.portfolio_from_workload(w, device=dev, layouts=layouts)
     ids = torch.from_numpy(yet.event_ids).to(dev)
@@ -302,14 +310,14 @@ def main():
     tvar = torch.empty((L, n_p), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64,
-            "skip": art.ART_VARIANT_SKIP}
+            "skip": art.ART_VARIANT_SKIP, "sparse": art.ART_VARIANT_SPARSE}
 
     def step():
         art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
         art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
 
     # variant choice: time each candidate forward (untimed for the result)
-    cands = [args.variant] if args.variant != "auto" else ["plain", "batched", "skip"]
+    cands = [args.variant] if args.variant != "auto" else ["plain", "batched", "skip", "sparse"]
     fwd_ms = {}
     for v in cands:
         art.art_set_variant(p, vmap[v])
@@ -364,12 +372,25 @@ def main():
     peak, peak_kind = measured_peaks()
     ab = algorithmic_bytes(w, variant)
     achieved = ab["hbm"] / (fwd_mean / 1e3) / 1e9
-    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_batched_fp64", "skip": "ylt_skip"}[variant]
+    # measured limits the driver's figures do not cover (libart probes)
+    probes = {}
+    if rank == 0:
+        probes = {"l2_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 64 << 20),
+                  "l2_gather64_gbs": art.art_probe(art.ART_PROBE_GATHER64, 64 << 20),
+                  "dram_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 8 << 30, 3),
+                  "stream_read_gbs": art.art_probe(art.ART_PROBE_STREAM, 8 << 30, 3),
+                  "fp64_add_gflops": art.art_probe(art.ART_PROBE_FP64ADD, 0, 3)}
+    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_batched_fp64", "skip": "ylt_skip",
+                   "sparse": "ylt_sparse"}[variant]
     traffic = recorded_traffic(kernel_name, args.config)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
             "kernel": kernel_name, "algorithmic_bytes_per_launch": ab["hbm"],
             "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": ab["l2"] / (fwd_mean / 1e3) / 1e9}
+    if probes:
+        roof["l2_gather_peak_gbs"] = probes["l2_gather32_gbs"]
+        roof["l2_frac"] = roof["l2_sector_gbs"] / probes["l2_gather32_gbs"]
+        roof["probes"] = probes
 
     # end to end: host buffers through the C ABI (ids H2D in chunks, YLT D2H),
     # then the metrics on a device copy of the YLT and their D2H

@@ -72,8 +72,10 @@ enum {
     ART_VARIANT_PLAIN = 1,    /* one launch per layer over a per-layer event-major table  */
     ART_VARIANT_BATCHED = 2,  /* one persistent launch over all layers (pool table)       */
     ART_VARIANT_FP64 = 3,     /* batched, with FP64 tables and FP64 per-event arithmetic  */
-    ART_VARIANT_SKIP = 4      /* one launch per layer group (<= 8 layers, <= 32 ELTs):
+    ART_VARIANT_SKIP = 4,     /* one launch per layer group (<= 8 layers, <= 32 ELTs):
                                  occupancy bitmap skips events whose losses are all zero  */
+    ART_VARIANT_SPARSE = 5    /* one persistent launch over all layers, reading an
+                                 event-major CSR of the non-zero losses (compressed ELTs) */
 };
 
 /* Layouts built by art_create_portfolio (bit mask). */
@@ -81,8 +83,10 @@ enum {
     ART_LAYOUT_LAYER = 1,     /* per layer: [C][n_pad] FP32, the layer's ELTs side by side */
     ART_LAYOUT_POOL = 2,      /* all ELTs:  [C][n_elt_pad] FP32, shared by every layer     */
     ART_LAYOUT_POOL64 = 4,    /* all ELTs:  [C][n_elt_pad] FP64 (precision study)          */
-    ART_LAYOUT_GROUP = 8      /* per layer group: [C][n_pad] FP32 over the group's ELTs
+    ART_LAYOUT_GROUP = 8,     /* per layer group: [C][n_pad] FP32 over the group's ELTs
                                  plus a C-bit occupancy bitmap                             */
+    ART_LAYOUT_SPARSE = 16    /* all ELTs: event-major CSR of the non-zero losses
+                                 (C + 1 offsets, 8 bytes per non-zero loss)                */
 };
 
 /* Flags. */
@@ -93,7 +97,7 @@ enum {
 };
 
 typedef struct {
-    int32_t layouts;          /* ART_LAYOUT_* mask; 0 means LAYER | POOL | GROUP               */
+    int32_t layouts;          /* ART_LAYOUT_* mask; 0 means LAYER | POOL | GROUP | SPARSE      */
     int32_t variant;          /* ART_VARIANT_*                                                */
     int32_t flags;            /* ART_FLAG_*                                                   */
     int32_t trial_tile;       /* batched: trials per work unit (0 = autotune / default)       */
@@ -286,7 +290,7 @@ ART_API art_status art_get_device_status(art_portfolio* p, cudaStream_t stream);
 
 /* Bytes of device memory the portfolio holds, per layout (NULL to skip). */
 ART_API art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes,
-                                     int64_t* pool64_bytes, int64_t* group_bytes);
+                                     int64_t* pool64_bytes, int64_t* group_bytes, int64_t* sparse_bytes);
 
 /* Free the portfolio (synchronises the device first). NULL is a no-op. */
 ART_API void art_destroy_portfolio(art_portfolio* p);
@@ -296,6 +300,27 @@ ART_API const char* art_status_string(art_status s);
 
 /* Text of the last CUDA error this thread saw inside the library. */
 ART_API const char* art_last_cuda_error(void);
+
+/* Probe kinds for art_probe. */
+enum {
+    ART_PROBE_STREAM = 0,     /* streaming read of a buffer: GB/s of buffer bytes            */
+    ART_PROBE_GATHER32 = 1,   /* random 32-byte sector reads: GB/s of sector bytes           */
+    ART_PROBE_GATHER64 = 2,   /* random 64-byte row reads (two sectors): GB/s of row bytes   */
+    ART_PROBE_GATHER4 = 3,    /* random 4-byte reads: GB/s of the 32-byte sectors touched    */
+    ART_PROBE_FP64ADD = 4     /* independent FP64 adds: GFLOP/s                             */
+};
+
+/*
+ * art_probe -- measure a limit the kernels run against (a measurement aid;
+ * the paper has no counterpart). The random-read probes are the roofline
+ * denominators of the table lookups of Section III: over a buffer below the
+ * L2 size they measure the L2 gather rate, over one far above it the DRAM
+ * gather rate. Allocates `bytes` (1 MiB .. 64 GiB; ignored for the FP64
+ * probe) on the current device, runs one warm-up and `reps` timed launches on
+ * the legacy default stream, writes the best rate to *result and frees the
+ * buffer. Synchronous. Errors: ART_EINVAL, ART_ENOMEM, ART_ECUDA.
+ */
+ART_API art_status art_probe(int32_t kind, int64_t bytes, int32_t reps, double* result);
 
 /* Library version, major * 10000 + minor * 100 + patch. */
 ART_API int32_t art_version(void);

@@ -18,15 +18,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libart.so")
 
 ART_OK, ART_EINVAL, ART_ENOMEM, ART_ECUDA, ART_EID_RANGE, ART_ETIMEOUT, ART_EUNSUPPORTED = range(7)
-ART_VARIANT_AUTO, ART_VARIANT_PLAIN, ART_VARIANT_BATCHED, ART_VARIANT_FP64, ART_VARIANT_SKIP = range(5)
-ART_LAYOUT_LAYER, ART_LAYOUT_POOL, ART_LAYOUT_POOL64, ART_LAYOUT_GROUP = 1, 2, 4, 8
+ART_VARIANT_AUTO, ART_VARIANT_PLAIN, ART_VARIANT_BATCHED, ART_VARIANT_FP64, ART_VARIANT_SKIP, ART_VARIANT_SPARSE = range(6)
+ART_LAYOUT_LAYER, ART_LAYOUT_POOL, ART_LAYOUT_POOL64, ART_LAYOUT_GROUP, ART_LAYOUT_SPARSE = 1, 2, 4, 8, 16
 ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH = 1, 2
 
 # Every entry point declared in include/art.h.
 EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set_variant", "art_run_ylt",
            "art_run_ylt_host", "art_metrics", "art_metrics_backward", "art_run_ylt_backward",
            "art_get_device_status", "art_get_footprint", "art_destroy_portfolio", "art_status_string",
-           "art_last_cuda_error", "art_version", "art_metrics_noalloc")
+           "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe")
 
 
 class LayerTerms(ctypes.Structure):
@@ -74,11 +74,12 @@ def lib():
         "art_metrics_noalloc": ([P, i64, i32, P, i32, P, P, P, P], st),
         "art_run_ylt_backward": ([P, i64, P, P, i32, P, P, P, P, P], st),
         "art_get_device_status": ([P, P], st),
-        "art_get_footprint": ([P, P, P, P, P], st),
+        "art_get_footprint": ([P, P, P, P, P, P], st),
         "art_destroy_portfolio": ([P], None),
         "art_status_string": ([st], ctypes.c_char_p),
         "art_last_cuda_error": ([], ctypes.c_char_p),
         "art_version": ([], i32),
+        "art_probe": ([i32, i64, i32, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -262,11 +263,10 @@ def art_get_device_status(p, stream=None) -> int:
 
 
 def art_get_footprint(p):
-    """Returns (layer, pool, pool64, group) bytes held on the device."""
-    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    _check(lib().art_get_footprint(_h(p), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
-           "art_get_footprint")
-    return a.value, b.value, c.value, d.value
+    """Returns (layer, pool, pool64, group, sparse) bytes held on the device."""
+    v = [ctypes.c_int64() for _ in range(5)]
+    _check(lib().art_get_footprint(_h(p), *[ctypes.byref(x) for x in v]), "art_get_footprint")
+    return tuple(x.value for x in v)
 
 
 def art_destroy_portfolio(p) -> None:
@@ -275,6 +275,16 @@ def art_destroy_portfolio(p) -> None:
 
 def art_status_string(status: int) -> str:
     return lib().art_status_string(int(status)).decode()
+
+
+ART_PROBE_STREAM, ART_PROBE_GATHER32, ART_PROBE_GATHER64, ART_PROBE_GATHER4, ART_PROBE_FP64ADD = range(5)
+
+
+def art_probe(kind: int, nbytes: int = 64 << 20, reps: int = 5) -> float:
+    """Measured rate (GB/s, or GFLOP/s for the FP64 probe); see include/art.h."""
+    out = ctypes.c_double()
+    _check(lib().art_probe(int(kind), int(nbytes), int(reps), ctypes.byref(out)), "art_probe")
+    return out.value
 
 
 def art_version() -> int:

@@ -280,6 +280,8 @@ void free_portfolio(art_portfolio* p) {
     cudaFree(p->d_occ);
     cudaFree(p->d_agg);
     cudaFree(p->d_work_counter);
+    cudaFree(p->sp_ptr);
+    cudaFree(p->sp_entries);
     cudaFree(p->d_flags);
     cudaFree(p->d_loff);
     cudaFree(p->d_lids);
@@ -300,6 +302,7 @@ int resolve_variant(const art_portfolio* p) {
     // few groups: the YET is streamed once per group, each event row read
     // only when its bit is set; many groups: one pass over a pool table
     if (!p->groups.empty() && p->groups.size() <= 2) return ART_VARIANT_SKIP;
+    if (p->sp_ptr && p->n_tiles > 0) return ART_VARIANT_SPARSE;
     if (p->pool && p->n_tiles > 0) return ART_VARIANT_BATCHED;
     if (!p->groups.empty()) return ART_VARIANT_SKIP;
     return ART_VARIANT_PLAIN;
@@ -308,6 +311,9 @@ int resolve_variant(const art_portfolio* p) {
 bool variant_available(const art_portfolio* p, int v) {
     if (v == ART_VARIANT_PLAIN) return (p->layouts & ART_LAYOUT_LAYER) != 0;
     if (v == ART_VARIANT_SKIP) return !p->groups.empty();
+    if (v == ART_VARIANT_SPARSE)
+        return p->sp_ptr != nullptr && p->n_tiles > 0 &&
+               (size_t)p->pool_np * 16 + (size_t)p->n_tiles * p->pool_np * 32 <= 200 * 1024;
     if (v == ART_VARIANT_BATCHED) return p->pool != nullptr && p->n_tiles > 0 && batched_smem(p, false) <= 200 * 1024;
     if (v == ART_VARIANT_FP64) return p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024;
     return false;
@@ -325,6 +331,7 @@ cudaError_t run_forward(art_portfolio* p, int variant, const YetArgs& y, double*
                         cudaStream_t s) {
     if (variant == ART_VARIANT_PLAIN) return launch_plain(p, y, ylt, branch, s);
     if (variant == ART_VARIANT_SKIP) return launch_skip(p, y, ylt, branch, s);
+    if (variant == ART_VARIANT_SPARSE) return launch_sparse(p, y, ylt, branch, s);
     return launch_batched(p, y, ylt, branch, variant == ART_VARIANT_FP64, s);
 }
 
@@ -383,12 +390,13 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
     }
     p->loff.assign(layer_elt_off_host, layer_elt_off_host + n_layers + 1);
     p->lids.assign(layer_elt_ids_host, layer_elt_ids_host + p->loff.back());
-    p->layouts = (opt && opt->layouts) ? opt->layouts : (ART_LAYOUT_LAYER | ART_LAYOUT_POOL | ART_LAYOUT_GROUP);
+    p->layouts = (opt && opt->layouts) ? opt->layouts
+                                       : (ART_LAYOUT_LAYER | ART_LAYOUT_POOL | ART_LAYOUT_GROUP | ART_LAYOUT_SPARSE);
     p->variant = opt ? opt->variant : ART_VARIANT_AUTO;
     p->flags = opt ? opt->flags : 0;
     p->trial_tile = opt ? opt->trial_tile : 0;
     p->cta_threads = opt ? opt->cta_threads : 0;
-    if (p->variant < ART_VARIANT_AUTO || p->variant > ART_VARIANT_SKIP || p->trial_tile < 0 ||
+    if (p->variant < ART_VARIANT_AUTO || p->variant > ART_VARIANT_SPARSE || p->trial_tile < 0 ||
         (p->cta_threads != 0 && (p->cta_threads % 32 != 0 || p->cta_threads > 1024))) {
         delete p;
         return ART_EINVAL;
@@ -432,7 +440,7 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
             }
             if (e) break;
         }
-        if ((p->layouts & (ART_LAYOUT_POOL | ART_LAYOUT_POOL64)) && n_elt <= kMaxPoolElts) {
+        if ((p->layouts & (ART_LAYOUT_POOL | ART_LAYOUT_POOL64 | ART_LAYOUT_SPARSE)) && n_elt <= kMaxPoolElts) {
             int epl = 1;
             while (32 * epl < n_elt) epl *= 2;
             p->pool_np = 32 * epl;
@@ -446,9 +454,14 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
                 if ((e = cudaMalloc(&p->pool64, bytes))) break;
                 p->pool64_bytes = (int64_t)bytes;
             }
-            if ((e = build_pool_table(elt_losses_dev, catalogue_size, n_elt, p->pool_np, p->pool, p->pool64, stream)))
+            if ((p->pool || p->pool64) &&
+                (e = build_pool_table(elt_losses_dev, catalogue_size, n_elt, p->pool_np, p->pool, p->pool64, stream)))
                 break;
             if ((e = build_batched_meta(p))) break;
+            // the CSR offsets are 32-bit: build it when every count fits
+            if ((p->layouts & ART_LAYOUT_SPARSE) && (int64_t)n_elt * catalogue_size < ((int64_t)1 << 32) &&
+                (e = build_sparse(p, elt_losses_dev, stream)))
+                break;
         }
         if ((p->layouts & ART_LAYOUT_GROUP) && (e = build_groups(p, elt_losses_dev, stream))) break;
         if (p->flags & ART_FLAG_L2_PERSIST) {
@@ -511,7 +524,7 @@ art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* el
 }
 
 art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads) {
-    if (!p || variant < ART_VARIANT_AUTO || variant > ART_VARIANT_SKIP || trial_tile < 0 || cta_threads < 0 ||
+    if (!p || variant < ART_VARIANT_AUTO || variant > ART_VARIANT_SPARSE || trial_tile < 0 || cta_threads < 0 ||
         cta_threads % 32 != 0 || cta_threads > 1024)
         return ART_EINVAL;
     if (variant != ART_VARIANT_AUTO && !variant_available(p, variant)) return ART_EUNSUPPORTED;
@@ -720,8 +733,9 @@ art_status art_get_device_status(art_portfolio* p, cudaStream_t stream) {
 }
 
 art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes, int64_t* pool64_bytes,
-                             int64_t* group_bytes) {
+                             int64_t* group_bytes, int64_t* sparse_bytes) {
     if (!p) return ART_EINVAL;
+    if (sparse_bytes) *sparse_bytes = p->sparse_bytes;
     if (group_bytes) *group_bytes = p->group_bytes;
     if (layer_bytes) *layer_bytes = p->layer_bytes;
     if (pool_bytes) *pool_bytes = p->pool_bytes;

@@ -100,6 +100,19 @@ struct BatchedArgs {
     int32_t slots;
 };
 
+// Compressed layout description (event-major CSR of the non-zero losses).
+struct SparseArgs {
+    const uint32_t* ptr;       // [C + 1]
+    const void* entries;       // [nnz] (loss FP32, ELT int32)
+    const float* elt_terms;    // [3][pool_np]
+    const uint8_t* memb;       // [n_tiles][pool_np][32]
+    const int32_t* slot_layer; // [n_tiles][slots][32]
+    const float* occ;          // [n_layers][2]
+    const double* agg;         // [n_layers][2]
+    int32_t pool_np;
+    int32_t n_tiles;
+};
+
 // A layer group for the bitmap-skip kernel: up to 8 layers whose ELTs number
 // at most 32 together, with one event-major table over the union of those
 // ELTs and an occupancy bitmap over the catalogue. Passed by value.
@@ -152,6 +165,12 @@ struct art_portfolio {
     std::vector<uint32_t*> group_bitmap;
     int64_t group_bytes = 0;
 
+    // ART_LAYOUT_SPARSE: event-major CSR of the non-zero losses
+    uint32_t* sp_ptr = nullptr;
+    void* sp_entries = nullptr;
+    uint32_t sp_nnz = 0;
+    int64_t sparse_bytes = 0;
+
     // batched metadata (device)
     float* d_elt_terms = nullptr;      // [3][pool_np]
     double* d_elt_terms64 = nullptr;   // [3][pool_np]
@@ -184,6 +203,8 @@ namespace art {
 
 // Host-side launchers (each returns a CUDA error code).
 cudaError_t launch_plain(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t launch_sparse(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t build_sparse(art_portfolio* p, const float* src, cudaStream_t s);
 cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
 cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np, uint32_t* bitmap, cudaStream_t s);
 cudaError_t launch_batched(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, bool fp64,

@@ -21,8 +21,11 @@
 // work units (layer tile x trial tile) from an atomic counter; trials of
 // uneven length balance dynamically. No warp ever waits on another.
 //
-// Precision: V = float is the mixed form (FP32 losses and per-event sums,
-// FP64 aggregate); V = double is the all-FP64 form over an FP64 pool table.
+// Precision: V = float is the mixed form (FP32 losses and per-event sums; the
+// per-slot aggregate is a compensated FP32 pair, Knuth's two-sum, folded into
+// FP64 at the end of the trial, where the aggregate terms apply in FP64);
+// V = double is the all-FP64 form over an FP64 pool table, with the aggregate
+// summed in FP64 event by event.
 #include "art_internal.cuh"
 
 namespace art {
@@ -60,6 +63,27 @@ __device__ __forceinline__ float fin_v(float y, float m, float d, float l) { ret
 __device__ __forceinline__ double fin_v(double y, double m, double d, double l) { return fin_f64(y, m, d, l); }
 __device__ __forceinline__ float xl_v(float v, float r, float l) { return xl_f32(v, r, l); }
 __device__ __forceinline__ double xl_v(double v, double r, double l) { return xl_f64(v, r, l); }
+
+// Per-slot aggregate: FP32 values go into a compensated FP32 pair (two-sum),
+// FP64 values straight into an FP64 sum.
+struct AggF32 {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = hi + v;
+        const float bp = t - hi;
+        lo += (hi - (t - bp)) + (v - bp);
+        hi = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+struct AggF64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <typename V> struct AggOf;
+template <> struct AggOf<float> { using type = AggF32; };
+template <> struct AggOf<double> { using type = AggF64; };
 
 template <typename V, int EPL, int SLOTS, int U>
 __global__ void __launch_bounds__(256) ylt_batched_kernel(const BatchedArgs a, const YetArgs y,
@@ -124,9 +148,7 @@ __global__ void __launch_bounds__(256) ylt_batched_kernel(const BatchedArgs a, c
             bool bad_off;
             trial_range(y, t, b, e, bad_off);
             bad_off_seen |= bad_off;
-            double S[SLOTS];
-#pragma unroll
-            for (int s = 0; s < SLOTS; ++s) S[s] = 0.0;
+            typename AggOf<V>::type S[SLOTS];
 
             for (int64_t d0 = b; d0 < e; d0 += 32) {
                 const int cnt = (int)min((int64_t)32, e - d0);
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(256) ylt_batched_kernel(const BatchedArgs a, c
 #pragma unroll
                         for (int s = 0; s < SLOTS; ++s) {
                             const V o = xl_v(x[s], occ_r[s], occ_l[s]);
-                            if (o > V(0)) S[s] += (double)o;
+                            if (o > V(0)) S[s].add(o);
                         }
                     }
                 }
@@ -180,9 +202,10 @@ __global__ void __launch_bounds__(256) ylt_batched_kernel(const BatchedArgs a, c
                 const int32_t j = jl[s];
                 if (j >= 0) {
                     const double ar = a.agg[2 * j], al = a.agg[2 * j + 1];
+                    const double sum = S[s].value();
                     const size_t w = (size_t)j * (size_t)y.n_trials + (size_t)t;
-                    ylt[w] = xl_f64(S[s], ar, al);
-                    if (branch) branch[w] = agg_branch(S[s], ar, al);
+                    ylt[w] = xl_f64(sum, ar, al);
+                    if (branch) branch[w] = agg_branch(sum, ar, al);
                 }
             }
         }

@@ -95,7 +95,11 @@ def test_other_entry_points_reject_bad_arguments_on_the_host(art):
     assert L.art_get_device_status(None, None) == art.ART_EINVAL
     assert L.art_update_terms(None, None, None, None, None) == art.ART_EINVAL
     assert L.art_set_variant(None, 1, 0, 0) == art.ART_EINVAL
-    assert L.art_get_footprint(None, None, None, None, None) == art.ART_EINVAL
+    assert L.art_get_footprint(None, None, None, None, None, None) == art.ART_EINVAL
+    out = ctypes.c_double()
+    assert L.art_probe(99, 1 << 20, 1, ctypes.byref(out)) == art.ART_EINVAL
+    assert L.art_probe(0, 16, 1, ctypes.byref(out)) == art.ART_EINVAL
+    assert L.art_probe(0, 1 << 20, 0, ctypes.byref(out)) == art.ART_EINVAL
     L.art_destroy_portfolio(None)  # no-op
 
 

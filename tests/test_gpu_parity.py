@@ -16,8 +16,10 @@ from gpu_util import assert_ylt_close, device_yet, gpu_metrics, oracle_sample, r
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_FP64, art.ART_VARIANT_SKIP]
-ALL_LAYOUTS = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_POOL64 | art.ART_LAYOUT_GROUP
+VARIANTS = [art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_FP64, art.ART_VARIANT_SKIP,
+            art.ART_VARIANT_SPARSE]
+ALL_LAYOUTS = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_POOL64 | art.ART_LAYOUT_GROUP
+               | art.ART_LAYOUT_SPARSE)
 
 
 def _small_cases():
@@ -94,7 +96,7 @@ def test_config1_sampled_plain_and_batched(c1u):
     T = w.yet.n_trials
     trials = np.unique(np.concatenate([[0, T - 1], rng.choice(T, 3000, replace=False)]))
     ref, gross, _ = oracle_sample(w, trials)
-    for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SKIP):
+    for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SKIP, art.ART_VARIANT_SPARSE):
         ylt, _ = run_ylt(p, w, v, yet=yet)
         got = ylt[:, torch.from_numpy(trials).cuda()].cpu().numpy()
         assert_ylt_close(got, ref, gross, f"c1u variant {v}")
@@ -140,6 +142,9 @@ def test_determinism_and_graph_replay():
         e, _ = run_ylt(p, w, art.ART_VARIANT_SKIP, yet=yet)
         f, _ = run_ylt(p, w, art.ART_VARIANT_SKIP, yet=yet)
         assert torch.equal(e, f)
+        h, _ = run_ylt(p, w, art.ART_VARIANT_SPARSE, yet=yet)
+        i, _ = run_ylt(p, w, art.ART_VARIANT_SPARSE, yet=yet)
+        assert torch.equal(h, i)
     finally:
         p.close()
     g = art.portfolio_from_workload(w, flags=art.ART_FLAG_GRAPH)
@@ -180,7 +185,7 @@ def test_out_of_range_ids_flag_without_trapping():
     bad = workloads.Workload(w.name, w.portfolio, workloads.YET(w.yet.n_trials, ids, 0, w.yet.trial_off), w.probs)
     p = art.portfolio_from_workload(w)
     try:
-        for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SKIP):
+        for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SKIP, art.ART_VARIANT_SPARSE):
             dids, off, k, T = device_yet(bad)
             art.art_set_variant(p, v)
             ylt = torch.zeros((w.portfolio.n_layers, T), dtype=torch.float64, device="cuda")
@@ -227,7 +232,7 @@ def test_update_terms_and_rounding():
         np.testing.assert_array_equal(t2[:, 2:], terms[:, 2:])
         prob = dict(w.oracle_problem(), occ_ret=t2[:, 0])
         ref, gross, _ = oracle.ylt(prob)
-        for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SKIP):
+        for v in (art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SKIP, art.ART_VARIANT_SPARSE):
             ylt, _ = run_ylt(p, w, v)
             assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"updated terms variant {v}")
     finally:
