@@ -152,58 +152,55 @@ def layer_groups(port):
 
 
 def algorithmic_bytes(w, variant: str):
-    """Algorithmic bytes of one forward launch set.
+    """Bytes one forward launch set moves, three ways.
 
-    hbm: compulsory DRAM traffic -- every YET id (4 B) and CSR offset read
-    once, every event-major table row a pass can touch read once from DRAM
-    (the distinct rows, bounded by the table), the YLT (8 B) and branch-free
-    output written once.
-    l2: the sectors the gathers touch -- 32 * ceil(4 n_pad / 32) bytes per
-    (event, layer) for the per-layer tables, 32 * ceil(4 n_pool / 32) per
-    event for the pool table -- plus the id stream.
+    s8d: the per-unit figure -- 4 B per event id (plus 8 B per CSR offset)
+      and the 32-byte sectors every table read touches (32 * ceil(row / 32)
+      per row read; 32 B of offsets plus 8 B per entry for the CSR), plus the
+      YLT written. The tables here (128 MB to 8 GB) do not fit the 126 MB L2
+      next to the id stream, so these count against HBM.
+    compulsory: ids, offsets and YLT once, plus every distinct row a pass can
+      touch read once (the least DRAM traffic the pass can have).
+    l2: the id stream plus the sectors the table reads touch (L2 traffic).
     """
     port, yet = w.portfolio, w.yet
     n_events = yet.n_events
     ids = 4 * n_events + (8 * (yet.n_trials + 1) if yet.trial_off is not None else 0)
     ylt = 8 * yet.n_trials * port.n_layers
     C = port.catalogue_size
-    sizes = port.elts_per_layer()
+    touched_frac = 1.0 - np.exp(-n_events / C)
+    sec = lambda nbytes: 32 * -(-nbytes // 32)
     pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
     if variant == "skip":
-        # per group: the id stream, one bitmap word per event (L1/L2), and a
-        # row read only for events with a non-zero loss in the group's ELTs
-        hbm = 0.0
-        l2 = 0.0
-        frac_touched = 1.0 - np.exp(-n_events / C)
+        reads, table = 0.0, 0.0
         for g in layer_groups(port):
             rowb = 4 * pad(len(g))
             nz = np.any(port.elt_losses[g] != 0, axis=0)
-            p_nz = float(nz.mean())
-            hbm += ids + C / 8 + nz.sum() * rowb * frac_touched
-            l2 += ids + n_events * p_nz * 32 * -(-rowb // 32)
-        return {"hbm": hbm + ylt, "l2": l2, "ids": ids, "ylt": ylt, "table": None}
+            reads += n_events * float(nz.mean()) * sec(rowb)
+            table += float(nz.sum()) * rowb + C / 8
+        n_groups = len(layer_groups(port))
+        return {"s8d": n_groups * ids + ylt + reads, "compulsory": n_groups * ids + ylt + table * touched_frac,
+                "l2": n_groups * ids + reads}
     if variant == "sparse":
-        # per event: the id, the CSR offsets (one sector) and 8 bytes per
-        # non-zero loss; the CSR (C + 1 offsets + entries) read once from DRAM
         nnz_per_event = float((port.elt_losses != 0).sum(axis=0).mean())
-        nnz_total = float((port.elt_losses != 0).sum())
-        csr = 4 * (C + 1) + 8 * nnz_total
-        return {"hbm": ids + ylt + csr * (1.0 - np.exp(-n_events / C)),
-                "l2": ids + n_events * (32 + 8 * nnz_per_event), "ids": ids, "ylt": ylt, "table": csr}
+        csr = 4 * (C + 1) + 8 * float((port.elt_losses != 0).sum())
+        reads = n_events * (32 + 8 * nnz_per_event)
+        return {"s8d": ids + ylt + reads, "compulsory": ids + ylt + csr * touched_frac, "l2": ids + reads}
     if variant == "plain":
-        row = np.array([4 * pad(int(n)) for n in sizes])
-        sectors = int(sum(32 * -(-r // 32) for r in row)) * n_events
-        table = int(row.sum()) * C
+        rows = [4 * pad(int(n)) for n in port.elts_per_layer()]
+        reads = float(sum(sec(r) for r in rows)) * n_events
+        table = float(sum(rows)) * C
+        n_launch = port.n_layers
     else:
         epl = 1
         while 32 * epl < port.n_elt:
             epl *= 2
         rowb = 32 * epl * (8 if variant == "fp64" else 4)
-        sectors = rowb * n_events
-        table = rowb * C
-    # distinct rows touched by a pass: every catalogue row with probability 1 - exp(-n_events / C)
-    touched = table * (1.0 - np.exp(-n_events / C))
-    return {"hbm": ids + ylt + touched, "l2": ids + sectors, "ids": ids, "ylt": ylt, "table": table}
+        reads = float(sec(rowb)) * n_events
+        table = float(rowb) * C
+        n_launch = 1
+    return {"s8d": n_launch * ids + ylt + reads, "compulsory": n_launch * ids + ylt + table * touched_frac,
+            "l2": n_launch * ids + reads}
 
 
 def run_reference(args):
@@ -274,6 +271,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probes", action="store_true", help="skip the libart bandwidth probes")
     ap.add_argument("--trials", type=int, default=0,
                     help="keep only the first N trials (small cases for profiling; 0 = the full workload)")
     args = ap.parse_args()
@@ -371,10 +369,11 @@ def main():
     # roofline of the dominant kernel (the forward)
     peak, peak_kind = measured_peaks()
     ab = algorithmic_bytes(w, variant)
-    achieved = ab["hbm"] / (fwd_mean / 1e3) / 1e9
+    secs = fwd_mean / 1e3
+    achieved = ab["s8d"] / secs / 1e9
     # measured limits the driver's figures do not cover (libart probes)
     probes = {}
-    if rank == 0:
+    if rank == 0 and not args.no_probes:
         probes = {"l2_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 64 << 20),
                   "l2_gather64_gbs": art.art_probe(art.ART_PROBE_GATHER64, 64 << 20),
                   "dram_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 8 << 30, 3),
@@ -384,9 +383,10 @@ def main():
                    "sparse": "ylt_sparse"}[variant]
     traffic = recorded_traffic(kernel_name, args.config)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
-            "kernel": kernel_name, "algorithmic_bytes_per_launch": ab["hbm"],
-            "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": ab["l2"] / (fwd_mean / 1e3) / 1e9}
+            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "kernel": kernel_name,
+            "algorithmic_bytes_per_launch": ab["s8d"],
+            "compulsory_bytes_per_launch": ab["compulsory"], "compulsory_gbs": ab["compulsory"] / secs / 1e9,
+            "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": ab["l2"] / secs / 1e9}
     if probes:
         roof["l2_gather_peak_gbs"] = probes["l2_gather32_gbs"]
         roof["l2_frac"] = roof["l2_sector_gbs"] / probes["l2_gather32_gbs"]
