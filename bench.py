@@ -329,8 +329,15 @@ def main():
         torch.cuda.synchronize(dev)
         fwd_ms[v] = e0.elapsed_time(e1) / 3
     variant = min(fwd_ms, key=fwd_ms.get)
-    art.art_set_variant(p, vmap[variant])
-    log(f"[bench] forward ms per variant: {fwd_ms}; using {variant}")
+    tune = None
+    if args.variant == "auto":
+        # the library's autotuner picks the variant and tile shapes on a sample
+        tune = art.art_autotune(p, T, ids, off, K, ylt, sample_trials=min(T, 65536), stream=stream)
+        inv = {v: k for k, v in vmap.items()}
+        variant = inv.get(tune["variant"], variant)
+    else:
+        art.art_set_variant(p, vmap[variant])
+    log(f"[bench] forward ms per variant (default shapes): {fwd_ms}; using {variant} {tune or ''}")
 
     for _ in range(args.warmup):
         step()
@@ -441,7 +448,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
-                       "variant": variant, "layers": L, "trials": T, "events": yet.n_events,
+                       "variant": variant, "autotune": tune, "layers": L, "trials": T, "events": yet.n_events,
                        "lookups_per_step": lookups,
                        "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
                        "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"},

@@ -283,6 +283,34 @@ ART_API art_status art_run_ylt_backward(art_portfolio* p, int64_t n_trials, cons
                                 const uint8_t* branch_dev, const double* grad_ylt_dev,
                                 double* grad_terms_dev, double* grad_mult_dev, cudaStream_t stream);
 
+/* Result of art_autotune. */
+typedef struct {
+    int32_t variant;      /* chosen ART_VARIANT_*                                  */
+    int32_t slots;        /* layer tile of the persistent kernels: 32 * slots layers */
+    int32_t trial_tile;   /* trials per work unit (0: the variant has none)        */
+    int32_t cta_threads;  /* threads per CTA (0: the variant's fixed shape)        */
+    float sample_ms;      /* best forward time on the sample                       */
+    int32_t candidates;   /* shapes timed                                          */
+    int32_t from_cache;   /* 1 when the shape came from the cache file             */
+    int32_t reserved;
+} art_tune_result;
+
+/*
+ * art_autotune -- pick the forward variant and the persistent kernels' tile
+ * shapes (layer tile: 32, 64 or 128 layers per warp; trials per work unit
+ * 1-16; 128 or 256 threads per CTA) by timing each candidate on the first
+ * `sample_trials` trials (0: 65,536) of the given YET, and keep the fastest
+ * in the portfolio (as art_set_variant would). ylt_dev receives the sample's
+ * YLT ([n_layers][sample] FP64; caller-owned scratch). When the environment
+ * variable ART_AUTOTUNE_CACHE names a file, a shape recorded there for the
+ * same device, portfolio shape and YET shape (trials bucketed by powers of
+ * two) is applied without timing, and a newly timed shape is appended.
+ * Synchronises the stream. Not for use during stream capture.
+ */
+ART_API art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
+                                const int64_t* trial_off_dev, int32_t events_per_trial, double* ylt_dev,
+                                int32_t sample_trials, cudaStream_t stream, art_tune_result* out);
+
 /* Synchronise the stream, then read and clear the portfolio's device error
  * flags: ART_OK, ART_EID_RANGE (an id outside [0, C) was seen; it counted as
  * zero loss) or ART_EINVAL (decreasing CSR offsets were seen). */

@@ -26,7 +26,7 @@ ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH = 1, 2
 EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set_variant", "art_run_ylt",
            "art_run_ylt_host", "art_metrics", "art_metrics_backward", "art_run_ylt_backward",
            "art_get_device_status", "art_get_footprint", "art_destroy_portfolio", "art_status_string",
-           "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe")
+           "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe", "art_autotune")
 
 
 class LayerTerms(ctypes.Structure):
@@ -38,6 +38,12 @@ class Options(ctypes.Structure):
     _fields_ = [("layouts", ctypes.c_int32), ("variant", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("trial_tile", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 3)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("slots", ctypes.c_int32), ("trial_tile", ctypes.c_int32),
+                ("cta_threads", ctypes.c_int32), ("sample_ms", ctypes.c_float), ("candidates", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ArtError(RuntimeError):
@@ -80,6 +86,7 @@ def lib():
         "art_last_cuda_error": ([], ctypes.c_char_p),
         "art_version": ([], i32),
         "art_probe": ([i32, i64, i32, P], st),
+        "art_autotune": ([P, i64, P, P, i32, P, i32, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -255,6 +262,17 @@ def art_run_ylt_backward(p, n_trials: int, event_ids, trial_off, events_per_tria
                                     _dptr(branch), _dptr(grad_ylt), _dptr(grad_terms), _dptr(grad_mult),
                                     _stream(stream))
     _check(rc, "art_run_ylt_backward")
+
+
+def art_autotune(p, n_trials: int, event_ids, trial_off, events_per_trial: int, ylt, sample_trials: int = 0,
+                 stream=None) -> dict:
+    """Time the variants and tile shapes on a sample of the YET and keep the
+    fastest in the portfolio; returns the chosen shape."""
+    r = TuneResult()
+    rc = lib().art_autotune(_h(p), int(n_trials), _dptr(event_ids), _dptr(trial_off), int(events_per_trial),
+                            _dptr(ylt), int(sample_trials), _stream(stream), ctypes.byref(r))
+    _check(rc, "art_autotune")
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
 
 
 def art_get_device_status(p, stream=None) -> int:

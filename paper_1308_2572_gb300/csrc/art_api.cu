@@ -2,7 +2,10 @@
 // stage (building the direct-access tables in the kernels' layouts), dispatch
 // to the kernels, host-buffer staging, CUDA-graph replay and status.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -139,31 +142,65 @@ cudaError_t upload_batched_terms(art_portfolio* p) {
     return cudaMemcpy(p->d_agg, agg.data(), sizeof(double) * agg.size(), cudaMemcpyHostToDevice);
 }
 
-cudaError_t build_batched_meta(art_portfolio* p) {
+}  // namespace
+
+// Layer tile of the persistent kernels: layer j sits at (tile, slot, lane)
+// with 32 * slots layers per tile; memb holds, per (tile, ELT, lane), the
+// bits of the lane's slots whose layer covers the ELT.
+cudaError_t art::set_layer_tile(art_portfolio* p, int32_t slots) {
     const int L = p->n_layers;
-    p->slots = L <= 64 ? 2 : (L <= 128 ? 4 : 8);
-    const int per_tile = 32 * p->slots;
-    p->n_tiles = (L + per_tile - 1) / per_tile;
+    const int per_tile = 32 * slots;
+    const int n_tiles = (L + per_tile - 1) / per_tile;
     const int np = p->pool_np;
-    std::vector<int32_t> slot_layer((size_t)p->n_tiles * p->slots * 32, -1);
-    std::vector<uint8_t> memb((size_t)p->n_tiles * np * 32, 0);
+    std::vector<int32_t> slot_layer((size_t)n_tiles * slots * 32, -1);
+    std::vector<uint8_t> memb((size_t)n_tiles * np * 32, 0);
     for (int j = 0; j < L; ++j) {
         const int tile = j / per_tile, r = j % per_tile, slot = r / 32, lane = r % 32;
-        slot_layer[((size_t)tile * p->slots + slot) * 32 + lane] = j;
+        slot_layer[((size_t)tile * slots + slot) * 32 + lane] = j;
         for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
             memb[((size_t)tile * np + p->lids[c]) * 32 + lane] |= (uint8_t)(1u << slot);
     }
+    int32_t* d_sl = nullptr;
+    uint8_t* d_mb = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_sl, sizeof(int32_t) * slot_layer.size()))) return e;
+    if ((e = cudaMalloc(&d_mb, memb.size()))) {
+        cudaFree(d_sl);
+        return e;
+    }
+    e = cudaMemcpy(d_sl, slot_layer.data(), sizeof(int32_t) * slot_layer.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_mb, memb.data(), memb.size(), cudaMemcpyHostToDevice);
+    if (e) {
+        cudaFree(d_sl);
+        cudaFree(d_mb);
+        return e;
+    }
+    cudaDeviceSynchronize();  // no launch may still read the old tile
+    cudaFree(p->d_slot_layer);
+    cudaFree(p->d_memb);
+    p->d_slot_layer = d_sl;
+    p->d_memb = d_mb;
+    p->slots = slots;
+    p->n_tiles = n_tiles;
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+
+cudaError_t build_batched_meta(art_portfolio* p) {
+    const int L = p->n_layers;
+    const int np = p->pool_np;
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_elt_terms, sizeof(float) * 3 * np))) return e;
     if ((e = cudaMalloc(&p->d_elt_terms64, sizeof(double) * 3 * np))) return e;
     if ((e = cudaMalloc(&p->d_occ, sizeof(float) * 2 * L))) return e;
     if ((e = cudaMalloc(&p->d_agg, sizeof(double) * 2 * L))) return e;
-    if ((e = cudaMalloc(&p->d_slot_layer, sizeof(int32_t) * slot_layer.size()))) return e;
-    if ((e = cudaMalloc(&p->d_memb, memb.size()))) return e;
     if ((e = cudaMalloc(&p->d_work_counter, sizeof(unsigned int)))) return e;
-    if ((e = cudaMemcpy(p->d_slot_layer, slot_layer.data(), sizeof(int32_t) * slot_layer.size(), cudaMemcpyHostToDevice)))
-        return e;
-    if ((e = cudaMemcpy(p->d_memb, memb.data(), memb.size(), cudaMemcpyHostToDevice))) return e;
+    if ((e = set_layer_tile(p, L <= 64 ? 2 : (L <= 128 ? 4 : 8)))) return e;
     return upload_batched_terms(p);
 }
 
@@ -744,5 +781,150 @@ art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64
 }
 
 void art_destroy_portfolio(art_portfolio* p) { free_portfolio(p); }
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+std::string tune_key(const art_portfolio* p, int64_t n_trials, int32_t k, bool csr) {
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, p->device);
+    int64_t sum_elts = 0;
+    for (int32_t j = 0; j < p->n_layers; ++j) sum_elts += p->loff[j + 1] - p->loff[j];
+    // trials bucketed by powers of two: the best shape does not move with a few trials
+    int lg = 0;
+    while (((int64_t)1 << (lg + 1)) <= n_trials) ++lg;
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|sm%d|C%d|E%d|L%d|S%lld|T2^%d|K%d|%s|lay%d", prop.name, prop.multiProcessorCount,
+                  p->catalogue, p->n_elt, p->n_layers, (long long)sum_elts, lg, k, csr ? "csr" : "dense", p->layouts);
+    return buf;
+}
+
+bool cache_lookup(const std::string& key, int32_t* v) {
+    const char* path = std::getenv("ART_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool hit = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char* tab = std::strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        int32_t a, b, c, d;
+        if (key == line && std::sscanf(tab + 1, "%d %d %d %d", &a, &b, &c, &d) == 4) {
+            v[0] = a; v[1] = b; v[2] = c; v[3] = d;
+            hit = true;  // the last matching line wins
+        }
+    }
+    std::fclose(f);
+    return hit;
+}
+
+void cache_store(const std::string& key, const int32_t* v, float ms) {
+    const char* path = std::getenv("ART_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s\t%d %d %d %d\t%.4f\n", key.c_str(), v[0], v[1], v[2], v[3], ms);
+    std::fclose(f);
+}
+
+cudaError_t apply_shape(art_portfolio* p, const int32_t* v) {
+    if ((v[0] == ART_VARIANT_BATCHED || v[0] == ART_VARIANT_SPARSE || v[0] == ART_VARIANT_FP64) && v[1] != p->slots) {
+        const cudaError_t e = set_layer_tile(p, v[1]);
+        if (e) return e;
+    }
+    p->variant = v[0];
+    p->trial_tile = v[2];
+    p->cta_threads = v[3];
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev, const int64_t* trial_off_dev,
+                        int32_t events_per_trial, double* ylt_dev, int32_t sample_trials, cudaStream_t stream,
+                        art_tune_result* out) {
+    if (!p || !ylt_dev || sample_trials < 0) return ART_EINVAL;
+    art_status st = validate_yet(n_trials, event_ids_dev, trial_off_dev, events_per_trial);
+    if (st) return st;
+    if (n_trials < 1) return ART_EINVAL;
+    const int64_t ts = std::min<int64_t>(n_trials, sample_trials > 0 ? sample_trials : 65536);
+    YetArgs y{event_ids_dev, trial_off_dev, ts, trial_off_dev ? 0 : events_per_trial, p->catalogue};
+    const std::string key = tune_key(p, n_trials, events_per_trial, trial_off_dev != nullptr);
+    int32_t best[4] = {p->variant, p->slots, p->trial_tile, p->cta_threads};
+    art_tune_result res;
+    std::memset(&res, 0, sizeof(res));
+    cudaError_t e = cudaSuccess;
+    if (cache_lookup(key, best)) {
+        const bool usable = variant_available(p, best[0]) || best[0] == ART_VARIANT_AUTO;
+        if (usable) {
+            if ((e = apply_shape(p, best))) return fail(e);
+            res.variant = best[0]; res.slots = best[1]; res.trial_tile = best[2]; res.cta_threads = best[3];
+            res.from_cache = 1;
+            if (out) *out = res;
+            return ART_OK;
+        }
+    }
+    // candidates: (variant, slots, trial tile, CTA threads)
+    std::vector<std::array<int32_t, 4>> cands;
+    if (variant_available(p, ART_VARIANT_PLAIN)) cands.push_back({ART_VARIANT_PLAIN, p->slots, 0, 0});
+    if (variant_available(p, ART_VARIANT_SKIP)) cands.push_back({ART_VARIANT_SKIP, p->slots, 0, 0});
+    const int32_t slot_opts[3] = {2, 4, 8};
+    for (int v : {ART_VARIANT_BATCHED, ART_VARIANT_SPARSE}) {
+        if (!variant_available(p, v)) continue;
+        for (int32_t sl : slot_opts) {
+            const int per_tile = 32 * sl;
+            const int64_t tiles = (p->n_layers + per_tile - 1) / per_tile;
+            if (sl > 2 && 32 * (sl / 2) >= p->n_layers) continue;  // no fewer tiles than a smaller slot count
+            if ((size_t)p->pool_np * 16 + (size_t)tiles * p->pool_np * 32 > 200 * 1024) continue;
+            for (int32_t tt : {1, 2, 4, 8, 16})
+                for (int32_t th : {128, 256}) cands.push_back({v, sl, tt, th});
+        }
+    }
+    const int32_t saved[4] = {p->variant, p->slots, p->trial_tile, p->cta_threads};
+    float best_ms = -1.0f;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))) return fail(e);
+    for (const auto& c : cands) {
+        if ((e = apply_shape(p, c.data()))) break;
+        if ((e = run_forward(p, c[0], y, ylt_dev, nullptr, stream))) break;  // warm-up
+        float ms_best = -1.0f;
+        for (int r = 0; r < 2 && !e; ++r) {
+            cudaEventRecord(a, stream);
+            e = run_forward(p, c[0], y, ylt_dev, nullptr, stream);
+            cudaEventRecord(b, stream);
+            if (!e) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (!e) cudaEventElapsedTime(&ms, a, b);
+            if (ms_best < 0 || ms < ms_best) ms_best = ms;
+        }
+        if (e) break;
+        ++res.candidates;
+        if (best_ms < 0 || ms_best < best_ms) {
+            best_ms = ms_best;
+            std::copy(c.begin(), c.end(), best);
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e) {
+        apply_shape(p, saved);
+        return fail(e);
+    }
+    if (best_ms < 0) return ART_EUNSUPPORTED;
+    if ((e = apply_shape(p, best))) return fail(e);
+    cache_store(key, best, best_ms);
+    res.variant = best[0]; res.slots = best[1]; res.trial_tile = best[2]; res.cta_threads = best[3];
+    res.sample_ms = best_ms;
+    if (out) *out = res;
+    return ART_OK;
+}
 
 }  // extern "C"

@@ -221,6 +221,9 @@ cudaError_t build_layer_table(const float* src, int32_t catalogue, const int32_t
 cudaError_t build_pool_table(const float* src, int32_t catalogue, int32_t n_elt, int32_t np, float* dst32,
                              double* dst64, cudaStream_t s);
 
+// (Re)build the layer tile of the persistent kernels (slots layers per lane).
+cudaError_t set_layer_tile(art_portfolio* p, int32_t slots);
+
 // k = ceil((1 - p) N) with the integer guard; at least 1, at most N.
 int64_t tail_count(double p, int64_t n);
 

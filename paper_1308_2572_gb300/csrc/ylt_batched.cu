@@ -221,7 +221,7 @@ static cudaError_t launch_cfg(art_portfolio* p, const BatchedArgs& a, const YetA
     const size_t smem = 3 * (size_t)(32 * EPL) * sizeof(V) + (size_t)a.n_tiles * (32 * EPL) * 32;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    const int threads = p->cta_threads > 0 ? p->cta_threads : 256;
+    const int threads = (p->cta_threads > 0 && p->cta_threads <= 256) ? p->cta_threads : 256;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (err != cudaSuccess) return err;

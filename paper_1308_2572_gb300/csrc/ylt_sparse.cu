@@ -163,7 +163,7 @@ cudaError_t launch_slots(art_portfolio* p, const SparseArgs& a, const YetArgs& y
     const size_t smem = (size_t)a.pool_np * sizeof(float4) + (size_t)a.n_tiles * a.pool_np * 32;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    const int threads = kSparseThreads;
+    const int threads = (p->cta_threads > 0 && p->cta_threads <= kSparseThreads) ? p->cta_threads : kSparseThreads;
     int per_sm = 0;
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem))) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
