@@ -432,6 +432,21 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "path": "art_run_ylt_host (pinned host YET, chunked H2D overlapped with compute) + art_metrics"}
 
+    # optional early exit (capped trials stop being read), reported separately
+    early = None
+    if variant == "skip":
+        art.art_set_flags(p, art.ART_FLAG_EARLY_EXIT)
+        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        early = {"forward_ms": e0.elapsed_time(e1) / 5,
+                 "note": "ART_FLAG_EARLY_EXIT: trials stop being read once capped; not part of value"}
+        art.art_set_flags(p, 0)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w)
@@ -454,7 +469,7 @@ def main():
                        "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"},
             "ms_per_1M_trial_ylt": fwd_mean * 1e6 / T,
             "forward_ms": fwd_mean, "forward_ms_by_variant": fwd_ms,
-            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "roofline": roof, "clocks": clk, "e2e": e2e, "early_exit": early, "gpu_launches": launches * args.steps,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

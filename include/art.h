@@ -93,7 +93,11 @@ enum {
 enum {
     ART_FLAG_L2_PERSIST = 1,  /* set a persisting L2 access-policy window over the hot
                                  table on the stream passed to each run call          */
-    ART_FLAG_GRAPH = 2        /* batched runs replay a cached CUDA graph of the launch */
+    ART_FLAG_GRAPH = 2,       /* batched runs replay a cached CUDA graph of the launch */
+    ART_FLAG_EARLY_EXIT = 4   /* skip variant: stop reading a trial once every layer of the
+                                 group has reached its aggregate cap (the aggregate never
+                                 decreases, so the loss is AggL); same results within FP32
+                                 rounding of the cap, far fewer lookups on capped trials  */
 };
 
 typedef struct {
@@ -149,6 +153,10 @@ ART_API art_status art_update_terms(art_portfolio* p, const float* elt_mult_host
 ART_API art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* elt_ded_host,
                          float* elt_lim_host, art_layer_terms* terms_host);
 
+/* Replace the portfolio's ART_FLAG_* flags (ART_FLAG_L2_PERSIST takes effect
+ * only if it was set at creation, which reserves the persisting L2 area). */
+ART_API art_status art_set_flags(art_portfolio* p, int32_t flags);
+
 /* Select the kernel variant (ART_VARIANT_*) and batched tile shape; 0 keeps
  * the current value of a tile parameter. */
 ART_API art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads);
@@ -193,6 +201,29 @@ ART_API art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t
 ART_API art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
                             const int64_t* trial_off_host, int32_t events_per_trial,
                             double* ylt_host, cudaStream_t stream);
+
+/*
+ * art_run_payouts -- Algorithm 1's running form for one layer (Section II:
+ * the cumulative sum of the occurrence-net losses, the aggregate terms on
+ * every cumulative value, the per-event difference, and the trial loss as
+ * their sum). For layer j and every trial, in trial order,
+ *     C_d = sum_{i <= d} o_i                        FP64
+ *     p_d = XL(C_d; AggR, AggL) - XL(C_{d-1}; AggR, AggL),  C_0 = 0
+ * with o_i as in art_run_ylt. Unlike the trial loss, the payouts depend on
+ * the order of the events (the aggregate limit runs out part way).
+ *  layer          0 .. n_layers-1 (needs the ART_LAYOUT_LAYER tables).
+ *  payouts_dev    NULL, or one FP64 per event of the YET, laid out like
+ *                 event_ids_dev (dense [T][K] or CSR positions).
+ *  exhaust_dev    NULL, or [T] int32: the 0-based position within the trial
+ *                 of the first event with C_d - AggR >= AggL (the event that
+ *                 exhausts the aggregate limit), -1 if none.
+ *  ylt_dev        NULL, or [T] FP64: XL(C_K; AggR, AggL), the sum of the p_d.
+ * Runs FP64 arithmetic per event: a reporting path, much slower than
+ * art_run_ylt. Errors: ART_EINVAL, ART_EUNSUPPORTED, ART_ECUDA.
+ */
+ART_API art_status art_run_payouts(art_portfolio* p, int32_t layer, int64_t n_trials, const int32_t* event_ids_dev,
+                                   const int64_t* trial_off_dev, int32_t events_per_trial, double* payouts_dev,
+                                   int32_t* exhaust_dev, double* ylt_dev, cudaStream_t stream);
 
 /*
  * art_metrics -- financial functions on the YLT (Section I: PML and TVaR;

@@ -20,13 +20,14 @@ LIB_PATH = os.path.join(_HERE, "_build", "libart.so")
 ART_OK, ART_EINVAL, ART_ENOMEM, ART_ECUDA, ART_EID_RANGE, ART_ETIMEOUT, ART_EUNSUPPORTED = range(7)
 ART_VARIANT_AUTO, ART_VARIANT_PLAIN, ART_VARIANT_BATCHED, ART_VARIANT_FP64, ART_VARIANT_SKIP, ART_VARIANT_SPARSE = range(6)
 ART_LAYOUT_LAYER, ART_LAYOUT_POOL, ART_LAYOUT_POOL64, ART_LAYOUT_GROUP, ART_LAYOUT_SPARSE = 1, 2, 4, 8, 16
-ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH = 1, 2
+ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH, ART_FLAG_EARLY_EXIT = 1, 2, 4
 
 # Every entry point declared in include/art.h.
 EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set_variant", "art_run_ylt",
            "art_run_ylt_host", "art_metrics", "art_metrics_backward", "art_run_ylt_backward",
            "art_get_device_status", "art_get_footprint", "art_destroy_portfolio", "art_status_string",
-           "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe", "art_autotune")
+           "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe", "art_autotune",
+           "art_run_payouts", "art_set_flags")
 
 
 class LayerTerms(ctypes.Structure):
@@ -73,6 +74,7 @@ def lib():
         "art_update_terms": ([P, P, P, P, P], st),
         "art_get_terms": ([P, P, P, P, P], st),
         "art_set_variant": ([P, i32, i32, i32], st),
+        "art_set_flags": ([P, i32], st),
         "art_run_ylt": ([P, i64, P, P, i32, P, P, P], st),
         "art_run_ylt_host": ([P, i64, P, P, i32, P, P], st),
         "art_metrics": ([P, i64, i32, P, i32, P, P, P, P], st),
@@ -87,6 +89,7 @@ def lib():
         "art_version": ([], i32),
         "art_probe": ([i32, i64, i32, P], st),
         "art_autotune": ([P, i64, P, P, i32, P, i32, P, P], st),
+        "art_run_payouts": ([P, i32, i64, P, P, i32, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -210,6 +213,10 @@ def art_set_variant(p, variant: int, trial_tile: int = 0, cta_threads: int = 0) 
     _check(lib().art_set_variant(_h(p), variant, trial_tile, cta_threads), "art_set_variant")
 
 
+def art_set_flags(p, flags: int) -> None:
+    _check(lib().art_set_flags(_h(p), int(flags)), "art_set_flags")
+
+
 def art_run_ylt(p, n_trials: int, event_ids, trial_off, events_per_trial: int, ylt, branch=None,
                 stream=None) -> None:
     """event_ids: CUDA int32; trial_off: CUDA int64 [T+1] or None (dense, K =
@@ -224,6 +231,17 @@ def art_run_ylt_host(p, n_trials: int, event_ids, trial_off, events_per_trial: i
     rc = lib().art_run_ylt_host(_h(p), int(n_trials), _hptr(event_ids), _hptr(trial_off), int(events_per_trial),
                                 _hptr(ylt), _stream(stream))
     _check(rc, "art_run_ylt_host")
+
+
+def art_run_payouts(p, layer: int, n_trials: int, event_ids, trial_off, events_per_trial: int, payouts=None,
+                    exhaust=None, ylt=None, stream=None) -> None:
+    """Per-event payouts of Algorithm 1's running form for one layer (CUDA
+    float64, laid out like event_ids), the position of the event exhausting
+    the aggregate limit per trial (CUDA int32 [T], -1 if none) and the trial
+    losses (CUDA float64 [T]); any output may be None."""
+    rc = lib().art_run_payouts(_h(p), int(layer), int(n_trials), _dptr(event_ids), _dptr(trial_off),
+                               int(events_per_trial), _dptr(payouts), _dptr(exhaust), _dptr(ylt), _stream(stream))
+    _check(rc, "art_run_payouts")
 
 
 def art_metrics(ylt, n_trials: int, n_layers: int, probs: Sequence[float], mean=None, pml=None, tvar=None,

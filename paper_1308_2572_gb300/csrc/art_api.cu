@@ -560,6 +560,16 @@ art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* el
     return ART_OK;
 }
 
+art_status art_set_flags(art_portfolio* p, int32_t flags) {
+    if (!p || (flags & ~(ART_FLAG_L2_PERSIST | ART_FLAG_GRAPH | ART_FLAG_EARLY_EXIT))) return ART_EINVAL;
+    p->flags = flags;
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    return ART_OK;
+}
+
 art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads) {
     if (!p || variant < ART_VARIANT_AUTO || variant > ART_VARIANT_SPARSE || trial_tile < 0 || cta_threads < 0 ||
         cta_threads % 32 != 0 || cta_threads > 1024)
@@ -716,6 +726,18 @@ art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* e
     const cudaError_t e2 = cudaStreamSynchronize(stream);
     if (e || e2) return fail(e ? e : e2);
     return ART_OK;
+}
+
+art_status art_run_payouts(art_portfolio* p, int32_t layer, int64_t n_trials, const int32_t* event_ids_dev,
+                           const int64_t* trial_off_dev, int32_t events_per_trial, double* payouts_dev,
+                           int32_t* exhaust_dev, double* ylt_dev, cudaStream_t stream) {
+    if (!p || layer < 0 || layer >= p->n_layers) return ART_EINVAL;
+    const art_status st = validate_yet(n_trials, event_ids_dev, trial_off_dev, events_per_trial);
+    if (st) return st;
+    if (!(p->layouts & ART_LAYOUT_LAYER)) return ART_EUNSUPPORTED;
+    YetArgs y{event_ids_dev, trial_off_dev, n_trials, trial_off_dev ? 0 : events_per_trial, p->catalogue};
+    const cudaError_t e = launch_payouts(p, layer, y, payouts_dev, exhaust_dev, ylt_dev, stream);
+    return e ? fail(e) : ART_OK;
 }
 
 art_status art_metrics(const double* ylt_dev, int64_t n_trials, int32_t n_layers, const double* probs_host,

@@ -203,6 +203,8 @@ namespace art {
 
 // Host-side launchers (each returns a CUDA error code).
 cudaError_t launch_plain(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t launch_payouts(art_portfolio* p, int32_t j, const YetArgs& y, double* payouts, int32_t* exhaust,
+                           double* ylt, cudaStream_t s);
 cudaError_t launch_sparse(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
 cudaError_t build_sparse(art_portfolio* p, const float* src, cudaStream_t s);
 cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);

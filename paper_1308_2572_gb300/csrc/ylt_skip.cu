@@ -138,9 +138,25 @@ __device__ __forceinline__ void load_chunk(const int32_t* __restrict__ ids, int3
     }
 }
 
+// True when every layer of the group has reached its aggregate cap: the sum
+// of the lanes' partial aggregates is at least AggR + AggL. The aggregate
+// never decreases (o >= 0), so the trial's loss is then AggL exactly.
+template <int LT>
+__device__ __forceinline__ bool group_capped(const GroupArgs& g, const float (&hi)[LT], const float (&lo)[LT]) {
+    bool all = true;
+#pragma unroll
+    for (int j = 0; j < LT; ++j) {
+        float v = hi[j] + lo[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (j < g.n_layers) all = all && ((double)v - g.agg_ret[j] >= g.agg_lim[j]);
+    }
+    return all;
+}
+
 template <int NP, int LT, bool VEC>
 __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupArgs g, const YetArgs y,
-                                                                  const int32_t smem_words,
+                                                                  const int32_t smem_words, const bool early_exit,
                                                                   double* __restrict__ ylt,
                                                                   uint8_t* __restrict__ branch,
                                                                   int* __restrict__ flags) {
@@ -193,6 +209,7 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
             lo[j] = 0.0f;
         }
         int qn = 0;  // warp-uniform queue length, < 32 between steps
+        bool capped_exit = false;
         if (n == 0 && tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
         for (int32_t c0 = 0; c0 < n; c0 += 32 * E) {
             int32_t id[E];
@@ -228,6 +245,14 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
                     __syncwarp();
                 }
             }
+            if (early_exit && group_capped<LT>(g, hi, lo)) {
+                // the rest of the trial cannot change its loss: skip it (and
+                // the queued events); request the next trial's first chunk
+                if (c0 + 32 * E < n && tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
+                qn = 0;
+                capped_exit = true;
+                break;
+            }
         }
         __syncwarp();
         if (lane < qn) eval_event<NP, LT>(g, q[lane], hi, lo);
@@ -239,8 +264,9 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
             if (lane == 0 && j < g.n_layers) {
                 const size_t wi = (size_t)g.layer[j] * (size_t)y.n_trials + (size_t)t;
-                ylt[wi] = xl_f64(sum, g.agg_ret[j], g.agg_lim[j]);
-                if (branch) branch[wi] = agg_branch(sum, g.agg_ret[j], g.agg_lim[j]);
+                // an early exit means every layer reached its cap: the loss is AggL
+                ylt[wi] = capped_exit ? g.agg_lim[j] : xl_f64(sum, g.agg_ret[j], g.agg_lim[j]);
+                if (branch) branch[wi] = capped_exit ? (uint8_t)2 : agg_branch(sum, g.agg_ret[j], g.agg_lim[j]);
             }
         }
         t = tn;
@@ -252,8 +278,8 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
 }
 
 template <int NP, int LT>
-cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, double* ylt,
-                         uint8_t* branch, int* flags, cudaStream_t s) {
+cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
+                         double* ylt, uint8_t* branch, int* flags, cudaStream_t s) {
     // 16-byte id loads when every trial starts and ends on a multiple of 4 ids
     const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
     auto kern = vec ? ylt_skip_kernel<NP, LT, true> : ylt_skip_kernel<NP, LT, false>;
@@ -268,17 +294,18 @@ cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int3
     const int smem = queue_bytes + smem_words * 4;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     const int64_t grid = std::min<int64_t>(num_sms, (y.n_trials + kSkipWarps - 1) / kSkipWarps);
-    kern<<<(unsigned)std::max<int64_t>(1, grid), kSkipThreads, smem, s>>>(g, y, smem_words, ylt, branch, flags);
+    kern<<<(unsigned)std::max<int64_t>(1, grid), kSkipThreads, smem, s>>>(g, y, smem_words, early, ylt, branch,
+                                                                          flags);
     return cudaGetLastError();
 }
 
 template <int NP>
-cudaError_t launch_lt(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, double* ylt,
+cudaError_t launch_lt(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early, double* ylt,
                       uint8_t* branch, int* flags, cudaStream_t s) {
-    if (g.n_layers <= 1) return launch_group<NP, 1>(g, y, num_sms, catalogue, ylt, branch, flags, s);
-    if (g.n_layers <= 2) return launch_group<NP, 2>(g, y, num_sms, catalogue, ylt, branch, flags, s);
-    if (g.n_layers <= 4) return launch_group<NP, 4>(g, y, num_sms, catalogue, ylt, branch, flags, s);
-    return launch_group<NP, 8>(g, y, num_sms, catalogue, ylt, branch, flags, s);
+    if (g.n_layers <= 1) return launch_group<NP, 1>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    if (g.n_layers <= 2) return launch_group<NP, 2>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    if (g.n_layers <= 4) return launch_group<NP, 4>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    return launch_group<NP, 8>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
 }
 
 // Bitmap of a group table: bit i set when row i has any non-zero entry.
@@ -301,15 +328,16 @@ cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np
 }
 
 cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s) {
+    const bool early = (p->flags & ART_FLAG_EARLY_EXIT) != 0;
     for (size_t gi = 0; gi < p->groups.size(); ++gi) {
         const GroupArgs& g = p->groups[gi];
         cudaError_t err;
         switch (p->group_np[gi]) {
-            case 4: err = launch_lt<4>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
-            case 8: err = launch_lt<8>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
-            case 16: err = launch_lt<16>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
-            case 24: err = launch_lt<24>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
-            case 32: err = launch_lt<32>(g, y, p->num_sms, p->catalogue, ylt, branch, p->d_flags, s); break;
+            case 4: err = launch_lt<4>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 8: err = launch_lt<8>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 16: err = launch_lt<16>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 24: err = launch_lt<24>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 32: err = launch_lt<32>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
             default: err = cudaErrorInvalidValue;
         }
         if (err != cudaSuccess) return err;

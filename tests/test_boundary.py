@@ -93,8 +93,10 @@ def test_other_entry_points_reject_bad_arguments_on_the_host(art):
     assert L.art_metrics_backward(fake, 10, 1, None, 0, None, None, fake, None, None) == art.ART_EINVAL
     assert L.art_run_ylt_backward(None, 10, fake, None, 5, fake, fake, fake, fake, None) == art.ART_EINVAL
     assert L.art_get_device_status(None, None) == art.ART_EINVAL
+    assert L.art_run_payouts(None, 0, 10, fake, None, 5, None, None, None, None) == art.ART_EINVAL
     assert L.art_update_terms(None, None, None, None, None) == art.ART_EINVAL
     assert L.art_set_variant(None, 1, 0, 0) == art.ART_EINVAL
+    assert L.art_set_flags(None, 0) == art.ART_EINVAL
     assert L.art_get_footprint(None, None, None, None, None, None) == art.ART_EINVAL
     out = ctypes.c_double()
     assert L.art_probe(99, 1 << 20, 1, ctypes.byref(out)) == art.ART_EINVAL

@@ -261,3 +261,27 @@ def test_multilayer_workloads_sampled(name, n_sample):
             del ylt
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("name,n", [("c0", None), ("c0u", None), ("c1", 40000), ("c3", 8000)])
+def test_early_exit_keeps_results(name, n):
+    """The skip variant's optional early exit (stop reading a trial once it is
+    capped) gives the oracle's results; on the literal one-layer terms, where
+    every trial caps, exactly AggL."""
+    w = workloads.make(name, n_trials=n)
+    p = art.portfolio_from_workload(w)
+    try:
+        yet = device_yet(w)
+        full, _ = run_ylt(p, w, art.ART_VARIANT_SKIP, yet=yet)
+        art.art_set_flags(p, art.ART_FLAG_EARLY_EXIT)
+        fast, _ = run_ylt(p, w, art.ART_VARIANT_SKIP, yet=yet)
+        T = w.yet.n_trials
+        trials = np.arange(0, T, max(1, T // 1500))
+        ref, gross, _ = oracle_sample(w, trials)
+        assert_ylt_close(fast[:, torch.from_numpy(trials).cuda()].cpu().numpy(), ref, gross, f"{name} early exit")
+        capped = full == torch.from_numpy(w.portfolio.agg_lim).cuda()[:, None]
+        assert torch.equal(fast[capped], full[capped])
+        if name in ("c0", "c1"):
+            assert torch.all(fast == 2e7)
+    finally:
+        p.close()
