@@ -48,6 +48,23 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def rank_max(value: float, dist, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (the step time that counts is
+    the slowest rank's); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, n_ranks: int, seconds: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank runs the same workload on its own GPU)."""
+    return n_ranks * units_per_rank / seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -363,14 +380,12 @@ def main():
     clk = clocks.stop()
     total_ms = start.elapsed_time(end)
     fwd = [a.elapsed_time(b) for a, b in ev]
+    total_ms = rank_max(total_ms, dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_step = total_ms / args.steps
     lookups = w.lookups()
-    value = world * lookups * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(lookups * args.steps, world, total_ms / 1e3)
     fwd_mean = float(np.mean(fwd))
 
     # roofline of the dominant kernel (the forward)
@@ -421,14 +436,10 @@ def main():
             out_h[L:L + L * n_p].copy_(pml.reshape(-1), non_blocking=True)
             out_h[L + L * n_p:].copy_(tvar.reshape(-1), non_blocking=True)
             torch.cuda.synchronize(dev)
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = rank_max((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
         h2d = yet.event_ids.nbytes + (0 if yet.trial_off is None else yet.trial_off.nbytes) + 8 * L * T
         d2h = 8 * L * T + 8 * L * (1 + 2 * n_p)
-        e2e = {"value": world * lookups / e2e_s, "unit": "trial-events*ELTs/s", "ms_per_step": e2e_s * 1e3,
+        e2e = {"value": whole_job_rate(lookups, world, e2e_s), "unit": "trial-events*ELTs/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "path": "art_run_ylt_host (pinned host YET, chunked H2D overlapped with compute) + art_metrics"}
 
