@@ -312,8 +312,10 @@ def main():
     log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
-    layouts = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE
-               | (art.ART_LAYOUT_POOL64 if args.variant == "fp64" else 0))
+    # a named variant builds only its own layout (keeps profiling runs small)
+    layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_GROUP, "batched": art.ART_LAYOUT_POOL,
+               "fp64": art.ART_LAYOUT_POOL64, "sparse": art.ART_LAYOUT_SPARSE}.get(
+        args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
     p = art.portfolio_from_workload(w, device=dev, layouts=layouts)
     ids = torch.from_numpy(yet.event_ids).to(dev)
     off = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).to(dev)

@@ -323,7 +323,7 @@ typedef struct {
     float sample_ms;      /* best forward time on the sample                       */
     int32_t candidates;   /* shapes timed                                          */
     int32_t from_cache;   /* 1 when the shape came from the cache file             */
-    int32_t reserved;
+    int32_t mapping;      /* sparse variant: 0 event broadcast, 1 per-lane scatter  */
 } art_tune_result;
 
 /*

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("slots", ctypes.c_int32), ("trial_tile", ctypes.c_int32),
                 ("cta_threads", ctypes.c_int32), ("sample_ms", ctypes.c_float), ("candidates", ctypes.c_int32),
-                ("from_cache", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("from_cache", ctypes.c_int32), ("mapping", ctypes.c_int32)]
 
 
 class ArtError(RuntimeError):
@@ -290,7 +290,7 @@ def art_autotune(p, n_trials: int, event_ids, trial_off, events_per_trial: int, 
     rc = lib().art_autotune(_h(p), int(n_trials), _dptr(event_ids), _dptr(trial_off), int(events_per_trial),
                             _dptr(ylt), int(sample_trials), _stream(stream), ctypes.byref(r))
     _check(rc, "art_autotune")
-    return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
 
 def art_get_device_status(p, stream=None) -> int:

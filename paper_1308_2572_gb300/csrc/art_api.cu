@@ -160,26 +160,62 @@ cudaError_t art::set_layer_tile(art_portfolio* p, int32_t slots) {
         for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
             memb[((size_t)tile * np + p->lids[c]) * 32 + lane] |= (uint8_t)(1u << slot);
     }
+    // per tile, per ELT: the tile-local indices of the layers covering it, in
+    // layer order (the sparse kernel's scatter lists)
+    std::vector<std::vector<uint8_t>> lists((size_t)n_tiles * np);
+    for (int j = 0; j < L; ++j)
+        for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
+            lists[(size_t)(j / per_tile) * np + p->lids[c]].push_back((uint8_t)(j % per_tile));
+    size_t stride = 16;
+    for (int t = 0; t < n_tiles; ++t) {
+        size_t tot = 0;
+        for (int e2 = 0; e2 < np; ++e2) tot += lists[(size_t)t * np + e2].size();
+        stride = std::max(stride, (tot + 15) & ~(size_t)15);
+    }
+    std::vector<uint16_t> tl_off((size_t)n_tiles * (np + 1));
+    std::vector<uint8_t> tl_lay((size_t)n_tiles * stride, 0);
+    for (int t = 0; t < n_tiles; ++t) {
+        uint16_t pos = 0;
+        for (int e2 = 0; e2 < np; ++e2) {
+            tl_off[(size_t)t * (np + 1) + e2] = pos;
+            for (uint8_t v : lists[(size_t)t * np + e2]) tl_lay[(size_t)t * stride + pos++] = v;
+        }
+        tl_off[(size_t)t * (np + 1) + np] = pos;
+    }
     int32_t* d_sl = nullptr;
     uint8_t* d_mb = nullptr;
+    uint16_t* d_to = nullptr;
+    uint8_t* d_tl = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_sl, sizeof(int32_t) * slot_layer.size()))) return e;
-    if ((e = cudaMalloc(&d_mb, memb.size()))) {
+    auto cleanup = [&]() {
         cudaFree(d_sl);
+        cudaFree(d_mb);
+        cudaFree(d_to);
+        cudaFree(d_tl);
+    };
+    if ((e = cudaMalloc(&d_sl, sizeof(int32_t) * slot_layer.size())) || (e = cudaMalloc(&d_mb, memb.size())) ||
+        (e = cudaMalloc(&d_to, sizeof(uint16_t) * tl_off.size())) || (e = cudaMalloc(&d_tl, tl_lay.size()))) {
+        cleanup();
         return e;
     }
     e = cudaMemcpy(d_sl, slot_layer.data(), sizeof(int32_t) * slot_layer.size(), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(d_mb, memb.data(), memb.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_to, tl_off.data(), sizeof(uint16_t) * tl_off.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_tl, tl_lay.data(), tl_lay.size(), cudaMemcpyHostToDevice);
     if (e) {
-        cudaFree(d_sl);
-        cudaFree(d_mb);
+        cleanup();
         return e;
     }
     cudaDeviceSynchronize();  // no launch may still read the old tile
     cudaFree(p->d_slot_layer);
     cudaFree(p->d_memb);
+    cudaFree(p->d_tl_off);
+    cudaFree(p->d_tl_lay);
     p->d_slot_layer = d_sl;
     p->d_memb = d_mb;
+    p->d_tl_off = d_to;
+    p->d_tl_lay = d_tl;
+    p->tl_stride = (int32_t)stride;
     p->slots = slots;
     p->n_tiles = n_tiles;
     if (p->graph_exec) {
@@ -298,6 +334,16 @@ cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t str
     return cudaSuccess;
 }
 
+// Shared memory of the sparse kernel: ELT terms, the tiles' scatter lists and
+// one [32 events][32 * slots + 1] FP32 accumulator block per warp.
+size_t sparse_smem(const art_portfolio* p, int warps) {
+    const size_t terms = (size_t)p->pool_np * 16;
+    const size_t off = (((size_t)p->n_tiles * (p->pool_np + 1) * 2) + 15) & ~(size_t)15;
+    const size_t lay = (size_t)p->n_tiles * p->tl_stride;
+    const size_t x = (size_t)warps * 32 * (32 * p->slots + 1) * 4;
+    return terms + off + lay + x;
+}
+
 size_t batched_smem(const art_portfolio* p, bool fp64) {
     return 3 * (size_t)p->pool_np * (fp64 ? 8 : 4) + (size_t)p->n_tiles * p->pool_np * 32;
 }
@@ -319,6 +365,8 @@ void free_portfolio(art_portfolio* p) {
     cudaFree(p->d_work_counter);
     cudaFree(p->sp_ptr);
     cudaFree(p->sp_entries);
+    cudaFree(p->d_tl_off);
+    cudaFree(p->d_tl_lay);
     cudaFree(p->d_flags);
     cudaFree(p->d_loff);
     cudaFree(p->d_lids);
@@ -348,9 +396,7 @@ int resolve_variant(const art_portfolio* p) {
 bool variant_available(const art_portfolio* p, int v) {
     if (v == ART_VARIANT_PLAIN) return (p->layouts & ART_LAYOUT_LAYER) != 0;
     if (v == ART_VARIANT_SKIP) return !p->groups.empty();
-    if (v == ART_VARIANT_SPARSE)
-        return p->sp_ptr != nullptr && p->n_tiles > 0 &&
-               (size_t)p->pool_np * 16 + (size_t)p->n_tiles * p->pool_np * 32 <= 200 * 1024;
+    if (v == ART_VARIANT_SPARSE) return p->sp_ptr != nullptr && p->n_tiles > 0 && sparse_smem(p, 1) <= 200 * 1024;
     if (v == ART_VARIANT_BATCHED) return p->pool != nullptr && p->n_tiles > 0 && batched_smem(p, false) <= 200 * 1024;
     if (v == ART_VARIANT_FP64) return p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024;
     return false;
@@ -834,9 +880,10 @@ bool cache_lookup(const std::string& key, int32_t* v) {
         char* tab = std::strchr(line, '\t');
         if (!tab) continue;
         *tab = 0;
-        int32_t a, b, c, d;
-        if (key == line && std::sscanf(tab + 1, "%d %d %d %d", &a, &b, &c, &d) == 4) {
-            v[0] = a; v[1] = b; v[2] = c; v[3] = d;
+        int32_t a, b, c, d, m = -1;
+        const int got = std::sscanf(tab + 1, "%d %d %d %d %d", &a, &b, &c, &d, &m);
+        if (key == line && got >= 4) {
+            v[0] = a; v[1] = b; v[2] = c; v[3] = d; v[4] = got == 5 ? m : -1;
             hit = true;  // the last matching line wins
         }
     }
@@ -849,7 +896,7 @@ void cache_store(const std::string& key, const int32_t* v, float ms) {
     if (!path || !*path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s\t%d %d %d %d\t%.4f\n", key.c_str(), v[0], v[1], v[2], v[3], ms);
+    std::fprintf(f, "%s\t%d %d %d %d %d\t%.4f\n", key.c_str(), v[0], v[1], v[2], v[3], v[4], ms);
     std::fclose(f);
 }
 
@@ -861,6 +908,7 @@ cudaError_t apply_shape(art_portfolio* p, const int32_t* v) {
     p->variant = v[0];
     p->trial_tile = v[2];
     p->cta_threads = v[3];
+    p->sparse_mapping = v[4];
     if (p->graph_exec) {
         cudaGraphExecDestroy(p->graph_exec);
         p->graph_exec = nullptr;
@@ -880,7 +928,7 @@ art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event
     const int64_t ts = std::min<int64_t>(n_trials, sample_trials > 0 ? sample_trials : 65536);
     YetArgs y{event_ids_dev, trial_off_dev, ts, trial_off_dev ? 0 : events_per_trial, p->catalogue};
     const std::string key = tune_key(p, n_trials, events_per_trial, trial_off_dev != nullptr);
-    int32_t best[4] = {p->variant, p->slots, p->trial_tile, p->cta_threads};
+    int32_t best[5] = {p->variant, p->slots, p->trial_tile, p->cta_threads, p->sparse_mapping};
     art_tune_result res;
     std::memset(&res, 0, sizeof(res));
     cudaError_t e = cudaSuccess;
@@ -889,15 +937,16 @@ art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event
         if (usable) {
             if ((e = apply_shape(p, best))) return fail(e);
             res.variant = best[0]; res.slots = best[1]; res.trial_tile = best[2]; res.cta_threads = best[3];
+            res.mapping = best[4];
             res.from_cache = 1;
             if (out) *out = res;
             return ART_OK;
         }
     }
     // candidates: (variant, slots, trial tile, CTA threads)
-    std::vector<std::array<int32_t, 4>> cands;
-    if (variant_available(p, ART_VARIANT_PLAIN)) cands.push_back({ART_VARIANT_PLAIN, p->slots, 0, 0});
-    if (variant_available(p, ART_VARIANT_SKIP)) cands.push_back({ART_VARIANT_SKIP, p->slots, 0, 0});
+    std::vector<std::array<int32_t, 5>> cands;
+    if (variant_available(p, ART_VARIANT_PLAIN)) cands.push_back({ART_VARIANT_PLAIN, p->slots, 0, 0, -1});
+    if (variant_available(p, ART_VARIANT_SKIP)) cands.push_back({ART_VARIANT_SKIP, p->slots, 0, 0, -1});
     const int32_t slot_opts[3] = {2, 4, 8};
     for (int v : {ART_VARIANT_BATCHED, ART_VARIANT_SPARSE}) {
         if (!variant_available(p, v)) continue;
@@ -906,11 +955,21 @@ art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event
             const int64_t tiles = (p->n_layers + per_tile - 1) / per_tile;
             if (sl > 2 && 32 * (sl / 2) >= p->n_layers) continue;  // no fewer tiles than a smaller slot count
             if ((size_t)p->pool_np * 16 + (size_t)tiles * p->pool_np * 32 > 200 * 1024) continue;
+            if (v == ART_VARIANT_SPARSE &&
+                (size_t)p->pool_np * 18 + (size_t)tiles * (p->pool_np + 8192) + 32 * (32 * sl + 1) * 4 > 200 * 1024)
+                continue;
             for (int32_t tt : {1, 2, 4, 8, 16})
-                for (int32_t th : {128, 256}) cands.push_back({v, sl, tt, th});
+                for (int32_t th : {128, 256}) {
+                    if (v == ART_VARIANT_SPARSE) {
+                        cands.push_back({v, sl, tt, th, 0});
+                        cands.push_back({v, sl, tt, th, 1});
+                    } else {
+                        cands.push_back({v, sl, tt, th, -1});
+                    }
+                }
         }
     }
-    const int32_t saved[4] = {p->variant, p->slots, p->trial_tile, p->cta_threads};
+    const int32_t saved[5] = {p->variant, p->slots, p->trial_tile, p->cta_threads, p->sparse_mapping};
     float best_ms = -1.0f;
     cudaEvent_t a = nullptr, b = nullptr;
     if ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))) return fail(e);
@@ -944,6 +1003,7 @@ art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event
     if ((e = apply_shape(p, best))) return fail(e);
     cache_store(key, best, best_ms);
     res.variant = best[0]; res.slots = best[1]; res.trial_tile = best[2]; res.cta_threads = best[3];
+    res.mapping = best[4];
     res.sample_ms = best_ms;
     if (out) *out = res;
     return ART_OK;

@@ -105,12 +105,15 @@ struct SparseArgs {
     const uint32_t* ptr;       // [C + 1]
     const void* entries;       // [nnz] (loss FP32, ELT int32)
     const float* elt_terms;    // [3][pool_np]
-    const uint8_t* memb;       // [n_tiles][pool_np][32]
+    const uint8_t* memb;       // [n_tiles][pool_np][32] slot bits per (ELT, lane)
+    const uint16_t* tl_off;    // [n_tiles][pool_np + 1]: ELT e's layers in the tile are
+    const uint8_t* tl_lay;     //   tl_lay[tile][tl_off[e] .. tl_off[e+1]) (tile-local index)
     const int32_t* slot_layer; // [n_tiles][slots][32]
     const float* occ;          // [n_layers][2]
     const double* agg;         // [n_layers][2]
     int32_t pool_np;
     int32_t n_tiles;
+    int32_t tl_stride;         // bytes of tl_lay per tile (multiple of 16)
 };
 
 // A layer group for the bitmap-skip kernel: up to 8 layers whose ELTs number
@@ -176,6 +179,10 @@ struct art_portfolio {
     double* d_elt_terms64 = nullptr;   // [3][pool_np]
     uint8_t* d_memb = nullptr;
     int32_t* d_slot_layer = nullptr;
+    uint16_t* d_tl_off = nullptr;      // per tile: ELT -> tile-local layer lists
+    uint8_t* d_tl_lay = nullptr;
+    int32_t tl_stride = 0;
+    int32_t sparse_mapping = -1;       // 0 broadcast, 1 scatter, -1 by layer tile
     float* d_occ = nullptr;
     double* d_agg = nullptr;
     int32_t slots = 0, n_tiles = 0;

@@ -11,17 +11,30 @@
 // whole table row. For the 256- and 512-ELT pools (about 1.5% non-zero) it is
 // 70-130 MB, mostly L2-resident, against 2-4 GB of direct-access rows.
 //
-// Mapping (as the batched kernel): a persistent grid whose warps pull work
-// units (layer tile x trial tile) from an atomic counter; a warp takes one
-// trial at a time; lane l owns the layers of slots s at (lane l, slot s).
-// Per group of 32 events: each lane reads its event's CSR range; a ballot
-// keeps the events with entries; for each such event (in trial order) the
-// warp reads its entries (the same address in every lane), every lane applies
-// F_e to the entry's loss and adds it to the per-event sums of its slots whose
-// layer covers the ELT (a per-(ELT, lane) bit mask in shared memory); then
-// each lane applies the occurrence terms to its slots and adds the result to
-// its per-slot aggregate, a compensated FP32 pair (two-sum) folded into FP64
-// at the end of the trial, where the aggregate terms are applied in FP64.
+// Two mappings over a persistent grid whose warps pull work units (layer
+// tile x trial tile) from an atomic counter, a warp taking one trial at a
+// time; the autotuner picks one (art_autotune), the default is "scatter" for
+// tiles of 64 layers and "broadcast" for larger ones.
+//
+// Broadcast: lane l owns the layers of slots s at (lane l, slot s). Per group
+// of 32 events each lane reads its event's CSR range; for each event with
+// entries, in trial order, the warp reads the entries (one address for all
+// lanes), every lane applies F_e and adds it to its slots whose layer covers
+// the ELT (a per-(ELT, lane) bit mask), then applies the occurrence terms.
+//
+// Scatter: 32 events per group. Phase 1: lane l walks the CSR entries of event l (in ELT order),
+// applies F_e to each loss and adds it to the event's per-layer sums in its
+// own row of a [32 events][layers] FP32 block in shared memory, through the
+// ELT's list of covering layers in the tile. Each row has one writer, so the
+// sums need no atomics and are formed in ELT order (deterministic). Phase 2:
+// lane l owns the layers of slots s at (lane l, slot s); for each event of
+// the group that had entries, in trial order, it reads the event's sums for
+// its layers, applies the occurrence terms, adds the result to its per-slot
+// aggregate (a compensated FP32 pair, two-sum) and clears the entry. At the
+// end of the trial the pairs are folded into FP64 and the aggregate terms are
+// applied in FP64.
+#include <algorithm>
+
 #include "art_internal.cuh"
 
 namespace art {
@@ -44,7 +57,160 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
 }
 
 template <int SLOTS>
-__global__ void __launch_bounds__(kSparseThreads) ylt_sparse_kernel(const SparseArgs a, const YetArgs y,
+__global__ void __launch_bounds__(kSparseThreads) ylt_sparse_scatter_kernel(const SparseArgs a, const YetArgs y,
+                                                                   const int32_t trial_tile, const int64_t n_ttiles,
+                                                                   unsigned int* __restrict__ counter,
+                                                                   double* __restrict__ ylt,
+                                                                   uint8_t* __restrict__ branch,
+                                                                   int* __restrict__ flags) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int LT = 32 * SLOTS;  // layers per tile
+    constexpr int XS = LT + 1;      // row stride of the accumulator block (bank spread)
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* s_terms = reinterpret_cast<float4*>(smem);                                  // [pool_np]
+    uint16_t* s_off = reinterpret_cast<uint16_t*>(s_terms + a.pool_np);                 // [n_tiles][pool_np + 1]
+    const size_t off_bytes = (((size_t)a.n_tiles * (a.pool_np + 1) * 2) + 15) & ~(size_t)15;
+    uint8_t* s_lay = reinterpret_cast<uint8_t*>(s_off) + off_bytes;                     // [n_tiles][tl_stride]
+    float* s_x = reinterpret_cast<float*>(s_lay + (size_t)a.n_tiles * a.tl_stride);    // [warps][32][XS]
+    for (int i = threadIdx.x; i < a.pool_np; i += blockDim.x)
+        s_terms[i] = make_float4(a.elt_terms[i], a.elt_terms[a.pool_np + i], a.elt_terms[2 * a.pool_np + i], 0.f);
+    for (int i = threadIdx.x; i < a.n_tiles * (a.pool_np + 1); i += blockDim.x) s_off[i] = a.tl_off[i];
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.tl_lay);
+        uint4* dst = reinterpret_cast<uint4*>(s_lay);
+        for (int i = threadIdx.x; i < a.n_tiles * a.tl_stride / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    const int n_warps_cta = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < n_warps_cta * 32 * XS; i += blockDim.x) s_x[i] = 0.0f;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* xw = s_x + (size_t)wib * 32 * XS;  // this warp's block; row l belongs to lane l in phase 1
+    const SparseEntry* __restrict__ entries = reinterpret_cast<const SparseEntry*>(a.entries);
+    const int64_t n_units = (int64_t)a.n_tiles * n_ttiles;
+    bool bad_id = false, bad_off_seen = false;
+
+    for (;;) {
+        unsigned int unit = 0;
+        if (lane == 0) unit = atomicAdd(counter, 1u);
+        unit = __shfl_sync(FULL, unit, 0);
+        if ((int64_t)unit >= n_units) break;
+        const int tile = (int)((int64_t)unit / n_ttiles);
+        const int64_t t0 = ((int64_t)unit % n_ttiles) * trial_tile;
+        const int64_t t1 = min(t0 + (int64_t)trial_tile, y.n_trials);
+
+        int32_t jl[SLOTS];
+        float occ_r[SLOTS], occ_l[SLOTS];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            jl[s] = a.slot_layer[(tile * SLOTS + s) * 32 + lane];
+            occ_r[s] = jl[s] >= 0 ? a.occ[2 * jl[s]] : 0.0f;
+            occ_l[s] = jl[s] >= 0 ? a.occ[2 * jl[s] + 1] : 0.0f;
+        }
+        const uint16_t* off = s_off + (size_t)tile * (a.pool_np + 1);
+        const uint8_t* lay = s_lay + (size_t)tile * a.tl_stride;
+        float* xr = xw + lane * XS;
+
+        for (int64_t t = t0; t < t1; ++t) {
+            int64_t b, e;
+            bool bad_off;
+            trial_range(y, t, b, e, bad_off);
+            bad_off_seen |= bad_off;
+            const int32_t* tid = y.ids + b;
+            const int32_t n = (int32_t)(e - b);
+            float hi[SLOTS], lo[SLOTS];
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) {
+                hi[s] = 0.0f;
+                lo[s] = 0.0f;
+            }
+            int32_t nid = lane < n ? ld_stream(tid + lane) : -1;
+            for (int32_t c0 = 0; c0 < n; c0 += 32) {
+                const int32_t id = nid;
+                // the next group's id is requested before this group's entries
+                nid = c0 + 32 + lane < n ? ld_stream(tid + c0 + 32 + lane) : -1;
+                const bool live = c0 + lane < n;
+                const bool ok = live && (unsigned)id < (unsigned)y.catalogue;
+                if (live && !ok) bad_id = true;
+                uint32_t p0 = 0, p1 = 0;
+                if (ok) {
+                    p0 = __ldg(a.ptr + id);
+                    p1 = __ldg(a.ptr + id + 1);
+                }
+                // phase 1: this lane's event into its own row
+                for (uint32_t k = p0; k < p1; ++k) {
+                    const SparseEntry en = entries[k];
+                    const float4 tm = s_terms[en.elt];
+                    const float f = fin_f32(en.loss, tm.x, tm.y, tm.z);
+                    const int q1 = off[en.elt + 1];
+                    for (int q = off[en.elt]; q < q1; ++q) xr[lay[q]] += f;
+                }
+                __syncwarp();
+                // phase 2: each lane folds its layers' sums, event by event in trial order
+                unsigned mask = __ballot_sync(FULL, p1 > p0);
+                while (mask) {
+                    const int ev = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    float* row = xw + ev * XS;
+#pragma unroll
+                    for (int s = 0; s < SLOTS; ++s) {
+                        const float x = row[lane + 32 * s];
+                        if (x != 0.0f) {
+                            row[lane + 32 * s] = 0.0f;
+                            const float o = xl_f32(x, occ_r[s], occ_l[s]);
+                            if (o > 0.0f) two_sum_acc(hi[s], lo[s], o);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) {
+                const int32_t j = jl[s];
+                if (j >= 0) {
+                    const double S = (double)hi[s] + (double)lo[s];
+                    const double ar = a.agg[2 * j], al = a.agg[2 * j + 1];
+                    const size_t w = (size_t)j * (size_t)y.n_trials + (size_t)t;
+                    ylt[w] = xl_f64(S, ar, al);
+                    if (branch) branch[w] = agg_branch(S, ar, al);
+                }
+            }
+        }
+    }
+    if (bad_id) atomicOr(flags + kFlagIdRange, 1);
+    if (bad_off_seen && lane == 0) atomicOr(flags + kFlagBadOffsets, 1);
+}
+
+template <int SLOTS>
+cudaError_t launch_scatter(art_portfolio* p, const SparseArgs& a, const YetArgs& y, double* ylt, uint8_t* branch,
+                           cudaStream_t s) {
+    auto kern = ylt_sparse_scatter_kernel<SLOTS>;
+    const size_t base = (size_t)a.pool_np * 16 + ((((size_t)a.n_tiles * (a.pool_np + 1) * 2) + 15) & ~(size_t)15) +
+                        (size_t)a.n_tiles * a.tl_stride;
+    const size_t per_warp = (size_t)32 * (32 * SLOTS + 1) * 4;
+    int warps = (p->cta_threads > 0 && p->cta_threads <= kSparseThreads) ? p->cta_threads / 32 : kSparseThreads / 32;
+    while (warps > 1 && base + warps * per_warp > 100 * 1024) --warps;  // at least two CTAs per SM
+    const size_t smem = base + warps * per_warp;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int threads = 32 * warps;
+    int per_sm = 0;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem))) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int32_t tt = p->trial_tile > 0 ? p->trial_tile : 4;
+    const int64_t n_ttiles = (y.n_trials + tt - 1) / tt;
+    if ((int64_t)a.n_tiles * n_ttiles >= 0xffffffffLL) return cudaErrorInvalidValue;
+    int64_t grid = (int64_t)p->num_sms * per_sm;
+    const int64_t units = (int64_t)a.n_tiles * n_ttiles;
+    grid = std::min<int64_t>(grid, (units + warps - 1) / warps);
+    if (grid < 1) grid = 1;
+    if ((err = cudaMemsetAsync(p->d_work_counter, 0, sizeof(unsigned int), s))) return err;
+    kern<<<(unsigned)grid, threads, smem, s>>>(a, y, tt, n_ttiles, p->d_work_counter, ylt, branch, p->d_flags);
+    return cudaGetLastError();
+}
+
+template <int SLOTS>
+__global__ void __launch_bounds__(kSparseThreads) ylt_sparse_bcast_kernel(const SparseArgs a, const YetArgs y,
                                                                    const int32_t trial_tile, const int64_t n_ttiles,
                                                                    unsigned int* __restrict__ counter,
                                                                    double* __restrict__ ylt,
@@ -157,9 +323,9 @@ __global__ void __launch_bounds__(kSparseThreads) ylt_sparse_kernel(const Sparse
 }
 
 template <int SLOTS>
-cudaError_t launch_slots(art_portfolio* p, const SparseArgs& a, const YetArgs& y, double* ylt, uint8_t* branch,
+cudaError_t launch_bcast(art_portfolio* p, const SparseArgs& a, const YetArgs& y, double* ylt, uint8_t* branch,
                          cudaStream_t s) {
-    auto kern = ylt_sparse_kernel<SLOTS>;
+    auto kern = ylt_sparse_bcast_kernel<SLOTS>;
     const size_t smem = (size_t)a.pool_np * sizeof(float4) + (size_t)a.n_tiles * a.pool_np * 32;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -177,6 +343,13 @@ cudaError_t launch_slots(art_portfolio* p, const SparseArgs& a, const YetArgs& y
     if ((err = cudaMemsetAsync(p->d_work_counter, 0, sizeof(unsigned int), s))) return err;
     kern<<<(unsigned)grid, threads, smem, s>>>(a, y, tt, n_ttiles, p->d_work_counter, ylt, branch, p->d_flags);
     return cudaGetLastError();
+}
+
+template <int SLOTS>
+cudaError_t launch_slots(art_portfolio* p, const SparseArgs& a, const YetArgs& y, double* ylt, uint8_t* branch,
+                         cudaStream_t s) {
+    const int mapping = p->sparse_mapping >= 0 ? p->sparse_mapping : (SLOTS == 2 ? 1 : 0);
+    return mapping == 1 ? launch_scatter<SLOTS>(p, a, y, ylt, branch, s) : launch_bcast<SLOTS>(p, a, y, ylt, branch, s);
 }
 
 // CSR build, pass 1: per event, the number of ELTs with a non-zero loss.
@@ -259,6 +432,9 @@ cudaError_t launch_sparse(art_portfolio* p, const YetArgs& y, double* ylt, uint8
     a.entries = p->sp_entries;
     a.elt_terms = p->d_elt_terms;
     a.memb = p->d_memb;
+    a.tl_off = p->d_tl_off;
+    a.tl_lay = p->d_tl_lay;
+    a.tl_stride = p->tl_stride;
     a.slot_layer = p->d_slot_layer;
     a.occ = p->d_occ;
     a.agg = p->d_agg;

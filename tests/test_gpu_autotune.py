@@ -48,8 +48,9 @@ def test_every_layer_tile_matches_the_oracle(tmp_path, monkeypatch, slots_varian
                               max_elts_per_layer=32, nnz_frac=0.08)
     ref, gross, _ = oracle.ylt(w.oracle_problem())
     v = {"batched": art.ART_VARIANT_BATCHED, "sparse": art.ART_VARIANT_SPARSE}[slots_variant]
-    for slots in (2, 4, 8):
-        cache = tmp_path / f"tune_{slots}.txt"
+    shapes = [(slots, m) for slots in (2, 4, 8) for m in ((0, 1) if slots_variant == "sparse" else (-1,))]
+    for slots, mapping in shapes:
+        cache = tmp_path / f"tune_{slots}_{mapping}.txt"
         monkeypatch.setenv("ART_AUTOTUNE_CACHE", str(cache))
         p = art.portfolio_from_workload(w)
         try:
@@ -59,13 +60,13 @@ def test_every_layer_tile_matches_the_oracle(tmp_path, monkeypatch, slots_varian
             r = art.art_autotune(p, T, ids, off, k, ylt, sample_trials=200)
             # rewrite the recorded shape with the forced tile and replay it
             key = cache.read_text().splitlines()[-1].split("\t")[0]
-            cache.write_text(f"{key}\t{v} {slots} 2 128\t0.0\n")
+            cache.write_text(f"{key}\t{v} {slots} 2 128 {mapping}\t0.0\n")
             r = art.art_autotune(p, T, ids, off, k, ylt, sample_trials=200)
-            assert r["from_cache"] == 1 and r["slots"] == slots and r["variant"] == v
+            assert r["from_cache"] == 1 and r["slots"] == slots and r["variant"] == v and r["mapping"] == mapping
             ylt.fill_(-1.0)
             art.art_run_ylt(p, T, ids, off, k, ylt)
             torch.cuda.synchronize()
             assert art.art_get_device_status(p) == art.ART_OK
-            assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"{slots_variant} slots {slots}")
+            assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"{slots_variant} slots {slots} mapping {mapping}")
         finally:
             p.close()
