@@ -128,9 +128,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {"ylt_plain": "ylt_plain.cu", "ylt_skip": "ylt_skip.cu", "ylt_batched": "ylt_batched.cu",
+                  "ylt_batched_fp64": "ylt_batched.cu", "ylt_sparse": "ylt_sparse.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the kernel's own source file and the shared device header."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1308_2572_gb300", "csrc"))):
+    for f in (KERNEL_SOURCES[kernel], "art_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1308_2572_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -147,7 +152,7 @@ def recorded_traffic(kernel: str, workload: str):
         return None
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    if not m or not h or h.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1))
 

@@ -174,7 +174,8 @@ ART_API art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t tr
  *
  *  n_trials           T >= 0 (0 is a no-op).
  *  event_ids_dev      int32 event ids. Dense: [T][K]. CSR: trial t is
- *                     event_ids_dev[off[t] .. off[t+1]).
+ *                     event_ids_dev[off[t] .. off[t+1]); must not be NULL for
+ *                     CSR input, even when every trial is empty.
  *  trial_off_dev      NULL for a dense YET, else [T+1] int64, off[0] = 0,
  *                     non-decreasing (checked on the device: a decreasing pair
  *                     is treated as an empty trial and flags ART_EINVAL via

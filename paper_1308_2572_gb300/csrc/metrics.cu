@@ -213,23 +213,29 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const double* __restrict
     }
 }
 
+// One warp per (layer, probability): the per-block partials summed by lane
+// stride, then a fixed shuffle tree (deterministic).
 __global__ void finalize_kernel(const SelState* __restrict__ st, int n_layers, int n_p, int nblk, int64_t n,
                                 const double* __restrict__ mean_part, const unsigned long long* __restrict__ tail_cnt,
                                 const double* __restrict__ tail_sum, double* mean, double* pml, double* tvar) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_layers * n_p) return;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n_layers * n_p) return;  // whole warp
     const int j = i / n_p, q = i % n_p;
-    if (q == 0 && mean) {
-        double m = 0.0;
-        for (int b = 0; b < nblk; ++b) m += mean_part[(size_t)j * nblk + b];
-        mean[j] = m / (double)n;
-    }
-    double sgt = 0.0;
+    double m = 0.0, sgt = 0.0;
     unsigned long long cgt = 0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = lane; b < nblk; b += 32) {
+        if (q == 0) m += mean_part[(size_t)j * nblk + b];
         sgt += tail_sum[(size_t)i * nblk + b];
         cgt += tail_cnt[(size_t)i * nblk + b];
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+        sgt += __shfl_xor_sync(0xffffffffu, sgt, o);
+        cgt += __shfl_xor_sync(0xffffffffu, cgt, o);
+    }
+    if (lane != 0) return;
+    if (q == 0 && mean) mean[j] = m / (double)n;
     const double v = __longlong_as_double((long long)st[i].prefix);
     const long long k = st[i].k;
     if (pml) pml[i] = v;
@@ -382,8 +388,8 @@ cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const do
         if (err) break;
         tail_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_p, st, tcnt, tsum);
         if ((err = cudaGetLastError())) break;
-        finalize_kernel<<<(n_prob + 127) / 128, 128, 0, s>>>(st, n_layers, n_p, nblk, n, msum, tcnt, tsum, mean,
-                                                             pml, tvar);
+        finalize_kernel<<<(n_prob + 3) / 4, 128, 0, s>>>(st, n_layers, n_p, nblk, n, msum, tcnt, tsum, mean, pml,
+                                                         tvar);
         err = cudaGetLastError();
     } while (0);
     const cudaError_t e2 = cudaFreeAsync(w, s);
@@ -517,7 +523,7 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
         if (err) break;
         tail_kernel<<<dim3(nblk, n_layers), kThreads, 0, stream>>>(ylt_dev, n_trials, n_p, st, tcnt, tsum);
         if ((err = cudaGetLastError())) break;
-        finalize_kernel<<<(n_prob + 127) / 128, 128, 0, stream>>>(st, n_layers, n_p, nblk, n_trials, msum, tcnt, tsum,
+        finalize_kernel<<<(n_prob + 3) / 4, 128, 0, stream>>>(st, n_layers, n_p, nblk, n_trials, msum, tcnt, tsum,
                                                                   mean_dev, pml_dev, tvar_dev);
         err = cudaGetLastError();
     } while (0);

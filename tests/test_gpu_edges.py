@@ -1,0 +1,102 @@
+"""Degenerate and edge inputs through every forward variant and the metrics:
+no events, no trials, no losses, one event, a catalogue that is not a
+multiple of 32, repeated runs (determinism of the metrics)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1308_2572_gb300 import art, workloads
+
+from gpu_util import assert_ylt_close, device_yet, gpu_metrics
+
+pytestmark = pytest.mark.gpu
+
+ALL = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_POOL64 | art.ART_LAYOUT_GROUP
+       | art.ART_LAYOUT_SPARSE)
+VARIANTS = [art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_FP64, art.ART_VARIANT_SKIP,
+            art.ART_VARIANT_SPARSE]
+
+
+def _run_all(w):
+    ref, gross, _ = oracle.ylt(w.oracle_problem())
+    p = art.portfolio_from_workload(w, layouts=ALL)
+    try:
+        ids, off, k, T = device_yet(w)
+        L = w.portfolio.n_layers
+        for v in VARIANTS:
+            art.art_set_variant(p, v)
+            y = torch.full((L, T), -5.0, dtype=torch.float64, device="cuda")
+            art.art_run_ylt(p, T, ids, off, k, y)
+            torch.cuda.synchronize()
+            assert art.art_get_device_status(p) == art.ART_OK
+            assert_ylt_close(y.cpu().numpy(), ref, gross, f"variant {v}")
+    finally:
+        p.close()
+    return ref
+
+
+def test_dense_trials_without_events():
+    w = workloads.random_case(501, n_trials=100, dense_k=0)
+    ref = _run_all(w)
+    assert np.all(ref == 0)
+
+
+def test_all_trials_empty_csr():
+    """A CSR YET whose trials are all empty: the ABI wants a non-NULL id
+    pointer for CSR input (it cannot read the offsets on the host), so one
+    unused id stands behind it."""
+    w = workloads.random_case(502, n_trials=64, min_len=0, max_len=0)
+    assert w.yet.n_events == 0
+    w = workloads.Workload(w.name, w.portfolio,
+                           workloads.YET(w.yet.n_trials, np.zeros(1, np.int32), 0, w.yet.trial_off), w.probs)
+    ref = _run_all(w)
+    assert np.all(ref == 0)
+
+
+def test_catalogue_not_a_multiple_of_32_and_ids_at_the_ends():
+    w = workloads.random_case(503, catalogue=1037, n_trials=200, dense_k=40)
+    ids = w.yet.event_ids.copy()
+    ids[::7] = 1036       # last catalogue entry
+    ids[3::11] = 0        # first
+    w = workloads.Workload(w.name, w.portfolio, workloads.YET(w.yet.n_trials, ids, 40), w.probs)
+    _run_all(w)
+
+
+def test_no_losses_at_all_gives_zero():
+    w = workloads.random_case(504, n_trials=50, dense_k=30)
+    w.portfolio.elt_losses[:] = 0.0
+    ref = _run_all(w)
+    assert np.all(ref == 0)
+
+
+def test_zero_trials_is_a_noop():
+    w = workloads.random_case(505, n_trials=10, dense_k=5)
+    p = art.portfolio_from_workload(w)
+    try:
+        ids, off, k, T = device_yet(w)
+        y = torch.full((w.portfolio.n_layers, 1), 3.0, dtype=torch.float64, device="cuda")
+        art.art_run_ylt(p, 0, ids, None, 5, y)
+        torch.cuda.synchronize()
+        assert torch.all(y == 3.0)
+    finally:
+        p.close()
+
+
+def test_metrics_edges_and_determinism():
+    g = torch.Generator(device="cpu").manual_seed(3)
+    cases = [torch.zeros((2, 1), dtype=torch.float64),                         # one trial
+             torch.full((3, 4097), 7.5, dtype=torch.float64),                  # all tied
+             torch.rand((1, 123457), generator=g, dtype=torch.float64) * 1e9,  # ragged size
+             torch.tensor([[0.0, -0.0, 1.0, 5e-324, 1e300, 2.0]], dtype=torch.float64)]  # signed zero, subnormal
+    for y in cases:
+        yd = y.cuda().contiguous()
+        probs = [0.5, 0.9, 0.99, 0.999999]
+        a = gpu_metrics(yd, probs)
+        b = gpu_metrics(yd, probs)
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v)  # bitwise repeatable
+        om, op, ot = oracle.metrics(np.abs(y.numpy()), probs)
+        np.testing.assert_array_equal(a[1], op)
+        np.testing.assert_allclose(a[2], ot, rtol=1e-12)
+        np.testing.assert_allclose(a[0], om, rtol=1e-12)
