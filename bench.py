@@ -41,6 +41,8 @@ CONFIG_TEXT = {
     "c0": "10,000 trials x 1,000 events, catalogue 100,000, 1 layer x 3 ELTs",
     "c2": "1,000,000 trials of clamp(Poisson(1000),200,2000) events (CSR), 64 layers x U{1..32} ELTs from a pool of 256",
     "c4": "1,000,000 trials x 1,000 events, 128 layers x U{4..32} ELTs from a pool of 512, lognormal(13,2.5)",
+    "c3": "c1's YET and 16 ELTs, 8 layers of 8 ELTs; step = forward + EL/TVaR_0.99 + their gradients w.r.t. "
+          "OccR, OccL, AggR, AggL and the 16 ELT multipliers (adjoint)",
 }
 
 
@@ -294,6 +296,8 @@ def main():
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probes", action="store_true", help="skip the libart bandwidth probes")
+    ap.add_argument("--l2-persist", action="store_true",
+                    help="persisting L2 access-policy window over the hot table (ART_FLAG_L2_PERSIST)")
     ap.add_argument("--trials", type=int, default=0,
                     help="keep only the first N trials (small cases for profiling; 0 = the full workload)")
     args = ap.parse_args()
@@ -321,7 +325,10 @@ def main():
     layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_GROUP, "batched": art.ART_LAYOUT_POOL,
                "fp64": art.ART_LAYOUT_POOL64, "sparse": art.ART_LAYOUT_SPARSE}.get(
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
-    p = art.portfolio_from_workload(w, device=dev, layouts=layouts)
+    if args.config == "c3":
+        layouts |= art.ART_LAYOUT_LAYER  # the adjoint reads the per-layer tables
+    p = art.portfolio_from_workload(w, device=dev, layouts=layouts,
+                                    flags=art.ART_FLAG_L2_PERSIST if args.l2_persist else 0)
     ids = torch.from_numpy(yet.event_ids).to(dev)
     off = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).to(dev)
     ylt = torch.empty((L, T), dtype=torch.float64, device=dev)
@@ -334,9 +341,22 @@ def main():
     vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64,
             "skip": art.ART_VARIANT_SKIP, "sparse": art.ART_VARIANT_SPARSE}
 
+    # the differentiation workload (c3) steps forward and backward: branch
+    # codes in the forward, then dLoss/dYLT for sum(EL + TVaR) and the adjoint
+    with_grad = args.config == "c3"
+    branch = torch.empty((L, T), dtype=torch.uint8, device=dev) if with_grad else None
+    gylt = torch.empty_like(ylt) if with_grad else None
+    ones_l = torch.ones(L, dtype=torch.float64, device=dev)
+    ones_lp = torch.ones((L, n_p), dtype=torch.float64, device=dev)
+    gterms = torch.empty((L, 4), dtype=torch.float64, device=dev)
+    gmult = torch.empty(port.n_elt, dtype=torch.float64, device=dev)
+
     def step():
-        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        art.art_run_ylt(p, T, ids, off, K, ylt, branch, stream)
         art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+        if with_grad:
+            art.art_metrics_backward(ylt, T, L, probs, pml, ones_l, ones_lp, gylt, stream)
+            art.art_run_ylt_backward(p, T, ids, off, K, branch, gylt, gterms, gmult, stream)
 
     # variant choice: time each candidate forward (untimed for the result)
     cands = [args.variant] if args.variant != "auto" else ["plain", "batched", "skip", "sparse"]
@@ -379,9 +399,12 @@ def main():
     start.record(stream)
     for i in range(args.steps):
         ev[i][0].record(stream)
-        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        art.art_run_ylt(p, T, ids, off, K, ylt, branch, stream)
         ev[i][1].record(stream)
         art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+        if with_grad:
+            art.art_metrics_backward(ylt, T, L, probs, pml, ones_l, ones_lp, gylt, stream)
+            art.art_run_ylt_backward(p, T, ids, off, K, branch, gylt, gterms, gmult, stream)
     end.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
@@ -474,6 +497,8 @@ def main():
     # (histogram + select), tail sums, finalize)
     n_groups = len(layer_groups(port))
     launches = {"plain": L, "skip": n_groups}.get(variant, 1) + 15
+    if with_grad:
+        launches += 3 + 2 * L + 1  # metrics backward (count, weights, grad) + per layer adjoint and reduce + scatter
     if rank == 0:
         line = {
             "metric": "trial-events x ELTs per second", "value": value, "unit": "trial-events*ELTs/s",
@@ -481,7 +506,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
-                       "variant": variant, "autotune": tune, "layers": L, "trials": T, "events": yet.n_events,
+                       "variant": variant, "autotune": tune, "l2_persist": bool(args.l2_persist), "layers": L, "trials": T, "events": yet.n_events,
                        "lookups_per_step": lookups,
                        "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
                        "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"},

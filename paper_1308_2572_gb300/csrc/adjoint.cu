@@ -14,9 +14,13 @@
 // order, same occurrence subtraction), so they match the forward bit for bit.
 //
 // Mapping: the plain forward's (warp per trial, lane per event), over a
-// persistent grid with a static trial stride; each lane accumulates its
-// weighted indicator sums in FP64 registers over all trials it visits, and
-// the sums are reduced warp -> CTA -> grid in a fixed order (deterministic).
+// persistent grid with a static trial stride. Within a trial each lane counts
+// its events on the middle and capped occurrence branches (integers) and sums
+// the losses l of each ELT's middle-branch events as a compensated FP32 pair
+// (two-sum, exact to second order); at the end of the trial these are scaled
+// by the trial's weight g into FP64 accumulators, so FP64 arithmetic runs per
+// trial, not per event (the FP64 pipe of this part is slow). The FP64 sums
+// are reduced warp -> CTA -> grid in a fixed order (deterministic).
 #include <limits>
 
 #include "art_internal.cuh"
@@ -26,6 +30,13 @@ namespace art {
 namespace {
 
 constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ void two_sum_add(float& s, float& e, float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    e += (s - (t - bp)) + (v - bp);
+    s = t;
+}
 
 template <int NP, int U>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const LayerArgs la, const YetArgs y,
@@ -57,6 +68,13 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const LayerArgs la
         int64_t b, e;
         bool bad_off;
         trial_range(y, t, b, e, bad_off);
+        int n_mid = 0, n_cap = 0;
+        float mh[NP], ml[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            mh[k] = 0.0f;
+            ml[k] = 0.0f;
+        }
         for (int64_t d0 = b; d0 < e; d0 += 32 * U) {
             int32_t id[U];
             bool live[U];
@@ -90,17 +108,22 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const LayerArgs la
                 const float wo = x - la.occ_ret;  // the forward's occurrence subtraction
                 const bool mid = wo > 0.0f && wo < la.occ_lim;
                 const bool cap = wo > la.occ_lim;
-                if (cap) acc_ol += gt;
+                n_cap += cap ? 1 : 0;
                 if (mid) {
-                    acc_or -= gt;
+                    ++n_mid;
 #pragma unroll
                     for (int k = 0; k < NP; ++k) {
                         const float wf = __fmaf_rn(la.m[k], v[k], -la.d[k]);
-                        if (wf > 0.0f && wf < la.lim[k]) acc_m[k] += gt * (double)v[k];
+                        if (wf > 0.0f && wf < la.lim[k]) two_sum_add(mh[k], ml[k], v[k]);
                     }
                 }
             }
         }
+        // once per trial: the lane's counts and sums, weighted by g, in FP64
+        acc_or -= gt * (double)n_mid;
+        acc_ol += gt * (double)n_cap;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) acc_m[k] += gt * ((double)mh[k] + (double)ml[k]);
     }
     // warp -> CTA -> grid partial, fixed order
     double vals[W];

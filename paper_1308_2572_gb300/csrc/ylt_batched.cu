@@ -243,7 +243,7 @@ static cudaError_t launch_cfg(art_portfolio* p, const BatchedArgs& a, const YetA
 template <typename V, int EPL>
 static cudaError_t launch_slots(art_portfolio* p, const BatchedArgs& a, const YetArgs& y, double* ylt,
                                 uint8_t* branch, cudaStream_t s) {
-    constexpr int U = sizeof(V) == 4 ? (EPL <= 8 ? 4 : 2) : (EPL <= 4 ? 4 : (EPL == 8 ? 2 : 1));
+    constexpr int U = sizeof(V) == 4 ? (EPL <= 8 ? 4 : 2) : (EPL <= 4 ? 4 : 2);
     switch (a.slots) {
         case 2: return launch_cfg<V, EPL, 2, U>(p, a, y, ylt, branch, s);
         case 4: return launch_cfg<V, EPL, 4, U>(p, a, y, ylt, branch, s);
