@@ -25,6 +25,13 @@
  *    limits may be +INFINITY (an unlimited cover).
  *  - No entry point waits on other CTAs or other GPUs; there are no spin
  *    waits in any kernel of this library.
+ *  - A portfolio belongs to the device that was current when it was created;
+ *    call the entry points that take it with that device current. A
+ *    portfolio is not thread-safe (its graph cache, staging buffers and work
+ *    counter are shared): use it from one host thread at a time, and order
+ *    run calls that share it on one stream (they share the work counter).
+ *  - Results are deterministic: the same inputs, variant and tile shape give
+ *    bitwise-equal outputs (no atomics take part in any sum).
  */
 #ifndef ART_H
 #define ART_H
