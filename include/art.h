@@ -309,13 +309,24 @@ ART_API art_status art_metrics_backward(const double* ylt_dev, int64_t n_trials,
  *   dG/dm_e    =  sum_j sum_t g a sum_d [o_d mid][D_e < m_e l < D_e + Lim_e] l,
  * with a = [branch == 1], c = [branch == 2] and l = l_e[E_{t,d}]; at a kink
  * the strict-inequality branch is taken. Trials whose branch is not 1 are not
- * re-read. The per-event branches are recomputed in the forward's FP32
- * arithmetic; sums are FP64 and deterministic.
+ * re-read. The per-event branches are recomputed in FP32 as the forward
+ * forms them; the results are deterministic.
+ * With the ART_LAYOUT_GROUP tables the YET is read once per layer group and
+ * only events with a loss in the group are evaluated; the per-event sums then
+ * follow the group table's ELT order (as the skip variant forms them) and the
+ * multiplier sums weight each event by g rounded to FP32, with compensated
+ * FP32 accumulation (relative error of order 1e-7). Without them, the
+ * ART_LAYOUT_LAYER tables are read once per layer in the layer's ELT order
+ * (as the plain variant forms them) and g is applied in FP64 per trial.
+ * An event whose per-event sum differs between the forward variant used and
+ * this order can fall on the other side of an occurrence kink only when it
+ * lies within FP32 rounding of that kink.
  *  branch_dev        [n_layers][T] from art_run_ylt on the same YET and terms.
  *  grad_ylt_dev      [n_layers][T] FP64.
  *  grad_terms_dev    [n_layers][4] FP64 output (OccR, OccL, AggR, AggL).
  *  grad_mult_dev     [n_elt] FP64 output.
- * Needs the ART_LAYOUT_LAYER tables. Scratch from the stream-ordered allocator.
+ * Needs ART_LAYOUT_GROUP or ART_LAYOUT_LAYER (else ART_EUNSUPPORTED). Scratch
+ * from the stream-ordered allocator.
  */
 ART_API art_status art_run_ylt_backward(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
                                 const int64_t* trial_off_dev, int32_t events_per_trial,

@@ -288,6 +288,7 @@ void refresh_group_terms(art_portfolio* p) {
                 for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
                     mem |= 1u << (std::find(el.begin(), el.end(), p->lids[c]) - el.begin());
             g.member[s] = mem;
+            for (int k = 0; k < kMaxLayerElts; ++k) g.coef[s][k] = ((mem >> k) & 1u) ? 1.0f : 0.0f;
             g.occ_ret[s] = real ? p->occ_ret[j] : 0.0f;
             g.occ_lim[s] = real ? p->occ_lim[j] : 0.0f;
             g.agg_ret[s] = real ? p->agg_ret[j] : 0.0;
@@ -819,9 +820,13 @@ art_status art_run_ylt_backward(art_portfolio* p, int64_t n_trials, const int32_
     art_status st = validate_yet(n_trials, event_ids_dev, trial_off_dev, events_per_trial);
     if (st) return st;
     if (!grad_terms_dev || !grad_mult_dev || (n_trials > 0 && (!branch_dev || !grad_ylt_dev))) return ART_EINVAL;
-    if (!(p->layouts & ART_LAYOUT_LAYER)) return ART_EUNSUPPORTED;
+    if (!(p->layouts & (ART_LAYOUT_GROUP | ART_LAYOUT_LAYER))) return ART_EUNSUPPORTED;
     YetArgs y{event_ids_dev, trial_off_dev, n_trials, trial_off_dev ? 0 : events_per_trial, p->catalogue};
-    const cudaError_t e = launch_adjoint(p, y, branch_dev, grad_ylt_dev, grad_terms_dev, grad_mult_dev, stream);
+    // one pass per layer group where the group tables exist, else one per layer
+    const cudaError_t e =
+        (p->layouts & ART_LAYOUT_GROUP)
+            ? launch_adjoint_groups(p, y, branch_dev, grad_ylt_dev, grad_terms_dev, grad_mult_dev, stream)
+            : launch_adjoint(p, y, branch_dev, grad_ylt_dev, grad_terms_dev, grad_mult_dev, stream);
     return e ? fail(e) : ART_OK;
 }
 

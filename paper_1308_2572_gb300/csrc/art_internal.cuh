@@ -127,6 +127,10 @@ struct GroupArgs {
     float d[kMaxLayerElts];
     float lim[kMaxLayerElts];
     uint32_t member[kMaxGroupLayers];  // bit k: the group's ELT k belongs to the layer
+    // the same membership as 0/1 coefficients: a layer's ELT sum is a chain of
+    // FMAs x = fma(c, f, x), which rounds exactly as x + f (c = 1) or leaves x
+    // unchanged (c = 0, f finite), with c a constant operand
+    float coef[kMaxGroupLayers][kMaxLayerElts];
     float occ_ret[kMaxGroupLayers], occ_lim[kMaxGroupLayers];
     double agg_ret[kMaxGroupLayers], agg_lim[kMaxGroupLayers];
     int32_t layer[kMaxGroupLayers];
@@ -220,6 +224,8 @@ cudaError_t launch_batched(art_portfolio* p, const YetArgs& y, double* ylt, uint
                            cudaStream_t s);
 cudaError_t launch_adjoint(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,
                            double* grad_terms, double* grad_mult, cudaStream_t s);
+cudaError_t launch_adjoint_groups(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,
+                                  double* grad_terms, double* grad_mult, cudaStream_t s);
 cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
                         double* mean, double* pml, double* tvar, cudaStream_t s);
 cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs,

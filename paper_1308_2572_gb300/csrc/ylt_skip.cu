@@ -92,8 +92,10 @@ __device__ __forceinline__ void eval_event(const GroupArgs& g, int32_t id, float
         float x = 0.0f;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            // a one-layer group covers every real column; padding columns add 0
-            if (LT == 1 || (g.member[j] & (1u << k))) x += f[k];
+            // a one-layer group covers every real column (padding columns add
+            // 0); otherwise the 0/1 coefficient selects the layer's columns
+            if constexpr (LT == 1) x += f[k];
+            else x = __fmaf_rn(g.coef[j][k], f[k], x);
         }
         const float o = xl_f32(x, g.occ_ret[j], g.occ_lim[j]);
         if (o > 0.0f) two_sum_acc(hi[j], lo[j], o);

@@ -22,10 +22,15 @@ N_TRIALS = 10_000
 PROB = 0.99
 
 
-@pytest.fixture(scope="module")
-def c3():
+# the adjoint reads the group tables when they exist (one pass per layer
+# group), else the per-layer tables (one pass per layer): both are checked
+LAYOUTS = {"group": art.ART_LAYOUT_LAYER | art.ART_LAYOUT_GROUP, "layer": art.ART_LAYOUT_LAYER}
+
+
+@pytest.fixture(scope="module", params=sorted(LAYOUTS))
+def c3(request):
     w = workloads.make("c3", n_trials=N_TRIALS)
-    p = art.portfolio_from_workload(w)
+    p = art.portfolio_from_workload(w, layouts=LAYOUTS[request.param])
     yet = device_yet(w)
     yield w, p, yet
     p.close()
@@ -164,3 +169,65 @@ def test_autograd_function(c3):
     for c in range(4):
         np.testing.assert_allclose(params[c].grad.numpy(), gt[:, c], rtol=1e-12, atol=0)
     np.testing.assert_allclose(mult.grad.numpy(), gm, rtol=1e-12, atol=0)
+
+
+def _adjoint(p, yet, br, g, L, n_elt):
+    ids, off, K, T = yet
+    gt = torch.empty((L, 4), dtype=torch.float64, device="cuda")
+    gm = torch.empty(n_elt, dtype=torch.float64, device="cuda")
+    art.art_run_ylt_backward(p, T, ids, off, K, br, g, gt, gm)
+    torch.cuda.synchronize()
+    return gt.cpu().numpy(), gm.cpu().numpy()
+
+
+def test_group_adjoint_many_groups_matches_layer_adjoint_and_oracle():
+    """Several layer groups sharing ELTs (a multiplier's gradient sums over
+    groups), ragged trials, random weights: the group adjoint against the
+    per-layer adjoint (same branch codes) and against the oracle."""
+    w = workloads.random_case(601, catalogue=3001, n_elt=40, n_layers=30, n_trials=4000, max_len=100,
+                              max_elts_per_layer=12, mult_range=(0.8, 1.25))
+    L, E, T = w.portfolio.n_layers, w.portfolio.n_elt, w.yet.n_trials
+    pg = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_GROUP | art.ART_LAYOUT_LAYER)
+    pl = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_LAYER)
+    try:
+        yet = device_yet(w)
+        ids, off, K, _ = yet
+        rng = np.random.Generator(np.random.PCG64(602))
+        g_host = rng.uniform(0.0, 2.0, size=(L, T)) / T
+        g_host[:, ::7] = 0.0  # trials without weight are skipped
+        g = torch.from_numpy(g_host).cuda()
+        ylt = torch.empty((L, T), dtype=torch.float64, device="cuda")
+        br = torch.empty((L, T), dtype=torch.uint8, device="cuda")
+        art.art_set_variant(pl, art.ART_VARIANT_PLAIN)
+        art.art_run_ylt(pl, T, ids, off, K, ylt, br)
+        assert len({int(x) for x in np.unique(br.cpu().numpy())}) == 3
+        gt_g, gm_g = _adjoint(pg, yet, br, g, L, E)
+        gt_l, gm_l = _adjoint(pl, yet, br, g, L, E)
+        np.testing.assert_allclose(gt_g, gt_l, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(gm_g, gm_l, rtol=2e-6, atol=1e-9 * np.abs(gm_l).max())
+        ot, om, _, _ = oracle.grad(w.oracle_problem(), g_host)
+        np.testing.assert_allclose(gt_g, ot, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(gm_g, om, rtol=2e-6, atol=1e-9 * np.abs(om).max())
+        # deterministic: a second run gives the same bits
+        gt2, gm2 = _adjoint(pg, yet, br, g, L, E)
+        assert np.array_equal(gt2, gt_g) and np.array_equal(gm2, gm_g)
+    finally:
+        pg.close()
+        pl.close()
+
+
+def test_backward_needs_group_or_layer_tables():
+    w = workloads.random_case(603, n_trials=20)
+    p = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_POOL)
+    try:
+        ids, off, K, T = device_yet(w)
+        L, E = w.portfolio.n_layers, w.portfolio.n_elt
+        br = torch.zeros((L, T), dtype=torch.uint8, device="cuda")
+        g = torch.zeros((L, T), dtype=torch.float64, device="cuda")
+        gt = torch.empty((L, 4), dtype=torch.float64, device="cuda")
+        gm = torch.empty(E, dtype=torch.float64, device="cuda")
+        with pytest.raises(art.ArtError) as ei:
+            art.art_run_ylt_backward(p, T, ids, off, K, br, g, gt, gm)
+        assert ei.value.status == art.ART_EUNSUPPORTED
+    finally:
+        p.close()
