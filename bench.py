@@ -159,20 +159,44 @@ def recorded_traffic(kernel: str, workload: str):
     return float(m.group(1))
 
 
-def layer_groups(port):
+def layer_groups(port, with_layers: bool = False):
     """The library's layer groups (consecutive layers while a group has at
-    most 8 layers and at most 32 distinct ELTs), as ELT-id lists."""
-    groups, uni, n = [], [], 0
+    most 8 layers and at most 32 distinct ELTs), as ELT-id lists (with
+    with_layers, as (ELT ids, layer ids) pairs)."""
+    groups, uni, lay = [], [], []
     for j in range(port.n_layers):
         elts = [int(e) for e in port.layer_elt_ids[port.layer_elt_off[j]:port.layer_elt_off[j + 1]]]
         merged = uni + [e for e in elts if e not in uni]
-        if n and (n >= 8 or len(merged) > 32):
-            groups.append(uni)
-            uni, n, merged = [], 0, list(elts)
-        uni, n = merged, n + 1
-    if n:
-        groups.append(uni)
-    return groups
+        if lay and (len(lay) >= 8 or len(merged) > 32):
+            groups.append((uni, lay))
+            uni, lay, merged = [], [], list(elts)
+        uni, lay = merged, lay + [j]
+    if lay:
+        groups.append((uni, lay))
+    return groups if with_layers else [g for g, _ in groups]
+
+
+def occurrence_density(port, layers) -> float:
+    """Fraction of catalogue events with a positive occurrence loss in any of
+    the given layers (the density of the skip variant's per-call bitmap).
+    Accounting only: FP64 on the host."""
+    rows = None
+    for j in layers:
+        e = port.layer_elt_ids[port.layer_elt_off[j]:port.layer_elt_off[j + 1]]
+        nz = np.any(port.elt_losses[e] != 0, axis=0)
+        rows = nz if rows is None else (rows | nz)
+    idx = np.nonzero(rows)[0]
+    hit = np.zeros(idx.size, dtype=bool)
+    for j in layers:
+        if not port.occ_lim[j] > 0:
+            continue
+        e = port.layer_elt_ids[port.layer_elt_off[j]:port.layer_elt_off[j + 1]]
+        x = np.zeros(idx.size)
+        for k in e:
+            l = port.elt_losses[k, idx].astype(np.float64)
+            x += np.clip(float(port.elt_mult[k]) * l - float(port.elt_ded[k]), 0.0, float(port.elt_lim[k]))
+        hit |= x > float(port.occ_ret[j])
+    return float(hit.sum()) / port.catalogue_size
 
 
 def algorithmic_bytes(w, variant: str):
@@ -181,8 +205,10 @@ def algorithmic_bytes(w, variant: str):
     s8d: the per-unit figure -- 4 B per event id (plus 8 B per CSR offset)
       and the 32-byte sectors every table read touches (32 * ceil(row / 32)
       per row read; 32 B of offsets plus 8 B per entry for the CSR), plus the
-      YLT written. The tables here (128 MB to 8 GB) do not fit the 126 MB L2
-      next to the id stream, so these count against HBM.
+      YLT written; for the skip variant, the rows read are those of the
+      per-call occurrence-loss table, plus its build pass (group table read
+      once, table and bitmap written). The tables here (128 MB to 8 GB) do
+      not fit the 126 MB L2 next to the id stream, so these count against HBM.
     compulsory: ids, offsets and YLT once, plus every distinct row a pass can
       touch read once (the least DRAM traffic the pass can have).
     l2: the id stream plus the sectors the table reads touch (L2 traffic).
@@ -196,15 +222,18 @@ def algorithmic_bytes(w, variant: str):
     sec = lambda nbytes: 32 * -(-nbytes // 32)
     pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
     if variant == "skip":
-        reads, table = 0.0, 0.0
-        for g in layer_groups(port):
-            rowb = 4 * pad(len(g))
-            nz = np.any(port.elt_losses[g] != 0, axis=0)
-            reads += n_events * float(nz.mean()) * sec(rowb)
-            table += float(nz.sum()) * rowb + C / 8
-        n_groups = len(layer_groups(port))
-        return {"s8d": n_groups * ids + ylt + reads, "compulsory": n_groups * ids + ylt + table * touched_frac,
-                "l2": n_groups * ids + reads}
+        # per group: one streamed pass over the group table that writes the
+        # occurrence-loss table X [C][LP] and its bitmap, then per event an id
+        # and, where X is non-zero, one sector of X
+        reads, build = 0.0, 0.0
+        groups = layer_groups(port, with_layers=True)
+        for elts, lays in groups:
+            lp = 1 if len(lays) <= 1 else (2 if len(lays) <= 2 else (4 if len(lays) <= 4 else 8))
+            reads += n_events * occurrence_density(port, lays) * sec(4 * lp)
+            build += C * 4 * pad(len(elts)) + C * 4 * lp + C / 8
+        n_groups = len(groups)
+        return {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
+                "l2": n_groups * ids + build + reads}
     if variant == "sparse":
         nnz_per_event = float((port.elt_losses != 0).sum(axis=0).mean())
         csr = 4 * (C + 1) + 8 * float((port.elt_losses != 0).sum())
@@ -493,12 +522,16 @@ def main():
         cpu = cpu_baseline(args, w)
 
     # kernels of ours launched per step: forward (one per layer for the plain
+    # variant, occurrence-table build + trial pass per group for the skip
     # variant, one persistent launch otherwise) + metrics (state init, 6 x
     # (histogram + select), tail sums, finalize)
     n_groups = len(layer_groups(port))
-    launches = {"plain": L, "skip": n_groups}.get(variant, 1) + 15
+    launches = {"plain": L, "skip": 2 * n_groups}.get(variant, 1) + 15
     if with_grad:
-        launches += 3 + 2 * L + 1  # metrics backward (count, weights, grad) + per layer adjoint and reduce + scatter
+        # metrics backward (count, weights, grad) + the adjoint: per group a
+        # pass and its reduction (group tables), else per layer a pass and its
+        # reduction plus one scatter
+        launches += 3 + (2 * n_groups if layouts & art.ART_LAYOUT_GROUP else 2 * L + 1)
     if rank == 0:
         line = {
             "metric": "trial-events x ELTs per second", "value": value, "unit": "trial-events*ELTs/s",

@@ -305,6 +305,8 @@ cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t str
     p->group_np.assign(ng, 0);
     p->group_tab.assign(ng, nullptr);
     p->group_bitmap.assign(ng, nullptr);
+    p->group_occ.assign(ng, nullptr);
+    p->group_occ_bits.assign(ng, nullptr);
     int32_t* d_el = nullptr;
     cudaError_t e = cudaMalloc(&d_el, sizeof(int32_t) * kMaxLayerElts * ng);
     if (e) return e;
@@ -316,7 +318,15 @@ cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t str
         const size_t bb = sizeof(uint32_t) * (((size_t)p->catalogue + 31) / 32);
         if ((e = cudaMalloc(&p->group_tab[gi], tb))) break;
         if ((e = cudaMalloc(&p->group_bitmap[gi], bb))) break;
-        p->group_bytes += (int64_t)(tb + bb);
+        const int nl = (int)p->group_layers[gi].size();
+        const int lt_pad = nl <= 1 ? 1 : nl <= 2 ? 2 : nl <= 4 ? 4 : 8;
+        const size_t ob = sizeof(float) * (size_t)p->catalogue * lt_pad;
+        if ((e = cudaMalloc(&p->group_occ[gi], ob))) break;
+        if ((e = cudaMalloc(&p->group_occ_bits[gi], bb))) break;
+        p->group_bytes += (int64_t)(tb + bb + ob + bb);
+        p->groups[gi].occ = p->group_occ[gi];
+        p->groups[gi].occ_bits = p->group_occ_bits[gi];
+        p->groups[gi].lt_pad = lt_pad;
         if ((e = cudaMemcpyAsync(d_el + gi * kMaxLayerElts, el.data(), sizeof(int32_t) * el.size(),
                                  cudaMemcpyHostToDevice, stream)))
             break;
@@ -355,6 +365,8 @@ void free_portfolio(art_portfolio* p) {
     for (float* t : p->layer_tab) cudaFree(t);
     for (float* t : p->group_tab) cudaFree(t);
     for (uint32_t* b : p->group_bitmap) cudaFree(b);
+    for (float* t : p->group_occ) cudaFree(t);
+    for (uint32_t* b : p->group_occ_bits) cudaFree(b);
     cudaFree(p->pool);
     cudaFree(p->pool64);
     cudaFree(p->d_elt_terms);

@@ -123,6 +123,12 @@ constexpr int kMaxGroupLayers = 8;
 struct GroupArgs {
     const float* table;       // [C][np] FP32 over the group's ELTs (union order)
     const uint32_t* bitmap;   // [ceil(C / 32)]: bit i set if row i is not all zero
+    // per-call occurrence-loss table of the forward: X[i][j] = O_j(x_ij) for
+    // the group's layers j (padded to lt_pad columns), and its bitmap (bit i
+    // set if any X[i][j] > 0); written by the forward before its trial pass
+    float* occ;               // [C][lt_pad] FP32
+    uint32_t* occ_bits;       // [ceil(C / 32)]
+    int32_t lt_pad;           // 1, 2, 4 or 8
     float m[kMaxLayerElts];   // terms of the group's ELTs (padding: 1, 0, inf)
     float d[kMaxLayerElts];
     float lim[kMaxLayerElts];
@@ -170,6 +176,8 @@ struct art_portfolio {
     std::vector<std::vector<int32_t>> group_layers; // layer ids per group
     std::vector<float*> group_tab;
     std::vector<uint32_t*> group_bitmap;
+    std::vector<float*> group_occ;            // occurrence-loss tables
+    std::vector<uint32_t*> group_occ_bits;
     int64_t group_bytes = 0;
 
     // ART_LAYOUT_SPARSE: event-major CSR of the non-zero losses

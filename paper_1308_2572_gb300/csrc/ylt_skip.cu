@@ -3,29 +3,35 @@
 // occupancy summary that Section VI's compressed representations point to).
 //
 // A group is up to 8 layers whose ELTs together number at most 32. It has a
-// direct-access table [C][np] FP32 over the union of its ELTs (event-major)
-// and a bitmap over the catalogue: bit i is set when any of those ELTs has a
-// non-zero loss for event i. An event with a clear bit contributes exactly
-// zero to every layer of the group (absent losses are 0 and F_e(0) = 0 since
-// D_e >= 0), so it is skipped without reading its row.
+// direct-access table [C][np] FP32 over the union of its ELTs (event-major).
 //
-// Mapping: a persistent grid of one CTA per SM. Each CTA copies the bitmap
-// into shared memory (as much of it as fits next to the queues: 1.79M events'
-// bits; the rest is read from global memory), so the per-event test is a
-// shared-memory load instead of a random L1 gather. Each warp walks a strided
-// sequence of trials as a stream of chunks of 32 * E events: the next chunk's
-// ids (from the same trial or the next one) are requested before the current
-// chunk is processed, hiding the DRAM latency of the id stream. The ids whose
-// bit is set go to a per-warp queue in shared memory; each time 32 are queued,
-// every lane takes one and evaluates it fully: one row read (np * 4
-// contiguous bytes in 256-bit loads, not allocated in L1), F_e per ELT in
-// FP32, the per-layer ELT sums in the group's ELT order, the occurrence
-// terms, and the occurrence-net loss added to the lane's per-layer aggregate.
-// That aggregate is a compensated FP32 pair (Knuth's two-sum: the pair holds
-// the exact sum up to a second-order term of order n u^2), folded into FP64
-// once per trial, so the FP64 pipe works per trial rather than per event; the
-// warp then reduces the lanes' FP64 partials and applies the aggregate terms
-// in FP64.
+// Steps 2-3 of Algorithm 1 (the financial terms, the ELT sum and the
+// occurrence terms) depend on the event id alone, not on the trial. So each
+// call first evaluates them once per catalogue event: X[i][j] = O_j(sum_{e in
+// layer j} F_e(l_e[i])) for every layer j of the group (FP32, in the group's
+// ELT order), plus a bitmap with bit i set when any X[i][j] > 0. The trial
+// pass then needs, per event occurrence, one bit test and, for the events
+// with a non-zero occurrence loss, one gather of X[E_d] (4 * LP contiguous
+// bytes); events with a clear bit add exactly 0 to every layer and are
+// skipped. The values are the ones the per-occurrence evaluation gives, bit
+// for bit: the same operations on the same operands.
+//
+// Mapping of the trial pass: a persistent grid of one CTA per SM. Each CTA
+// copies the bitmap into shared memory (as much of it as fits next to the
+// queues: 1.79M events' bits; the rest is read from global memory), so the
+// per-event test is a shared-memory load. Each warp walks a strided sequence
+// of trials as a stream of chunks of 32 * E events: the next chunk's ids
+// (from the same trial or the next one) are requested before the current
+// chunk is processed, hiding the DRAM latency of the id stream. For groups
+// of 1-2 layers every lane gathers X for its own events whose bit is set
+// (predicated loads, E in flight per lane). For wider groups the ids whose
+// bit is set go to a per-warp queue in shared memory and each time 32 are
+// queued every lane takes one, so the per-event work (one row of LP floats
+// and LT accumulations) runs on full warps. The per-lane, per-layer aggregate
+// is a compensated FP32 pair (Knuth's two-sum: the pair holds the exact sum
+// up to a second-order term of order n u^2), folded into FP64 once per trial,
+// so the FP64 pipe works per trial rather than per event; the warp then
+// reduces the lanes' FP64 partials and applies the aggregate terms in FP64.
 #include <algorithm>
 #include <limits>
 
@@ -74,32 +80,31 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
     e += err;
 }
 
-template <int NP, int LT>
-__device__ __forceinline__ void eval_event(const GroupArgs& g, int32_t id, float (&hi)[LT], float (&lo)[LT]) {
-    const float* row = g.table + (size_t)id * NP;
-    float f[NP];
-    if constexpr (NP % 8 == 0) {
+__device__ __forceinline__ float ld_occ1(const float* p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void ld_occ2(const float* p, float* v) {
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "l"(p));
+}
+
+// Row i of the occurrence-loss table: LP (1, 2, 4 or 8) contiguous floats.
+template <int LP>
+__device__ __forceinline__ void ld_occ_row(const float* x, int32_t id, float (&o)[LP]) {
+    const float* p = x + (size_t)id * LP;
+    if constexpr (LP == 1) o[0] = ld_occ1(p);
+    else if constexpr (LP == 2) ld_occ2(p, o);
+    else if constexpr (LP == 4) ld_row4(p, o);
+    else ld_row8(p, o);
+}
+
+template <int LT>
+__device__ __forceinline__ void add_occ(const float* o, float (&hi)[LT], float (&lo)[LT]) {
 #pragma unroll
-        for (int q = 0; q < NP / 8; ++q) ld_row8(row + 8 * q, f + 8 * q);
-    } else {
-#pragma unroll
-        for (int q = 0; q < NP / 4; ++q) ld_row4(row + 4 * q, f + 4 * q);
-    }
-#pragma unroll
-    for (int k = 0; k < NP; ++k) f[k] = fin_f32(f[k], g.m[k], g.d[k], g.lim[k]);
-#pragma unroll
-    for (int j = 0; j < LT; ++j) {
-        float x = 0.0f;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            // a one-layer group covers every real column (padding columns add
-            // 0); otherwise the 0/1 coefficient selects the layer's columns
-            if constexpr (LT == 1) x += f[k];
-            else x = __fmaf_rn(g.coef[j][k], f[k], x);
-        }
-        const float o = xl_f32(x, g.occ_ret[j], g.occ_lim[j]);
-        if (o > 0.0f) two_sum_acc(hi[j], lo[j], o);
-    }
+    for (int j = 0; j < LT; ++j)
+        if (o[j] > 0.0f) two_sum_acc(hi[j], lo[j], o[j]);
 }
 
 __device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
@@ -156,7 +161,7 @@ __device__ __forceinline__ bool group_capped(const GroupArgs& g, const float (&h
     return all;
 }
 
-template <int NP, int LT, bool VEC>
+template <int LT, int LP, bool VEC, bool COMPACT>
 __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupArgs g, const YetArgs y,
                                                                   const int32_t smem_words, const bool early_exit,
                                                                   double* __restrict__ ylt,
@@ -165,10 +170,10 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int E = kSkipIdsPerLane;  // ids per lane per chunk: a chunk is 32 * E events
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    int32_t* s_queue = reinterpret_cast<int32_t*>(s_dyn);  // [kSkipWarps][kQueue]
-    uint32_t* s_bits = s_dyn + kSkipWarps * kQueue;          // the first smem_words words of the bitmap
+    int32_t* s_queue = reinterpret_cast<int32_t*>(s_dyn);  // [kSkipWarps][kQueue] (COMPACT only)
+    uint32_t* s_bits = s_dyn + (COMPACT ? kSkipWarps * kQueue : 0);  // the first smem_words words of the bitmap
     {
-        const uint4* src = reinterpret_cast<const uint4*>(g.bitmap);
+        const uint4* src = reinterpret_cast<const uint4*>(g.occ_bits);
         uint4* dst = reinterpret_cast<uint4*>(s_bits);
         for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) dst[i] = src[i];
     }
@@ -228,24 +233,41 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
                 if (live && !ok) bad_id = true;
                 const int32_t wi = id[k] >> 5;
                 uint32_t w = 0u;
-                if (ok) w = wi < smem_words ? s_bits[wi] : ld_bitmap(g.bitmap + wi);
+                if (ok) w = wi < smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);
                 nz[k] = (w >> (id[k] & 31)) & 1u;
             }
+            if constexpr (COMPACT) {
 #pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const unsigned m = __ballot_sync(FULL, nz[k]);
-                if (nz[k]) q[qn + __popc(m & lt_mask)] = id[k];
-                qn += __popc(m);
-                if (qn >= 32) {
-                    __syncwarp();
-                    const int32_t mine = q[lane];
-                    const int32_t carry = q[32 + lane];
-                    __syncwarp();
-                    q[lane] = carry;  // entries 32 .. qn-1 move to the front
-                    qn -= 32;
-                    eval_event<NP, LT>(g, mine, hi, lo);
-                    __syncwarp();
+                for (int k = 0; k < E; ++k) {
+                    const unsigned m = __ballot_sync(FULL, nz[k]);
+                    if (nz[k]) q[qn + __popc(m & lt_mask)] = id[k];
+                    qn += __popc(m);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        const int32_t mine = q[lane];
+                        const int32_t carry = q[32 + lane];
+                        __syncwarp();
+                        q[lane] = carry;  // entries 32 .. qn-1 move to the front
+                        qn -= 32;
+                        float o[LP];
+                        ld_occ_row<LP>(g.occ, mine, o);
+                        add_occ<LT>(o, hi, lo);
+                        __syncwarp();
+                    }
                 }
+            } else {
+                // every lane gathers its own non-zero events, E loads in flight
+                float o[E][LP];
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    if (nz[k]) ld_occ_row<LP>(g.occ, id[k], o[k]);
+                    else {
+#pragma unroll
+                        for (int j = 0; j < LP; ++j) o[k][j] = 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < E; ++k) add_occ<LT>(o[k], hi, lo);
             }
             if (early_exit && group_capped<LT>(g, hi, lo)) {
                 // the rest of the trial cannot change its loss: skip it (and
@@ -256,9 +278,15 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
                 break;
             }
         }
-        __syncwarp();
-        if (lane < qn) eval_event<NP, LT>(g, q[lane], hi, lo);
-        __syncwarp();
+        if constexpr (COMPACT) {
+            __syncwarp();
+            if (lane < qn) {
+                float o[LP];
+                ld_occ_row<LP>(g.occ, q[lane], o);
+                add_occ<LT>(o, hi, lo);
+            }
+            __syncwarp();
+        }
 #pragma unroll
         for (int j = 0; j < LT; ++j) {
             double sum = (double)hi[j] + (double)lo[j];
@@ -279,17 +307,70 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
     if (lane == 0 && bad_off_seen) atomicOr(flags + kFlagBadOffsets, 1);
 }
 
-template <int NP, int LT>
+// Occurrence-loss table of a group (steps 2-3 per catalogue event): thread i
+// reads row i of the group table and writes X[i][0..LP) (layers >= LT: 0);
+// lane 0 of each warp writes the bitmap word of its 32 events.
+template <int NP, int LT, int LP>
+__global__ void __launch_bounds__(256) build_occ_kernel(const GroupArgs g, int32_t catalogue, int32_t words,
+                                                        float* __restrict__ occ, uint32_t* __restrict__ bits) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool nz = false;
+    if (i < catalogue) {
+        const float4* row = reinterpret_cast<const float4*>(g.table) + i * (NP / 4);
+        float f[NP];
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) {
+            const float4 r = __ldcs(row + q);
+            f[4 * q + 0] = r.x;
+            f[4 * q + 1] = r.y;
+            f[4 * q + 2] = r.z;
+            f[4 * q + 3] = r.w;
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) f[k] = fin_f32(f[k], g.m[k], g.d[k], g.lim[k]);
+        float o[LP];
+#pragma unroll
+        for (int j = 0; j < LP; ++j) {
+            o[j] = 0.0f;
+            if (j < LT) {
+                float x = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    // a one-layer group covers every real column (padding
+                    // columns add 0); otherwise the 0/1 coefficient selects
+                    // the layer's columns
+                    if constexpr (LT == 1) x += f[k];
+                    else x = __fmaf_rn(g.coef[j][k], f[k], x);
+                }
+                o[j] = xl_f32(x, g.occ_ret[j], g.occ_lim[j]);
+                nz |= o[j] > 0.0f;
+            }
+        }
+        float* dst = occ + i * LP;
+        if constexpr (LP == 1) dst[0] = o[0];
+        else if constexpr (LP == 2) *reinterpret_cast<float2*>(dst) = make_float2(o[0], o[1]);
+        else {
+#pragma unroll
+            for (int q = 0; q < LP / 4; ++q)
+                reinterpret_cast<float4*>(dst)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bits[i >> 5] = m;
+}
+
+template <int LT, int LP>
 cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
                          double* ylt, uint8_t* branch, int* flags, cudaStream_t s) {
+    constexpr bool COMPACT = LT >= 4;
     // 16-byte id loads when every trial starts and ends on a multiple of 4 ids
     const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
-    auto kern = vec ? ylt_skip_kernel<NP, LT, true> : ylt_skip_kernel<NP, LT, false>;
+    auto kern = vec ? ylt_skip_kernel<LT, LP, true, COMPACT> : ylt_skip_kernel<LT, LP, false, COMPACT>;
     int dev = 0, max_optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
-    const int queue_bytes = kSkipWarps * kQueue * 4;
+    const int queue_bytes = COMPACT ? kSkipWarps * kQueue * 4 : 0;
     const int words = (int)(((int64_t)catalogue + 31) / 32);
     // whole 16-byte groups of words that fit next to the queues
     const int smem_words = std::max(0, std::min(words, (max_optin - queue_bytes) / 4) & ~3);
@@ -301,13 +382,28 @@ cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int3
     return cudaGetLastError();
 }
 
+template <int NP, int LT, int LP>
+cudaError_t launch_build(const GroupArgs& g, int32_t catalogue, cudaStream_t s) {
+    const int32_t words = (int32_t)(((int64_t)catalogue + 31) / 32);
+    const int64_t n = (int64_t)words * 32;
+    build_occ_kernel<NP, LT, LP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, catalogue, words, g.occ, g.occ_bits);
+    return cudaGetLastError();
+}
+
 template <int NP>
+cudaError_t build_lt(const GroupArgs& g, int32_t catalogue, cudaStream_t s) {
+    if (g.n_layers <= 1) return launch_build<NP, 1, 1>(g, catalogue, s);
+    if (g.n_layers <= 2) return launch_build<NP, 2, 2>(g, catalogue, s);
+    if (g.n_layers <= 4) return launch_build<NP, 4, 4>(g, catalogue, s);
+    return launch_build<NP, 8, 8>(g, catalogue, s);
+}
+
 cudaError_t launch_lt(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early, double* ylt,
                       uint8_t* branch, int* flags, cudaStream_t s) {
-    if (g.n_layers <= 1) return launch_group<NP, 1>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
-    if (g.n_layers <= 2) return launch_group<NP, 2>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
-    if (g.n_layers <= 4) return launch_group<NP, 4>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
-    return launch_group<NP, 8>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    if (g.n_layers <= 1) return launch_group<1, 1>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    if (g.n_layers <= 2) return launch_group<2, 2>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    if (g.n_layers <= 4) return launch_group<4, 4>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
+    return launch_group<8, 8>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
 }
 
 // Bitmap of a group table: bit i set when row i has any non-zero entry.
@@ -334,14 +430,18 @@ cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t
     for (size_t gi = 0; gi < p->groups.size(); ++gi) {
         const GroupArgs& g = p->groups[gi];
         cudaError_t err;
+        // steps 2-3 once per catalogue event, with the terms as they are now
         switch (p->group_np[gi]) {
-            case 4: err = launch_lt<4>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
-            case 8: err = launch_lt<8>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
-            case 16: err = launch_lt<16>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
-            case 24: err = launch_lt<24>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
-            case 32: err = launch_lt<32>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 4: err = build_lt<4>(g, p->catalogue, s); break;
+            case 8: err = build_lt<8>(g, p->catalogue, s); break;
+            case 16: err = build_lt<16>(g, p->catalogue, s); break;
+            case 24: err = build_lt<24>(g, p->catalogue, s); break;
+            case 32: err = build_lt<32>(g, p->catalogue, s); break;
             default: err = cudaErrorInvalidValue;
         }
+        if (err != cudaSuccess) return err;
+        if (y.n_trials == 0) continue;
+        err = launch_lt(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s);
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
