@@ -321,9 +321,13 @@ cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t str
         const int nl = (int)p->group_layers[gi].size();
         const int lt_pad = nl <= 1 ? 1 : nl <= 2 ? 2 : nl <= 4 ? 4 : 8;
         const size_t ob = sizeof(float) * (size_t)p->catalogue * lt_pad;
+        // the occurrence bitmap is zero-padded to whole 16-byte groups (the
+        // forward copies it into shared memory 16 bytes at a time)
+        const size_t obb = 16 * (((size_t)p->catalogue + 127) / 128);
         if ((e = cudaMalloc(&p->group_occ[gi], ob))) break;
-        if ((e = cudaMalloc(&p->group_occ_bits[gi], bb))) break;
-        p->group_bytes += (int64_t)(tb + bb + ob + bb);
+        if ((e = cudaMalloc(&p->group_occ_bits[gi], obb))) break;
+        if ((e = cudaMemsetAsync(p->group_occ_bits[gi], 0, obb, stream))) break;
+        p->group_bytes += (int64_t)(tb + bb + ob + obb);
         p->groups[gi].occ = p->group_occ[gi];
         p->groups[gi].occ_bits = p->group_occ_bits[gi];
         p->groups[gi].lt_pad = lt_pad;

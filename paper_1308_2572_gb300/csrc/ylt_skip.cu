@@ -161,7 +161,19 @@ __device__ __forceinline__ bool group_capped(const GroupArgs& g, const float (&h
     return all;
 }
 
-template <int LT, int LP, bool VEC, bool COMPACT>
+// (h, l) += (h2, l2) for compensated FP32 pairs: two-sum of the high parts,
+// the error and both low parts into the low part. Symmetric in its operands
+// (the two-sum error is exact), so xor-shuffle reductions give every lane the
+// same bits.
+__device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2) {
+    const float t = h + h2;
+    const float bp = t - h;
+    const float err = (h - (t - bp)) + (h2 - bp);
+    h = t;
+    l = (l + l2) + err;
+}
+
+template <int LT, int LP, bool VEC, bool COMPACT, bool FOLD>
 __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupArgs g, const YetArgs y,
                                                                   const int32_t smem_words, const bool early_exit,
                                                                   double* __restrict__ ylt,
@@ -171,11 +183,25 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
     constexpr int E = kSkipIdsPerLane;  // ids per lane per chunk: a chunk is 32 * E events
     extern __shared__ __align__(16) uint32_t s_dyn[];
     int32_t* s_queue = reinterpret_cast<int32_t*>(s_dyn);  // [kSkipWarps][kQueue] (COMPACT only)
-    uint32_t* s_bits = s_dyn + (COMPACT ? kSkipWarps * kQueue : 0);  // the first smem_words words of the bitmap
+    uint32_t* s_bits = s_dyn + (COMPACT ? kSkipWarps * kQueue : 0);  // smem_words words of the bitmap
     {
+        // FOLD: word w holds bitmap words w and w + smem_words OR-ed together
+        // (a superset test: an event whose bit is set only through the fold
+        // gathers a row of zeros, which adds exactly 0)
         const uint4* src = reinterpret_cast<const uint4*>(g.occ_bits);
         uint4* dst = reinterpret_cast<uint4*>(s_bits);
-        for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) dst[i] = src[i];
+        const int words = (int)(((int64_t)y.catalogue + 31) / 32);
+        for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) {
+            uint4 v = src[i];
+            if (FOLD && 4 * i + smem_words < words) {  // occ_bits is zero-padded to whole uint4
+                const uint4 u = src[i + smem_words / 4];
+                v.x |= u.x;
+                v.y |= u.y;
+                v.z |= u.z;
+                v.w |= u.w;
+            }
+            dst[i] = v;
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -183,6 +209,40 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n_warps = (int64_t)gridDim.x * kSkipWarps;
     bool bad_id = false, bad_off_seen = false;
+
+    // groups of 1-2 layers: results of up to 32 trials, lane s holding the
+    // s-th, so the FP64 steps (fold of the pair, aggregate terms, branch code)
+    // run once per 32 trials; wider groups: lane j finalises layer j of each
+    // trial
+    constexpr bool BATCH = LT <= 2;
+    int32_t my_layer = 0;
+    double my_ret = 0.0, my_lim = 0.0;
+#pragma unroll
+    for (int j = 0; j < LT; ++j)
+        if (lane == j) {
+            my_layer = g.layer[j];
+            my_ret = g.agg_ret[j];
+            my_lim = g.agg_lim[j];
+        }
+    float rh[BATCH ? LT : 1], rl[BATCH ? LT : 1];
+    int64_t rt = -1;
+    bool rcap = false;
+    int slot = 0;
+    auto flush = [&]() {
+        if (BATCH && rt >= 0) {
+#pragma unroll
+            for (int j = 0; j < LT; ++j) {
+                if (j < g.n_layers) {
+                    const double sum = (double)rh[j] + (double)rl[j];
+                    const size_t wi = (size_t)g.layer[j] * (size_t)y.n_trials + (size_t)rt;
+                    // an early exit means every layer reached its cap: the loss is AggL
+                    ylt[wi] = rcap ? g.agg_lim[j] : xl_f64(sum, g.agg_ret[j], g.agg_lim[j]);
+                    if (branch) branch[wi] = rcap ? (uint8_t)2 : agg_branch(sum, g.agg_ret[j], g.agg_lim[j]);
+                }
+            }
+        }
+        rt = -1;
+    };
 
     int64_t t = (int64_t)blockIdx.x * kSkipWarps + wib;
     const int32_t* tid = y.ids;  // ids of the current trial
@@ -222,18 +282,25 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
             int32_t id[E];
 #pragma unroll
             for (int k = 0; k < E; ++k) id[k] = pre[k];
+            const bool full_chunk = c0 + 32 * E <= n;
             // request the next chunk (this trial's, or the next trial's first) now
             if (c0 + 32 * E < n) load_chunk<E, VEC>(tid, c0 + 32 * E, n, lane, pre);
             else if (tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
             bool nz[E];
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const bool live = slot_pos<VEC>(c0, k, lane) < n;
+                // every slot of a full chunk is an event of the trial
+                const bool live = full_chunk || slot_pos<VEC>(c0, k, lane) < n;
                 const bool ok = live && (unsigned)id[k] < (unsigned)y.catalogue;
-                if (live && !ok) bad_id = true;
-                const int32_t wi = id[k] >> 5;
+                bad_id |= live && !ok;
+                int32_t wi = id[k] >> 5;
                 uint32_t w = 0u;
-                if (ok) w = wi < smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);
+                if constexpr (FOLD) {
+                    wi = wi >= smem_words ? wi - smem_words : wi;
+                    if (ok) w = s_bits[wi];
+                } else {
+                    if (ok) w = wi < smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);
+                }
                 nz[k] = (w >> (id[k] & 31)) & 1u;
             }
             if constexpr (COMPACT) {
@@ -287,22 +354,48 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
             }
             __syncwarp();
         }
+        // the trial's aggregate: the lanes' pairs summed across the warp in
+        // compensated FP32
 #pragma unroll
         for (int j = 0; j < LT; ++j) {
-            double sum = (double)hi[j] + (double)lo[j];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-            if (lane == 0 && j < g.n_layers) {
-                const size_t wi = (size_t)g.layer[j] * (size_t)y.n_trials + (size_t)t;
-                // an early exit means every layer reached its cap: the loss is AggL
-                ylt[wi] = capped_exit ? g.agg_lim[j] : xl_f64(sum, g.agg_ret[j], g.agg_lim[j]);
-                if (branch) branch[wi] = capped_exit ? (uint8_t)2 : agg_branch(sum, g.agg_ret[j], g.agg_lim[j]);
+            for (int o = 16; o > 0; o >>= 1)
+                pair_add(hi[j], lo[j], __shfl_xor_sync(FULL, hi[j], o), __shfl_xor_sync(FULL, lo[j], o));
+        }
+        if constexpr (BATCH) {
+            if (lane == slot) {
+#pragma unroll
+                for (int j = 0; j < LT; ++j) {
+                    rh[j] = hi[j];
+                    rl[j] = lo[j];
+                }
+                rt = t;
+                rcap = capped_exit;
+            }
+            if (++slot == 32) {
+                flush();
+                slot = 0;
+            }
+        } else {
+            float mh = 0.0f, ml = 0.0f;
+#pragma unroll
+            for (int j = 0; j < LT; ++j)
+                if (lane == j) {
+                    mh = hi[j];
+                    ml = lo[j];
+                }
+            if (lane < g.n_layers) {
+                const double sum = (double)mh + (double)ml;
+                const size_t wi = (size_t)my_layer * (size_t)y.n_trials + (size_t)t;
+                ylt[wi] = capped_exit ? my_lim : xl_f64(sum, my_ret, my_lim);
+                if (branch) branch[wi] = capped_exit ? (uint8_t)2 : agg_branch(sum, my_ret, my_lim);
             }
         }
         t = tn;
         tid = tidn;
         n = nn;
     }
+    flush();
     if (bad_id) atomicOr(flags + kFlagIdRange, 1);
     if (lane == 0 && bad_off_seen) atomicOr(flags + kFlagBadOffsets, 1);
 }
@@ -363,9 +456,6 @@ template <int LT, int LP>
 cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
                          double* ylt, uint8_t* branch, int* flags, cudaStream_t s) {
     constexpr bool COMPACT = LT >= 4;
-    // 16-byte id loads when every trial starts and ends on a multiple of 4 ids
-    const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
-    auto kern = vec ? ylt_skip_kernel<LT, LP, true, COMPACT> : ylt_skip_kernel<LT, LP, false, COMPACT>;
     int dev = 0, max_optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -373,8 +463,14 @@ cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int3
     const int queue_bytes = COMPACT ? kSkipWarps * kQueue * 4 : 0;
     const int words = (int)(((int64_t)catalogue + 31) / 32);
     // whole 16-byte groups of words that fit next to the queues
-    const int smem_words = std::max(0, std::min(words, (max_optin - queue_bytes) / 4) & ~3);
+    const int smem_words = std::max(4, std::min((words + 3) & ~3, (max_optin - queue_bytes) / 4) & ~3);
     const int smem = queue_bytes + smem_words * 4;
+    // the bitmap folds once into shared memory when it is at most twice as long
+    const bool fold = words <= 2 * smem_words;
+    // 16-byte id loads when every trial starts and ends on a multiple of 4 ids
+    const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
+    auto kern = vec ? (fold ? ylt_skip_kernel<LT, LP, true, COMPACT, true> : ylt_skip_kernel<LT, LP, true, COMPACT, false>)
+                    : (fold ? ylt_skip_kernel<LT, LP, false, COMPACT, true> : ylt_skip_kernel<LT, LP, false, COMPACT, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     const int64_t grid = std::min<int64_t>(num_sms, (y.n_trials + kSkipWarps - 1) / kSkipWarps);
     kern<<<(unsigned)std::max<int64_t>(1, grid), kSkipThreads, smem, s>>>(g, y, smem_words, early, ylt, branch,
