@@ -176,6 +176,12 @@ def layer_groups(port, with_layers: bool = False):
     return groups if with_layers else [g for g, _ in groups]
 
 
+def occurrence_groups(port):
+    """The skip variant's occurrence groups: runs of up to 8 consecutive
+    layers, as lists of layer ids."""
+    return [list(range(j, min(j + 8, port.n_layers))) for j in range(0, port.n_layers, 8)]
+
+
 def occurrence_density(port, layers) -> float:
     """Fraction of catalogue events with a positive occurrence loss in any of
     the given layers (the density of the skip variant's per-call bitmap).
@@ -222,15 +228,14 @@ def algorithmic_bytes(w, variant: str):
     sec = lambda nbytes: 32 * -(-nbytes // 32)
     pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
     if variant == "skip":
-        # per group: one streamed pass over the group table that writes the
-        # occurrence-loss table X [C][LP] and its bitmap, then per event an id
-        # and, where X is non-zero, one sector of X
-        reads, build = 0.0, 0.0
-        groups = layer_groups(port, with_layers=True)
-        for elts, lays in groups:
-            lp = 1 if len(lays) <= 1 else (2 if len(lays) <= 2 else (4 if len(lays) <= 4 else 8))
-            reads += n_events * occurrence_density(port, lays) * sec(4 * lp)
-            build += C * 4 * pad(len(elts)) + C * 4 * lp + C / 8
+        # one streamed pass over the per-layer tables that writes each
+        # occurrence group's table X [C][LP] and its bitmap, then per group
+        # and event an id and, where X is non-zero, one sector of X
+        L = port.n_layers
+        lp = 1 if L <= 1 else (2 if L <= 2 else (4 if L <= 4 else 8))
+        groups = occurrence_groups(port)
+        reads = sum(n_events * occurrence_density(port, lays) * sec(4 * lp) for lays in groups)
+        build = float(sum(4 * pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (C * 4 * lp + C / 8)
         n_groups = len(groups)
         return {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
                 "l2": n_groups * ids + build + reads}
@@ -351,11 +356,11 @@ def main():
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
     # a named variant builds only its own layout (keeps profiling runs small)
-    layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_GROUP, "batched": art.ART_LAYOUT_POOL,
+    layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_LAYER, "batched": art.ART_LAYOUT_POOL,
                "fp64": art.ART_LAYOUT_POOL64, "sparse": art.ART_LAYOUT_SPARSE}.get(
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
     if args.config == "c3":
-        layouts |= art.ART_LAYOUT_LAYER  # the adjoint reads the per-layer tables
+        layouts |= art.ART_LAYOUT_GROUP  # the adjoint reads the group tables
     p = art.portfolio_from_workload(w, device=dev, layouts=layouts,
                                     flags=art.ART_FLAG_L2_PERSIST if args.l2_persist else 0)
     ids = torch.from_numpy(yet.event_ids).to(dev)
@@ -522,11 +527,11 @@ def main():
         cpu = cpu_baseline(args, w)
 
     # kernels of ours launched per step: forward (one per layer for the plain
-    # variant, occurrence-table build + trial pass per group for the skip
-    # variant, one persistent launch otherwise) + metrics (state init, 6 x
+    # variant, one occurrence-table build plus a trial pass per occurrence
+    # group for the skip variant, one persistent launch otherwise) + metrics (state init, 6 x
     # (histogram + select), tail sums, finalize)
     n_groups = len(layer_groups(port))
-    launches = {"plain": L, "skip": 2 * n_groups}.get(variant, 1) + 15
+    launches = {"plain": L, "skip": 1 + len(occurrence_groups(port))}.get(variant, 1) + 15
     if with_grad:
         # metrics backward (count, weights, grad) + the adjoint: per group a
         # pass and its reduction (group tables), else per layer a pass and its

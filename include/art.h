@@ -79,19 +79,25 @@ enum {
     ART_VARIANT_PLAIN = 1,    /* one launch per layer over a per-layer event-major table  */
     ART_VARIANT_BATCHED = 2,  /* one persistent launch over all layers (pool table)       */
     ART_VARIANT_FP64 = 3,     /* batched, with FP64 tables and FP64 per-event arithmetic  */
-    ART_VARIANT_SKIP = 4,     /* one launch per layer group (<= 8 layers, <= 32 ELTs):
-                                 occupancy bitmap skips events whose losses are all zero  */
+    ART_VARIANT_SKIP = 4,     /* per call, the occurrence loss of every catalogue event
+                                 for every layer (one build launch from the per-layer
+                                 tables), then one trial pass per run of <= 8 layers that
+                                 skips events with zero occurrence loss (bitmap)         */
     ART_VARIANT_SPARSE = 5    /* one persistent launch over all layers, reading an
                                  event-major CSR of the non-zero losses (compressed ELTs) */
 };
 
 /* Layouts built by art_create_portfolio (bit mask). */
 enum {
-    ART_LAYOUT_LAYER = 1,     /* per layer: [C][n_pad] FP32, the layer's ELTs side by side */
+    ART_LAYOUT_LAYER = 1,     /* per layer: [C][n_pad] FP32, the layer's ELTs side by side;
+                                 plus, per run of <= 8 layers, a [C + 1][<= 8] FP32
+                                 occurrence-loss table and bitmap written by the skip
+                                 variant on every call (counted with the layer bytes)     */
     ART_LAYOUT_POOL = 2,      /* all ELTs:  [C][n_elt_pad] FP32, shared by every layer     */
     ART_LAYOUT_POOL64 = 4,    /* all ELTs:  [C][n_elt_pad] FP64 (precision study)          */
-    ART_LAYOUT_GROUP = 8,     /* per layer group: [C][n_pad] FP32 over the group's ELTs
-                                 plus a C-bit occupancy bitmap                             */
+    ART_LAYOUT_GROUP = 8,     /* per layer group (<= 8 layers, <= 32 ELTs together):
+                                 [C][n_pad] FP32 over the group's ELTs plus a C-bit
+                                 occupancy bitmap; read by art_run_ylt_backward           */
     ART_LAYOUT_SPARSE = 16    /* all ELTs: event-major CSR of the non-zero losses
                                  (C + 1 offsets, 8 bytes per non-zero loss)                */
 };
@@ -313,7 +319,8 @@ ART_API art_status art_metrics_backward(const double* ylt_dev, int64_t n_trials,
  * forms them; the results are deterministic.
  * With the ART_LAYOUT_GROUP tables the YET is read once per layer group and
  * only events with a loss in the group are evaluated; the per-event sums then
- * follow the group table's ELT order (as the skip variant forms them) and the
+ * follow the group table's ELT order (the union of the group's layers' ELTs
+ * in order of first appearance) and the
  * multiplier sums weight each event by g rounded to FP32, with compensated
  * FP32 accumulation (relative error of order 1e-7). Without them, the
  * ART_LAYOUT_LAYER tables are read once per layer in the layer's ELT order

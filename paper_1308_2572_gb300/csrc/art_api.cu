@@ -298,6 +298,78 @@ void refresh_group_terms(art_portfolio* p) {
     }
 }
 
+// Terms of every layer as the occurrence-table build reads them, and the
+// aggregate terms of the occurrence groups (kernel parameters).
+cudaError_t upload_layer_build(art_portfolio* p) {
+    std::vector<LayerBuildArgs> lb(p->n_layers);
+    for (int32_t j = 0; j < p->n_layers; ++j) {
+        LayerBuildArgs& a = lb[j];
+        a.table = p->layer_tab[j];
+        const int32_t b = p->loff[j], n = p->loff[j + 1] - b;
+        for (int k = 0; k < kMaxLayerElts; ++k) {
+            const bool real = k < n;
+            const int32_t e = real ? p->lids[b + k] : 0;
+            a.m[k] = real ? p->mult[e] : 1.0f;
+            a.d[k] = real ? p->ded[e] : 0.0f;
+            a.lim[k] = real ? p->lim[e] : std::numeric_limits<float>::infinity();
+        }
+        a.occ_ret = p->occ_ret[j];
+        a.occ_lim = p->occ_lim[j];
+        a.np = p->layer_np[j];
+        a.pad_ = 0;
+    }
+    for (OccGroupArgs& g : p->ogroups)
+        for (int s = 0; s < g.n_layers; ++s) {
+            g.agg_ret[s] = p->agg_ret[g.layer[s]];
+            g.agg_lim[s] = p->agg_lim[g.layer[s]];
+        }
+    return cudaMemcpy(p->d_lbuild, lb.data(), sizeof(LayerBuildArgs) * lb.size(), cudaMemcpyHostToDevice);
+}
+
+// Occurrence groups of the skip variant: runs of up to 8 consecutive layers,
+// each with an occurrence-loss table [C][og_lp] and a zero-padded bitmap.
+cudaError_t build_occ_groups(art_portfolio* p) {
+    const int32_t L = p->n_layers;
+    const int32_t per = std::min(L, kMaxOccLayers);
+    p->og_lp = per <= 1 ? 1 : per <= 2 ? 2 : per <= 4 ? 4 : 8;
+    const int32_t ng = (L + kMaxOccLayers - 1) / kMaxOccLayers;
+    p->ogroups.assign(ng, OccGroupArgs{});
+    p->og_occ.assign(ng, nullptr);
+    p->og_bits.assign(ng, nullptr);
+    std::vector<OccBuildGroup> bg(ng);
+    // X has one more row than the catalogue and the bitmap one more bit (the
+    // sentinel C, where out-of-range ids land: bit clear, row zero); the
+    // bitmap is zero-padded to whole 16-byte groups (the trial pass copies it
+    // into shared memory 16 bytes at a time)
+    const size_t xb = sizeof(float) * ((size_t)p->catalogue + 1) * p->og_lp;
+    const size_t bb = 16 * (((size_t)p->catalogue / 32 + 1 + 3) / 4);
+    cudaError_t e = cudaSuccess;
+    for (int32_t gi = 0; gi < ng && !e; ++gi) {
+        if ((e = cudaMalloc(&p->og_occ[gi], xb))) break;
+        if ((e = cudaMalloc(&p->og_bits[gi], bb))) break;
+        if ((e = cudaMemset(p->og_occ[gi], 0, xb))) break;
+        if ((e = cudaMemset(p->og_bits[gi], 0, bb))) break;
+        p->occ_bytes += (int64_t)(xb + bb);
+        OccGroupArgs& g = p->ogroups[gi];
+        g.occ = p->og_occ[gi];
+        g.occ_bits = p->og_bits[gi];
+        g.n_layers = std::min(kMaxOccLayers, L - gi * kMaxOccLayers);
+        bg[gi].occ = p->og_occ[gi];
+        bg[gi].occ_bits = p->og_bits[gi];
+        bg[gi].n_layers = g.n_layers;
+        for (int s = 0; s < kMaxOccLayers; ++s) {
+            const bool real = s < g.n_layers;
+            g.layer[s] = real ? gi * kMaxOccLayers + s : 0;
+            bg[gi].layer[s] = g.layer[s];
+        }
+    }
+    if (e) return e;
+    if ((e = cudaMalloc(&p->d_lbuild, sizeof(LayerBuildArgs) * L))) return e;
+    if ((e = cudaMalloc(&p->d_ogroups, sizeof(OccBuildGroup) * ng))) return e;
+    if ((e = cudaMemcpy(p->d_ogroups, bg.data(), sizeof(OccBuildGroup) * ng, cudaMemcpyHostToDevice))) return e;
+    return upload_layer_build(p);
+}
+
 cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t stream) {
     form_groups(p);
     const size_t ng = p->group_elts.size();
@@ -305,8 +377,6 @@ cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t str
     p->group_np.assign(ng, 0);
     p->group_tab.assign(ng, nullptr);
     p->group_bitmap.assign(ng, nullptr);
-    p->group_occ.assign(ng, nullptr);
-    p->group_occ_bits.assign(ng, nullptr);
     int32_t* d_el = nullptr;
     cudaError_t e = cudaMalloc(&d_el, sizeof(int32_t) * kMaxLayerElts * ng);
     if (e) return e;
@@ -318,19 +388,7 @@ cudaError_t build_groups(art_portfolio* p, const float* losses, cudaStream_t str
         const size_t bb = sizeof(uint32_t) * (((size_t)p->catalogue + 31) / 32);
         if ((e = cudaMalloc(&p->group_tab[gi], tb))) break;
         if ((e = cudaMalloc(&p->group_bitmap[gi], bb))) break;
-        const int nl = (int)p->group_layers[gi].size();
-        const int lt_pad = nl <= 1 ? 1 : nl <= 2 ? 2 : nl <= 4 ? 4 : 8;
-        const size_t ob = sizeof(float) * (size_t)p->catalogue * lt_pad;
-        // the occurrence bitmap is zero-padded to whole 16-byte groups (the
-        // forward copies it into shared memory 16 bytes at a time)
-        const size_t obb = 16 * (((size_t)p->catalogue + 127) / 128);
-        if ((e = cudaMalloc(&p->group_occ[gi], ob))) break;
-        if ((e = cudaMalloc(&p->group_occ_bits[gi], obb))) break;
-        if ((e = cudaMemsetAsync(p->group_occ_bits[gi], 0, obb, stream))) break;
-        p->group_bytes += (int64_t)(tb + bb + ob + obb);
-        p->groups[gi].occ = p->group_occ[gi];
-        p->groups[gi].occ_bits = p->group_occ_bits[gi];
-        p->groups[gi].lt_pad = lt_pad;
+        p->group_bytes += (int64_t)(tb + bb);
         if ((e = cudaMemcpyAsync(d_el + gi * kMaxLayerElts, el.data(), sizeof(int32_t) * el.size(),
                                  cudaMemcpyHostToDevice, stream)))
             break;
@@ -369,8 +427,10 @@ void free_portfolio(art_portfolio* p) {
     for (float* t : p->layer_tab) cudaFree(t);
     for (float* t : p->group_tab) cudaFree(t);
     for (uint32_t* b : p->group_bitmap) cudaFree(b);
-    for (float* t : p->group_occ) cudaFree(t);
-    for (uint32_t* b : p->group_occ_bits) cudaFree(b);
+    for (float* t : p->og_occ) cudaFree(t);
+    for (uint32_t* b : p->og_bits) cudaFree(b);
+    cudaFree(p->d_lbuild);
+    cudaFree(p->d_ogroups);
     cudaFree(p->pool);
     cudaFree(p->pool64);
     cudaFree(p->d_elt_terms);
@@ -412,7 +472,7 @@ int resolve_variant(const art_portfolio* p) {
 
 bool variant_available(const art_portfolio* p, int v) {
     if (v == ART_VARIANT_PLAIN) return (p->layouts & ART_LAYOUT_LAYER) != 0;
-    if (v == ART_VARIANT_SKIP) return !p->groups.empty();
+    if (v == ART_VARIANT_SKIP) return !p->ogroups.empty();
     if (v == ART_VARIANT_SPARSE) return p->sp_ptr != nullptr && p->n_tiles > 0 && sparse_smem(p, 1) <= 200 * 1024;
     if (v == ART_VARIANT_BATCHED) return p->pool != nullptr && p->n_tiles > 0 && batched_smem(p, false) <= 200 * 1024;
     if (v == ART_VARIANT_FP64) return p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024;
@@ -539,6 +599,7 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
                                       stream);
             }
             if (e) break;
+            if ((e = build_occ_groups(p))) break;
         }
         if ((p->layouts & (ART_LAYOUT_POOL | ART_LAYOUT_POOL64 | ART_LAYOUT_SPARSE)) && n_elt <= kMaxPoolElts) {
             int epl = 1;
@@ -604,6 +665,10 @@ art_status art_update_terms(art_portfolio* p, const float* elt_mult_host, const 
         if (e) return fail(e);
     }
     refresh_group_terms(p);
+    if (p->d_lbuild) {
+        const cudaError_t e = upload_layer_build(p);
+        if (e) return fail(e);
+    }
     if (p->graph_exec) {  // the plain variant bakes terms into launch parameters
         cudaGraphExecDestroy(p->graph_exec);
         p->graph_exec = nullptr;
@@ -863,7 +928,7 @@ art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64
     if (!p) return ART_EINVAL;
     if (sparse_bytes) *sparse_bytes = p->sparse_bytes;
     if (group_bytes) *group_bytes = p->group_bytes;
-    if (layer_bytes) *layer_bytes = p->layer_bytes;
+    if (layer_bytes) *layer_bytes = p->layer_bytes + p->occ_bytes;
     if (pool_bytes) *pool_bytes = p->pool_bytes;
     if (pool64_bytes) *pool64_bytes = p->pool64_bytes;
     return ART_OK;

@@ -123,12 +123,6 @@ constexpr int kMaxGroupLayers = 8;
 struct GroupArgs {
     const float* table;       // [C][np] FP32 over the group's ELTs (union order)
     const uint32_t* bitmap;   // [ceil(C / 32)]: bit i set if row i is not all zero
-    // per-call occurrence-loss table of the forward: X[i][j] = O_j(x_ij) for
-    // the group's layers j (padded to lt_pad columns), and its bitmap (bit i
-    // set if any X[i][j] > 0); written by the forward before its trial pass
-    float* occ;               // [C][lt_pad] FP32
-    uint32_t* occ_bits;       // [ceil(C / 32)]
-    int32_t lt_pad;           // 1, 2, 4 or 8
     float m[kMaxLayerElts];   // terms of the group's ELTs (padding: 1, 0, inf)
     float d[kMaxLayerElts];
     float lim[kMaxLayerElts];
@@ -140,6 +134,41 @@ struct GroupArgs {
     float occ_ret[kMaxGroupLayers], occ_lim[kMaxGroupLayers];
     double agg_ret[kMaxGroupLayers], agg_lim[kMaxGroupLayers];
     int32_t layer[kMaxGroupLayers];
+    int32_t n_layers;
+};
+
+// The skip variant works on occurrence groups: up to 8 consecutive layers,
+// whatever their ELTs. Each forward call writes, per group, the
+// occurrence-loss table X[i][s] = O_j(x_ij) for the group's layer j in slot s
+// (Algorithm 1 steps 2-3 evaluated once per catalogue event; slots past the
+// group's layers hold 0) and its bitmap (bit i set if any X[i][s] > 0); the
+// trial pass then reads those. Passed by value.
+constexpr int kMaxOccLayers = 8;
+struct OccGroupArgs {
+    const float* occ;          // [C][lt_pad] FP32
+    const uint32_t* occ_bits;  // [ceil(C / 128) * 4] (zero-padded to 16-byte groups)
+    int32_t layer[kMaxOccLayers];
+    double agg_ret[kMaxOccLayers], agg_lim[kMaxOccLayers];
+    int32_t n_layers;
+};
+
+// One layer as the occurrence-table build reads it (device array, one entry
+// per layer; padding ELTs have m = 1, D = 0, Lim = inf and zero columns).
+struct LayerBuildArgs {
+    const float* table;        // the layer's [C][np] table (ART_LAYOUT_LAYER)
+    float m[kMaxLayerElts];
+    float d[kMaxLayerElts];
+    float lim[kMaxLayerElts];
+    float occ_ret, occ_lim;
+    int32_t np;
+    int32_t pad_;
+};
+
+// One occurrence group as the build reads it (device array).
+struct OccBuildGroup {
+    float* occ;
+    uint32_t* occ_bits;
+    int32_t layer[kMaxOccLayers];
     int32_t n_layers;
 };
 
@@ -176,8 +205,16 @@ struct art_portfolio {
     std::vector<std::vector<int32_t>> group_layers; // layer ids per group
     std::vector<float*> group_tab;
     std::vector<uint32_t*> group_bitmap;
-    std::vector<float*> group_occ;            // occurrence-loss tables
-    std::vector<uint32_t*> group_occ_bits;
+
+    // skip variant (needs ART_LAYOUT_LAYER): occurrence groups and their
+    // per-call occurrence-loss tables and bitmaps
+    std::vector<art::OccGroupArgs> ogroups;
+    int32_t og_lp = 0;                          // slots per row of X (1, 2, 4 or 8)
+    std::vector<float*> og_occ;
+    std::vector<uint32_t*> og_bits;
+    art::LayerBuildArgs* d_lbuild = nullptr;    // [n_layers]
+    art::OccBuildGroup* d_ogroups = nullptr;    // [n_ogroups]
+    int64_t occ_bytes = 0;
     int64_t group_bytes = 0;
 
     // ART_LAYOUT_SPARSE: event-major CSR of the non-zero losses
@@ -228,6 +265,8 @@ cudaError_t launch_sparse(art_portfolio* p, const YetArgs& y, double* ylt, uint8
 cudaError_t build_sparse(art_portfolio* p, const float* src, cudaStream_t s);
 cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
 cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np, uint32_t* bitmap, cudaStream_t s);
+// Write every occurrence group's X and bitmap (one launch) from the layer tables.
+cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s);
 cudaError_t launch_batched(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, bool fp64,
                            cudaStream_t s);
 cudaError_t launch_adjoint(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,

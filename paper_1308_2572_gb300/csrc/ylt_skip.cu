@@ -1,20 +1,19 @@
-// ylt_skip.cu -- the forward pass for layer groups with an occupancy bitmap
-// (Section II, Algorithm 1; Section III's direct-access tables, plus the
-// occupancy summary that Section VI's compressed representations point to).
-//
-// A group is up to 8 layers whose ELTs together number at most 32. It has a
-// direct-access table [C][np] FP32 over the union of its ELTs (event-major).
+// ylt_skip.cu -- the forward pass by occurrence groups with an occupancy
+// bitmap (Section II, Algorithm 1, over Section III's direct-access tables,
+// plus the occupancy summary that Section VI's compressed representations
+// point to).
 //
 // Steps 2-3 of Algorithm 1 (the financial terms, the ELT sum and the
 // occurrence terms) depend on the event id alone, not on the trial. So each
-// call first evaluates them once per catalogue event: X[i][j] = O_j(sum_{e in
-// layer j} F_e(l_e[i])) for every layer j of the group (FP32, in the group's
-// ELT order), plus a bitmap with bit i set when any X[i][j] > 0. The trial
-// pass then needs, per event occurrence, one bit test and, for the events
-// with a non-zero occurrence loss, one gather of X[E_d] (4 * LP contiguous
-// bytes); events with a clear bit add exactly 0 to every layer and are
-// skipped. The values are the ones the per-occurrence evaluation gives, bit
-// for bit: the same operations on the same operands.
+// call first evaluates them once per catalogue event, for every occurrence
+// group (up to 8 consecutive layers): X[i][s] = O_j(sum_{e in layer j}
+// F_e(l_e[i])) for the group's layer j in slot s, in FP32 and in the layer's
+// ELT order (read from the per-layer tables), plus a bitmap with bit i set
+// when any X[i][s] > 0. The trial pass then needs, per event occurrence, one
+// bit test and, for the events with a non-zero occurrence loss, one gather
+// of X[E_d] (4 * LP contiguous bytes); events with a clear bit add exactly 0
+// to every layer and are skipped. The values are the ones the per-occurrence
+// evaluation gives, bit for bit: the same operations on the same operands.
 //
 // Mapping of the trial pass: a persistent grid of one CTA per SM. Each CTA
 // copies the bitmap into shared memory (as much of it as fits next to the
@@ -149,7 +148,7 @@ __device__ __forceinline__ void load_chunk(const int32_t* __restrict__ ids, int3
 // of the lanes' partial aggregates is at least AggR + AggL. The aggregate
 // never decreases (o >= 0), so the trial's loss is then AggL exactly.
 template <int LT>
-__device__ __forceinline__ bool group_capped(const GroupArgs& g, const float (&hi)[LT], const float (&lo)[LT]) {
+__device__ __forceinline__ bool group_capped(const OccGroupArgs& g, const float (&hi)[LT], const float (&lo)[LT]) {
     bool all = true;
 #pragma unroll
     for (int j = 0; j < LT; ++j) {
@@ -174,7 +173,7 @@ __device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2)
 }
 
 template <int LT, int LP, bool VEC, bool COMPACT, bool FOLD>
-__global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupArgs g, const YetArgs y,
+__global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGroupArgs g, const YetArgs y,
                                                                   const int32_t smem_words, const bool early_exit,
                                                                   double* __restrict__ ylt,
                                                                   uint8_t* __restrict__ branch,
@@ -190,7 +189,7 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
         // gathers a row of zeros, which adds exactly 0)
         const uint4* src = reinterpret_cast<const uint4*>(g.occ_bits);
         uint4* dst = reinterpret_cast<uint4*>(s_bits);
-        const int words = (int)(((int64_t)y.catalogue + 31) / 32);
+        const int words = (y.catalogue >> 5) + 1;  // bits 0 .. C (C: the sentinel)
         for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) {
             uint4 v = src[i];
             if (FOLD && 4 * i + smem_words < words) {  // occ_bits is zero-padded to whole uint4
@@ -208,7 +207,8 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
     int32_t* q = s_queue + wib * kQueue;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n_warps = (int64_t)gridDim.x * kSkipWarps;
-    bool bad_id = false, bad_off_seen = false;
+    uint32_t max_id = 0;  // largest id seen (an id >= C raises the range flag)
+    bool bad_off_seen = false;
 
     // groups of 1-2 layers: results of up to 32 trials, lane s holding the
     // s-th, so the FP64 steps (fold of the pair, aggregate terms, branch code)
@@ -286,28 +286,41 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
             // request the next chunk (this trial's, or the next trial's first) now
             if (c0 + 32 * E < n) load_chunk<E, VEC>(tid, c0 + 32 * E, n, lane, pre);
             else if (tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
+            // ids outside [0, C) (and the empty slots of a partial chunk) map
+            // to the sentinel C: its bit is clear and its row of X is zero
+            uint32_t uid[E];
+            if (full_chunk) {  // every slot of a full chunk is an event of the trial
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    max_id = max(max_id, (uint32_t)id[k]);
+                    uid[k] = min((uint32_t)id[k], (uint32_t)y.catalogue);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const bool live = slot_pos<VEC>(c0, k, lane) < n;
+                    max_id = max(max_id, live ? (uint32_t)id[k] : 0u);
+                    uid[k] = live ? min((uint32_t)id[k], (uint32_t)y.catalogue) : (uint32_t)y.catalogue;
+                }
+            }
             bool nz[E];
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                // every slot of a full chunk is an event of the trial
-                const bool live = full_chunk || slot_pos<VEC>(c0, k, lane) < n;
-                const bool ok = live && (unsigned)id[k] < (unsigned)y.catalogue;
-                bad_id |= live && !ok;
-                int32_t wi = id[k] >> 5;
-                uint32_t w = 0u;
+                uint32_t wi = uid[k] >> 5;
+                uint32_t w;
                 if constexpr (FOLD) {
-                    wi = wi >= smem_words ? wi - smem_words : wi;
-                    if (ok) w = s_bits[wi];
+                    wi = wi >= (uint32_t)smem_words ? wi - (uint32_t)smem_words : wi;
+                    w = s_bits[wi];
                 } else {
-                    if (ok) w = wi < smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);
+                    w = wi < (uint32_t)smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);
                 }
-                nz[k] = (w >> (id[k] & 31)) & 1u;
+                nz[k] = (w >> (uid[k] & 31)) & 1u;
             }
             if constexpr (COMPACT) {
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const unsigned m = __ballot_sync(FULL, nz[k]);
-                    if (nz[k]) q[qn + __popc(m & lt_mask)] = id[k];
+                    if (nz[k]) q[qn + __popc(m & lt_mask)] = (int32_t)uid[k];
                     qn += __popc(m);
                     if (qn >= 32) {
                         __syncwarp();
@@ -327,7 +340,7 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
                 float o[E][LP];
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    if (nz[k]) ld_occ_row<LP>(g.occ, id[k], o[k]);
+                    if (nz[k]) ld_occ_row<LP>(g.occ, (int32_t)uid[k], o[k]);
                     else {
 #pragma unroll
                         for (int j = 0; j < LP; ++j) o[k][j] = 0.0f;
@@ -396,50 +409,51 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const GroupAr
         n = nn;
     }
     flush();
-    if (bad_id) atomicOr(flags + kFlagIdRange, 1);
+    if (max_id >= (uint32_t)y.catalogue) atomicOr(flags + kFlagIdRange, 1);
     if (lane == 0 && bad_off_seen) atomicOr(flags + kFlagBadOffsets, 1);
 }
 
-// Occurrence-loss table of a group (steps 2-3 per catalogue event): thread i
-// reads row i of the group table and writes X[i][0..LP) (layers >= LT: 0);
-// lane 0 of each warp writes the bitmap word of its 32 events.
-template <int NP, int LT, int LP>
-__global__ void __launch_bounds__(256) build_occ_kernel(const GroupArgs g, int32_t catalogue, int32_t words,
-                                                        float* __restrict__ occ, uint32_t* __restrict__ bits) {
+// Occurrence-loss tables (steps 2-3 once per catalogue event): block
+// (x, y) covers 256 events of occurrence group y; thread i sums F_e over row
+// i of each of the group's layer tables in the layer's ELT order (padding
+// columns add exactly 0), applies the occurrence terms and writes X[i][0..LP)
+// (slots past the group's layers: 0); lane 0 of each warp writes the bitmap
+// word of its 32 events. The group's layer terms are staged in shared memory.
+template <int LP>
+__global__ void __launch_bounds__(256) build_occ_kernel(const LayerBuildArgs* __restrict__ lbuild,
+                                                        const OccBuildGroup* __restrict__ groups, int32_t catalogue,
+                                                        int32_t words) {
+    __shared__ LayerBuildArgs s_lb[LP];
+    const OccBuildGroup& grp = groups[blockIdx.y];
+    const int nl = grp.n_layers;
+    for (int w = threadIdx.x; w < nl * (int)(sizeof(LayerBuildArgs) / 4); w += blockDim.x) {
+        const int s = w / (int)(sizeof(LayerBuildArgs) / 4), o = w % (int)(sizeof(LayerBuildArgs) / 4);
+        reinterpret_cast<uint32_t*>(&s_lb[s])[o] = reinterpret_cast<const uint32_t*>(&lbuild[grp.layer[s]])[o];
+    }
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool nz = false;
     if (i < catalogue) {
-        const float4* row = reinterpret_cast<const float4*>(g.table) + i * (NP / 4);
-        float f[NP];
-#pragma unroll
-        for (int q = 0; q < NP / 4; ++q) {
-            const float4 r = __ldcs(row + q);
-            f[4 * q + 0] = r.x;
-            f[4 * q + 1] = r.y;
-            f[4 * q + 2] = r.z;
-            f[4 * q + 3] = r.w;
-        }
-#pragma unroll
-        for (int k = 0; k < NP; ++k) f[k] = fin_f32(f[k], g.m[k], g.d[k], g.lim[k]);
         float o[LP];
 #pragma unroll
-        for (int j = 0; j < LP; ++j) {
-            o[j] = 0.0f;
-            if (j < LT) {
+        for (int s = 0; s < LP; ++s) {
+            o[s] = 0.0f;
+            if (s < nl) {
+                const LayerBuildArgs& a = s_lb[s];
+                const float4* row = reinterpret_cast<const float4*>(a.table) + i * (a.np / 4);
                 float x = 0.0f;
-#pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    // a one-layer group covers every real column (padding
-                    // columns add 0); otherwise the 0/1 coefficient selects
-                    // the layer's columns
-                    if constexpr (LT == 1) x += f[k];
-                    else x = __fmaf_rn(g.coef[j][k], f[k], x);
+                for (int q = 0; q < a.np / 4; ++q) {
+                    const float4 r = __ldcs(row + q);
+                    x += fin_f32(r.x, a.m[4 * q + 0], a.d[4 * q + 0], a.lim[4 * q + 0]);
+                    x += fin_f32(r.y, a.m[4 * q + 1], a.d[4 * q + 1], a.lim[4 * q + 1]);
+                    x += fin_f32(r.z, a.m[4 * q + 2], a.d[4 * q + 2], a.lim[4 * q + 2]);
+                    x += fin_f32(r.w, a.m[4 * q + 3], a.d[4 * q + 3], a.lim[4 * q + 3]);
                 }
-                o[j] = xl_f32(x, g.occ_ret[j], g.occ_lim[j]);
-                nz |= o[j] > 0.0f;
+                o[s] = xl_f32(x, a.occ_ret, a.occ_lim);
+                nz |= o[s] > 0.0f;
             }
         }
-        float* dst = occ + i * LP;
+        float* dst = grp.occ + i * LP;
         if constexpr (LP == 1) dst[0] = o[0];
         else if constexpr (LP == 2) *reinterpret_cast<float2*>(dst) = make_float2(o[0], o[1]);
         else {
@@ -449,11 +463,11 @@ __global__ void __launch_bounds__(256) build_occ_kernel(const GroupArgs g, int32
         }
     }
     const unsigned m = __ballot_sync(0xffffffffu, nz);
-    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bits[i >> 5] = m;
+    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
 }
 
 template <int LT, int LP>
-cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
+cudaError_t launch_group(const OccGroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
                          double* ylt, uint8_t* branch, int* flags, cudaStream_t s) {
     constexpr bool COMPACT = LT >= 4;
     int dev = 0, max_optin = 0;
@@ -461,7 +475,7 @@ cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int3
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
     const int queue_bytes = COMPACT ? kSkipWarps * kQueue * 4 : 0;
-    const int words = (int)(((int64_t)catalogue + 31) / 32);
+    const int words = (catalogue >> 5) + 1;  // bits 0 .. C (C: the sentinel)
     // whole 16-byte groups of words that fit next to the queues
     const int smem_words = std::max(4, std::min((words + 3) & ~3, (max_optin - queue_bytes) / 4) & ~3);
     const int smem = queue_bytes + smem_words * 4;
@@ -476,30 +490,6 @@ cudaError_t launch_group(const GroupArgs& g, const YetArgs& y, int num_sms, int3
     kern<<<(unsigned)std::max<int64_t>(1, grid), kSkipThreads, smem, s>>>(g, y, smem_words, early, ylt, branch,
                                                                           flags);
     return cudaGetLastError();
-}
-
-template <int NP, int LT, int LP>
-cudaError_t launch_build(const GroupArgs& g, int32_t catalogue, cudaStream_t s) {
-    const int32_t words = (int32_t)(((int64_t)catalogue + 31) / 32);
-    const int64_t n = (int64_t)words * 32;
-    build_occ_kernel<NP, LT, LP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, catalogue, words, g.occ, g.occ_bits);
-    return cudaGetLastError();
-}
-
-template <int NP>
-cudaError_t build_lt(const GroupArgs& g, int32_t catalogue, cudaStream_t s) {
-    if (g.n_layers <= 1) return launch_build<NP, 1, 1>(g, catalogue, s);
-    if (g.n_layers <= 2) return launch_build<NP, 2, 2>(g, catalogue, s);
-    if (g.n_layers <= 4) return launch_build<NP, 4, 4>(g, catalogue, s);
-    return launch_build<NP, 8, 8>(g, catalogue, s);
-}
-
-cudaError_t launch_lt(const GroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early, double* ylt,
-                      uint8_t* branch, int* flags, cudaStream_t s) {
-    if (g.n_layers <= 1) return launch_group<1, 1>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
-    if (g.n_layers <= 2) return launch_group<2, 2>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
-    if (g.n_layers <= 4) return launch_group<4, 4>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
-    return launch_group<8, 8>(g, y, num_sms, catalogue, early, ylt, branch, flags, s);
 }
 
 // Bitmap of a group table: bit i set when row i has any non-zero entry.
@@ -521,23 +511,32 @@ cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np
     return cudaGetLastError();
 }
 
+cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s) {
+    const int32_t words = (int32_t)(((int64_t)p->catalogue + 31) / 32);
+    const dim3 grid((unsigned)(((int64_t)words * 32 + 255) / 256), (unsigned)p->ogroups.size());
+    switch (p->og_lp) {
+        case 1: build_occ_kernel<1><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+        case 2: build_occ_kernel<2><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+        case 4: build_occ_kernel<4><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+        case 8: build_occ_kernel<8><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s) {
     const bool early = (p->flags & ART_FLAG_EARLY_EXIT) != 0;
-    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
-        const GroupArgs& g = p->groups[gi];
-        cudaError_t err;
-        // steps 2-3 once per catalogue event, with the terms as they are now
-        switch (p->group_np[gi]) {
-            case 4: err = build_lt<4>(g, p->catalogue, s); break;
-            case 8: err = build_lt<8>(g, p->catalogue, s); break;
-            case 16: err = build_lt<16>(g, p->catalogue, s); break;
-            case 24: err = build_lt<24>(g, p->catalogue, s); break;
-            case 32: err = build_lt<32>(g, p->catalogue, s); break;
+    // steps 2-3 once per catalogue event, with the terms as they are now
+    cudaError_t err = build_occurrence(p, s);
+    if (err != cudaSuccess || y.n_trials == 0) return err;
+    for (const OccGroupArgs& g : p->ogroups) {
+        switch (p->og_lp) {
+            case 1: err = launch_group<1, 1>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 2: err = launch_group<2, 2>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 4: err = launch_group<4, 4>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 8: err = launch_group<8, 8>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
             default: err = cudaErrorInvalidValue;
         }
-        if (err != cudaSuccess) return err;
-        if (y.n_trials == 0) continue;
-        err = launch_lt(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s);
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
