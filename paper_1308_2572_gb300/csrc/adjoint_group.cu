@@ -1,9 +1,6 @@
 // adjoint_group.cu -- the adjoint of the forward pass (the pricing
-// sensitivity added around Section II's Algorithm 1) over layer groups: one
-// pass over the YET per group of up to 8 layers rather than one per layer,
-// and only the events whose bit is set in the group's occupancy bitmap are
-// evaluated (an event with a clear bit has x_dj = 0 for every layer j of the
-// group, which lies on no middle branch, so it contributes nothing).
+// sensitivity added around Section II's Algorithm 1) over layer groups (up
+// to 8 layers whose ELTs number at most 32 together, ART_LAYOUT_GROUP).
 //
 // With a_j = [branch_j == mid] and c_j = [branch_j == capped] from the
 // forward's aggregate branch codes and g_j the trial's weight:
@@ -12,25 +9,32 @@
 //   dOccL_j =  g_j a_j #{d : x_dj > OccR_j + OccL_j},
 //   dm_e    = sum_d [D_e < m_e l_de < D_e + Lim_e] l_de w_de,
 //             w_de = sum_{j covering e} g_j a_j [o_dj on its middle branch].
-// The per-event sums x_dj are recomputed in FP32 in the group table's ELT
-// order, exactly as the group forward (the skip variant) forms them.
 //
-// Mapping: warp per trial over a persistent grid (static stride). Lanes
-// 0..LT-1 read the trial's branch code and weight of their layer; a trial
-// with no layer on the middle branch costs nothing more. Otherwise the warp
-// streams the trial's ids 32 * E at a time, tests their bits, queues the
-// events with a loss in shared memory and evaluates them 32 at a time (lane =
-// event). Per event: the row (one 256-bit load per 8 columns), F_e and its
-// middle-branch test per column, the layer sums over their member columns,
-// each layer's occurrence branch, the weights w_de (FMA chains with 0/1
-// coefficients) and, where non-zero, l_de w_de added to the lane's compensated
-// FP32 pair of column e (the lanes' pairs live in shared memory, one column
-// per lane, so they cost no registers; few columns of a row are non-zero).
-// After each batch the branch flags are counted across the warp (integer
-// reductions) on lane j, which scales its layer's counts by g_j in FP64 at
-// the end of the trial; so FP64 runs per trial, not per event. The final per-lane
-// values are reduced warp -> CTA in a fixed order, and the CTA partials are
-// summed in block order (no atomics: deterministic).
+// Which occurrence branch each layer takes, and which ELT terms are on their
+// middle branch, depend on the event id alone. So each call first evaluates
+// them once per catalogue event i (the group table row, F_e and the layer
+// sums x_ij in FP32, in the group's ELT order): M_i, the layers on the middle
+// branch; K_i, the layers on the capped branch; and U_i, the ELT columns on
+// their middle branch; plus a bitmap of the events with M_i or K_i non-zero
+// (only those contribute). The trial pass is then shaped like the forward's:
+// a persistent CTA per SM with the bitmap in shared memory (folded once when
+// it does not fit), a warp per trial streaming its ids, and a per-warp queue
+// of the events whose bit is set, evaluated 32 at a time (lane = event):
+//   - the layer counts: per lane, 8-bit counters for the 8 layers packed in
+//     a 64-bit word, incremented by a table lookup of M (and K); reduced
+//     across the warp with integer reductions at the end of the trial (and
+//     every 255 batches), then lane j scales layer j's counts by g_j in FP64;
+//   - the multipliers: for each column k in U_i with M_i non-zero, the lane
+//     adds l_ik * W[M_i & C_k] to its FP32 partial of column k, where C_k is
+//     the set of layers covering column k and W[S] = sum_{j in S} g_j a_j is
+//     a 2^LT-entry table of the trial's weights (FP32, per warp, built per
+//     trial); at the end of the trial the partials are summed across the
+//     warp and lane k adds the total to its compensated FP32 pair.
+// A trial with no layer on the middle branch costs only its branch codes.
+// The lane values are reduced warp -> CTA -> grid in a fixed order (no
+// atomics: deterministic). Rounding: the per-event products and the W
+// entries are FP32 (a few units in the last place of FP32 per term), the
+// sums compensated or FP64.
 #include <algorithm>
 #include <limits>
 
@@ -40,22 +44,20 @@ namespace art {
 
 namespace {
 
-constexpr int kAgThreads = 256;
+constexpr int kAgThreads = 512;
 constexpr int kAgWarps = kAgThreads / 32;
-constexpr int kAgIds = 8;                   // ids per lane per chunk
-constexpr int kAgQueue = 32 * kAgIds + 32;  // per-warp queue: a chunk plus a partial batch
+constexpr int kAgIds = 8;    // ids per lane per chunk
+constexpr int kAgQueue = 64;  // per-warp queue entries
 
-// hi + lo += v without losing the rounding error of the FP32 add (two-sum)
-__device__ __forceinline__ void two_sum_add(float2& a, float v) {
-    const float t = a.x + v;
-    const float bp = t - a.x;
-    a.y += (a.x - (t - bp)) + (v - bp);
-    a.x = t;
-}
-
-__device__ __forceinline__ uint32_t ld_bits(const uint32_t* p) {
+__device__ __forceinline__ uint32_t ld_bits_global(const uint32_t* p) {
     uint32_t v;
     asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_mask(const uint2* p) {
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     return v;
 }
 
@@ -71,104 +73,146 @@ __device__ __forceinline__ void ld_row4(const float* p, float* v) {
         : "l"(p));
 }
 
-// One event on one lane. Returns the layers on their middle (bits 0..7) and
-// capped (bits 8..15) occurrence branches; adds l w to the lane's pair of
-// each column on its middle branch with a non-zero weight. acc is the lane's
-// column of pairs in shared memory (stride 32).
+// (h, l) += v, keeping the rounding error of the FP32 add (two-sum)
+__device__ __forceinline__ void two_sum_add(float& h, float& l, float v) {
+    const float t = h + v;
+    const float bp = t - h;
+    l += (h - (t - bp)) + (v - bp);
+    h = t;
+}
+
+// Per catalogue event i of a group: masks[i] = (M | K << 8, U) and bit i of
+// the bitmap set when M | K is non-zero. Row C (the sentinel for ids outside
+// the catalogue) is never written: it stays zero.
 template <int NP, int LT>
-__device__ __forceinline__ uint32_t eval_adjoint(const GroupArgs& g, int32_t id, const float (&ga)[LT],
-                                                 float2* acc) {
-    const float* row = g.table + (size_t)id * NP;
-    float v[NP];
-    if constexpr (NP % 8 == 0) {
+__global__ void __launch_bounds__(256) adj_masks_kernel(const GroupArgs g, int32_t catalogue, int32_t words,
+                                                        uint2* __restrict__ masks, uint32_t* __restrict__ bits) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool rel = false;
+    if (i < catalogue) {
+        const float4* row = reinterpret_cast<const float4*>(g.table) + i * (NP / 4);
+        float v[NP];
 #pragma unroll
-        for (int q = 0; q < NP / 8; ++q) ld_row8(row + 8 * q, v + 8 * q);
-    } else {
-#pragma unroll
-        for (int q = 0; q < NP / 4; ++q) ld_row4(row + 4 * q, v + 4 * q);
-    }
-    float f[NP];
-    uint32_t fmid = 0u;  // bit k: F_k on its middle branch
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        const float wf = __fmaf_rn(g.m[k], v[k], -g.d[k]);
-        f[k] = fminf(fmaxf(wf, 0.0f), g.lim[k]);
-        if (wf > 0.0f && wf < g.lim[k]) fmid |= 1u << k;
-    }
-    uint32_t bits = 0u;
-    float mw[LT];  // g_j a_j [o_dj on its middle branch]
-#pragma unroll
-    for (int j = 0; j < LT; ++j) {
-        float x = 0.0f;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            // member columns in the group's ELT order (the same roundings as
-            // the forward's 0/1-coefficient FMA chain)
-            if (LT == 1 || (g.member[j] & (1u << k))) x += f[k];
+        for (int q = 0; q < NP / 4; ++q) {
+            const float4 r = __ldcs(row + q);
+            v[4 * q + 0] = r.x;
+            v[4 * q + 1] = r.y;
+            v[4 * q + 2] = r.z;
+            v[4 * q + 3] = r.w;
         }
-        const float wo = x - g.occ_ret[j];  // the forward's occurrence subtraction
-        const bool mid = wo > 0.0f && wo < g.occ_lim[j];
-        if (mid) bits |= 1u << j;
-        if (wo > g.occ_lim[j]) bits |= 1u << (8 + j);
-        mw[j] = mid ? ga[j] : 0.0f;
-    }
-    if (bits & 0xffu) {
+        float f[NP];
+        uint32_t u = 0u;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            if ((fmid >> k) & 1u) {
-                float wk = 0.0f;
+            const float wf = __fmaf_rn(g.m[k], v[k], -g.d[k]);
+            f[k] = fminf(fmaxf(wf, 0.0f), g.lim[k]);
+            if (wf > 0.0f && wf < g.lim[k]) u |= 1u << k;
+        }
+        uint32_t mk = 0u;
 #pragma unroll
-                for (int j = 0; j < LT; ++j) {
-                    if constexpr (LT == 1) wk += mw[j];
-                    else wk = __fmaf_rn(g.coef[j][k], mw[j], wk);
+        for (int j = 0; j < LT; ++j) {
+            if (j < g.n_layers) {
+                float x = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    if constexpr (LT == 1) x += f[k];
+                    else x = __fmaf_rn(g.coef[j][k], f[k], x);
                 }
-                if (wk != 0.0f) {
-                    float2 a = acc[32 * k];
-                    two_sum_add(a, v[k] * wk);
-                    acc[32 * k] = a;
-                }
+                const float wo = x - g.occ_ret[j];  // the forward's occurrence subtraction
+                if (wo > 0.0f && wo < g.occ_lim[j]) mk |= 1u << j;
+                if (wo > g.occ_lim[j]) mk |= 1u << (8 + j);
             }
         }
+        masks[i] = make_uint2(mk, (mk & 0xffu) ? u : 0u);
+        rel = mk != 0u;
     }
-    return bits;
+    const unsigned m = __ballot_sync(0xffffffffu, rel);
+    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bits[i >> 5] = m;
 }
 
-// Lane j < LT adds the warp's count of events on layer j's middle and capped
-// occurrence branches.
-template <int LT>
-__device__ __forceinline__ void count_branches(uint32_t bits, int lane, uint32_t& n_mid, uint32_t& n_cap) {
-#pragma unroll
-    for (int j = 0; j < LT; ++j) {
-        const uint32_t m = __reduce_add_sync(0xffffffffu, (bits >> j) & 1u);
-        const uint32_t c = __reduce_add_sync(0xffffffffu, (bits >> (8 + j)) & 1u);
-        if (lane == j) {
-            n_mid += m;
-            n_cap += c;
-        }
-    }
-}
-
+// One queued event on one lane: the packed layer counters and, when a layer
+// is on its middle branch, the column partials.
 template <int NP, int LT>
-__global__ void __launch_bounds__(kAgThreads, 2) adjoint_group_kernel(const GroupArgs g, const YetArgs y,
-                                                                      const uint8_t* __restrict__ branch,
-                                                                      const double* __restrict__ gw,
-                                                                      double* __restrict__ partial) {
+__device__ __forceinline__ void eval_event(const GroupArgs& g, const uint2* __restrict__ masks, uint32_t id,
+                                           const uint64_t* s_spread, const float* s_w, const uint32_t* s_col,
+                                           uint64_t& cnt_mid, uint64_t& cnt_cap, float (&part)[NP]) {
+    const uint2 mk = ld_mask(masks + id);
+    const uint32_t m = mk.x & 0xffu;
+    cnt_mid += s_spread[m];
+    cnt_cap += s_spread[(mk.x >> 8) & 0xffu];
+    if (mk.y != 0u) {  // U is stored only where M is non-zero
+        const float* row = g.table + (size_t)id * NP;
+        float v[NP];
+        if constexpr (NP % 8 == 0) {
+#pragma unroll
+            for (int q = 0; q < NP / 8; ++q) ld_row8(row + 8 * q, v + 8 * q);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NP / 4; ++q) ld_row4(row + 4 * q, v + 4 * q);
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+            if ((mk.y >> k) & 1u) part[k] = __fmaf_rn(v[k], s_w[m & s_col[k]], part[k]);
+    }
+}
+
+template <int NP, int LT, bool VEC, bool FOLD>
+__global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const GroupArgs g, const YetArgs y,
+                                                                     const uint2* __restrict__ masks,
+                                                                     const uint32_t* __restrict__ gbits,
+                                                                     const int32_t smem_words,
+                                                                     const uint8_t* __restrict__ branch,
+                                                                     const double* __restrict__ gw,
+                                                                     double* __restrict__ partial) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int E = kAgIds;
-    constexpr int W = 4 * LT + NP;  // OccR[LT], OccL[LT], AggR[LT], AggL[LT], then the columns
-    extern __shared__ __align__(16) float2 s_acc[];  // [kAgWarps][NP][32]: every lane's column pairs
-    __shared__ int32_t s_queue[kAgWarps][kAgQueue];
-    __shared__ double s_red[kAgWarps][W];
+    constexpr int NW = 1 << LT;      // entries of a warp's weight table
+    constexpr int W = 4 * LT + NP;   // OccR[LT], OccL[LT], AggR[LT], AggL[LT], then the columns
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    uint64_t* s_spread = reinterpret_cast<uint64_t*>(s_dyn);            // [256]
+    double* s_red = reinterpret_cast<double*>(s_dyn + 512);              // [kAgWarps][W]
+    uint32_t* s_col = s_dyn + 512 + 2 * kAgWarps * W;                    // [32]
+    float* s_wt = reinterpret_cast<float*>(s_col + 32);                  // [kAgWarps][NW]
+    int32_t* s_queue = reinterpret_cast<int32_t*>(s_wt + kAgWarps * NW); // [kAgWarps][kAgQueue]
+    uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_queue + kAgWarps * kAgQueue);
+    {
+        // s_spread[m]: byte j is bit j of m (adds one to layer j's counter)
+        for (int m = threadIdx.x; m < 256; m += blockDim.x) {
+            uint64_t v = 0;
+            for (int j = 0; j < 8; ++j) v |= (uint64_t)((m >> j) & 1) << (8 * j);
+            s_spread[m] = v;
+        }
+        if (threadIdx.x < 32) {
+            uint32_t c = 0;
+            for (int j = 0; j < LT; ++j)
+                if (j < g.n_layers) c |= ((g.member[j] >> threadIdx.x) & 1u) << j;
+            s_col[threadIdx.x] = c;
+        }
+        const uint4* src = reinterpret_cast<const uint4*>(gbits);
+        uint4* dst = reinterpret_cast<uint4*>(s_bits);
+        const int words = (y.catalogue >> 5) + 1;  // bits 0 .. C (C: the sentinel)
+        for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) {
+            uint4 v = src[i];
+            if (FOLD && 4 * i + smem_words < words) {  // the bitmap is zero-padded to whole uint4
+                const uint4 u = src[i + smem_words / 4];
+                v.x |= u.x;
+                v.y |= u.y;
+                v.z |= u.z;
+                v.w |= u.w;
+            }
+            dst[i] = v;
+        }
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int32_t* q = s_queue[wib];
-    float2* acc = s_acc + (size_t)wib * NP * 32 + lane;
-#pragma unroll
-    for (int k = 0; k < NP; ++k) acc[32 * k] = make_float2(0.0f, 0.0f);
+    int32_t* q = s_queue + wib * kAgQueue;
+    float* s_w = s_wt + wib * NW;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n_warps = (int64_t)gridDim.x * kAgWarps;
 
-    // lane j < LT keeps layer j's four term sums
+    // lane j < LT keeps layer j's four term sums; lane k < NP column k's pair
     double acc_or = 0.0, acc_ol = 0.0, acc_ar = 0.0, acc_al = 0.0;
+    float col_h = 0.0f, col_l = 0.0f;
     int32_t my_layer = -1;
 #pragma unroll
     for (int j = 0; j < LT; ++j)
@@ -186,54 +230,107 @@ __global__ void __launch_bounds__(kAgThreads, 2) adjoint_group_kernel(const Grou
         if (code == 2) acc_al += gt;
         const bool mid_l = code == 1 && gt != 0.0;
         if (!__ballot_sync(FULL, mid_l)) continue;  // no layer of the group has a middle-branch weight
-        float ga[LT];
+        // the trial's weight table W[S] = sum_{j in S} g_j a_j
+        {
+            float ga[LT];
 #pragma unroll
-        for (int j = 0; j < LT; ++j) ga[j] = __shfl_sync(FULL, mid_l ? (float)gt : 0.0f, j);
-        uint32_t n_mid = 0, n_cap = 0;
+            for (int j = 0; j < LT; ++j) ga[j] = __shfl_sync(FULL, mid_l ? (float)gt : 0.0f, j);
+            for (int s = lane; s < NW; s += 32) {
+                float w = 0.0f;
+#pragma unroll
+                for (int j = 0; j < LT; ++j)
+                    if ((s >> j) & 1) w += ga[j];
+                s_w[s] = w;
+            }
+            __syncwarp();
+        }
+        uint64_t cnt_mid = 0, cnt_cap = 0;
+        float part[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) part[k] = 0.0f;
+        // lane j adds the warp's counts of layer j, scaled by g_j, and clears them
+        auto flush_counts = [&]() {
+#pragma unroll
+            for (int j = 0; j < LT; ++j) {
+                const uint32_t cm = __reduce_add_sync(FULL, (uint32_t)(cnt_mid >> (8 * j)) & 0xffu);
+                const uint32_t cc = __reduce_add_sync(FULL, (uint32_t)(cnt_cap >> (8 * j)) & 0xffu);
+                if (lane == j && mid_l) {
+                    acc_or -= gt * (double)cm;
+                    acc_ol += gt * (double)cc;
+                }
+            }
+            cnt_mid = 0;
+            cnt_cap = 0;
+        };
         int64_t b, e;
         bool bad_off;
         trial_range(y, t, b, e, bad_off);
-        int qn = 0;  // warp-uniform, < 32 between chunks
+        int qn = 0;        // warp-uniform, < 32 between chunks
+        int batches = 0;   // batches since the counters were cleared (each lane's byte counters < 256)
         for (int64_t c0 = b; c0 < e; c0 += 32 * E) {
-            int32_t id[E];
+            uint32_t uid[E];
+            if constexpr (VEC) {
+#pragma unroll
+                for (int h = 0; h < E / 4; ++h) {
+                    const int64_t d = c0 + 128 * h + 4 * lane;
+                    int4 w4 = make_int4(-1, -1, -1, -1);
+                    if (d < e) w4 = __ldcs(reinterpret_cast<const int4*>(y.ids + d));  // e and d are multiples of 4
+                    uid[4 * h + 0] = min((uint32_t)w4.x, (uint32_t)y.catalogue);
+                    uid[4 * h + 1] = min((uint32_t)w4.y, (uint32_t)y.catalogue);
+                    uid[4 * h + 2] = min((uint32_t)w4.z, (uint32_t)y.catalogue);
+                    uid[4 * h + 3] = min((uint32_t)w4.w, (uint32_t)y.catalogue);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int64_t d = c0 + 32 * k + lane;
+                    uid[k] = d < e ? min((uint32_t)ld_stream(y.ids + d), (uint32_t)y.catalogue)
+                                   : (uint32_t)y.catalogue;
+                }
+            }
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const int64_t d = c0 + 32 * k + lane;
-                id[k] = d < e ? ld_stream(y.ids + d) : -1;
-            }
-            uint32_t word[E];
-#pragma unroll
-            for (int k = 0; k < E; ++k)
-                word[k] = (unsigned)id[k] < (unsigned)y.catalogue ? ld_bits(g.bitmap + (id[k] >> 5)) : 0u;
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const bool nz = (word[k] >> (id[k] & 31)) & 1u;
-                const unsigned m = __ballot_sync(FULL, nz);
-                if (nz) q[qn + __popc(m & lt_mask)] = id[k];
-                qn += __popc(m);
-            }
-            // evaluate full batches of 32 from the top of the queue
-            while (qn >= 32) {
-                __syncwarp();
-                const int32_t mine = q[qn - 32 + lane];
-                __syncwarp();
-                qn -= 32;
-                const uint32_t bits = eval_adjoint<NP, LT>(g, mine, ga, acc);
-                count_branches<LT>(bits, lane, n_mid, n_cap);
+                uint32_t wi = uid[k] >> 5;
+                uint32_t w;
+                if constexpr (FOLD) {
+                    wi = wi >= (uint32_t)smem_words ? wi - (uint32_t)smem_words : wi;
+                    w = s_bits[wi];
+                } else {
+                    w = wi < (uint32_t)smem_words ? s_bits[wi] : ld_bits_global(gbits + wi);
+                }
+                const bool nz = (w >> (uid[k] & 31)) & 1u;
+                const unsigned mm = __ballot_sync(FULL, nz);
+                if (nz) q[qn + __popc(mm & lt_mask)] = (int32_t)uid[k];
+                qn += __popc(mm);
+                if (qn >= 32) {
+                    __syncwarp();
+                    const int32_t mine = q[lane];
+                    const int32_t carry = q[32 + lane];
+                    __syncwarp();
+                    q[lane] = carry;  // entries 32 .. qn-1 move to the front
+                    qn -= 32;
+                    eval_event<NP, LT>(g, masks, (uint32_t)mine, s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
+                    if (++batches == 255) {
+                        flush_counts();
+                        batches = 0;
+                    }
+                    __syncwarp();
+                }
             }
         }
         __syncwarp();
-        if (qn > 0) {
-            const int32_t mine = lane < qn ? q[lane] : -1;
-            __syncwarp();
-            const uint32_t bits = mine >= 0 ? eval_adjoint<NP, LT>(g, mine, ga, acc) : 0u;
-            count_branches<LT>(bits, lane, n_mid, n_cap);
+        if (lane < qn) eval_event<NP, LT>(g, masks, (uint32_t)q[lane], s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
+        __syncwarp();
+        flush_counts();
+        // the trial's column partials, summed across the warp, go to lane k's pair
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float v = part[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+            if (lane == k) two_sum_add(col_h, col_l, v);
         }
-        // the trial's occurrence counts, scaled by the layer's weight, on lane j
-        if (mid_l) {
-            acc_or -= gt * (double)n_mid;
-            acc_ol += gt * (double)n_cap;
-        }
+        __syncwarp();  // the weight table is rebuilt by the next trial
     }
     // the lane values in FP64, reduced warp -> CTA in a fixed order
 #pragma unroll
@@ -244,16 +341,15 @@ __global__ void __launch_bounds__(kAgThreads, 2) adjoint_group_kernel(const Grou
             const double mine = c == 0 ? acc_or : c == 1 ? acc_ol : c == 2 ? acc_ar : acc_al;
             v = lane == j ? mine : 0.0;
         } else {
-            const float2 a = acc[32 * (i - 4 * LT)];
-            v = (double)a.x + (double)a.y;
+            v = lane == i - 4 * LT ? (double)col_h + (double)col_l : 0.0;
         }
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-        if (lane == 0) s_red[wib][i] = v;
+        if (lane == 0) s_red[wib * W + i] = v;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         double s = 0.0;
-        for (int wv = 0; wv < kAgWarps; ++wv) s += s_red[wv][i];
+        for (int wv = 0; wv < kAgWarps; ++wv) s += s_red[wv * W + i];
         partial[(size_t)blockIdx.x * W + i] = s;
     }
 }
@@ -286,47 +382,70 @@ __global__ void group_scatter_kernel(const double* __restrict__ partial, int nbl
     }
 }
 
+struct Scratch {
+    uint2* masks;     // [C + 1]
+    uint32_t* bits;   // zero-padded to whole 16-byte groups, bits 0 .. C
+    double* partial;  // [num_sms][4 * 8 + 32]
+};
+
 template <int NP, int LT>
 cudaError_t launch_one(const GroupArgs& g, const GroupIndex& gix, const YetArgs& y, const uint8_t* branch,
-                       const double* gw, double* partial, int num_sms, int max_blocks, double* grad_terms,
-                       double* grad_mult, cudaStream_t s) {
-    const int smem = (int)sizeof(float2) * kAgWarps * NP * 32;
-    auto kern = adjoint_group_kernel<NP, LT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int per_sm = 0;
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAgThreads, smem);
-    if (e) return e;
-    const int nblk = std::max(1, std::min(max_blocks, num_sms * std::max(1, per_sm)));
-    kern<<<nblk, kAgThreads, smem, s>>>(g, y, branch, gw, partial);
+                       const double* gw, const Scratch& sc, int num_sms, double* grad_terms, double* grad_mult,
+                       cudaStream_t s) {
+    const int32_t C = y.catalogue;
+    const int32_t words_w = (int32_t)(((int64_t)C + 31) / 32);  // words the mask kernel writes
+    adj_masks_kernel<NP, LT><<<(unsigned)(((int64_t)words_w * 32 + 255) / 256), 256, 0, s>>>(g, C, words_w, sc.masks,
+                                                                                            sc.bits);
+    cudaError_t e = cudaGetLastError();
+    if (e || y.n_trials == 0) return e;
+    int dev = 0, max_optin = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    constexpr int W = 4 * LT + NP;
+    const int fixed = 4 * (512 + 2 * kAgWarps * W + 32 + kAgWarps * (1 << LT) + kAgWarps * kAgQueue);
+    const int words = (C >> 5) + 1;  // bits 0 .. C (C: the sentinel)
+    const int smem_words = std::max(4, std::min((words + 3) & ~3, (max_optin - fixed) / 4) & ~3);
+    const int smem = fixed + 4 * smem_words;
+    const bool fold = words <= 2 * smem_words;
+    const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
+    auto kern = vec ? (fold ? adjoint_pass_kernel<NP, LT, true, true> : adjoint_pass_kernel<NP, LT, true, false>)
+                    : (fold ? adjoint_pass_kernel<NP, LT, false, true> : adjoint_pass_kernel<NP, LT, false, false>);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms, (y.n_trials + kAgWarps - 1) / kAgWarps));
+    kern<<<nblk, kAgThreads, smem, s>>>(g, y, sc.masks, sc.bits, smem_words, branch, gw, sc.partial);
     if ((e = cudaGetLastError())) return e;
-    group_scatter_kernel<<<1, 128, 0, s>>>(partial, nblk, LT, NP, gix, grad_terms, grad_mult);
+    group_scatter_kernel<<<1, 128, 0, s>>>(sc.partial, nblk, LT, NP, gix, grad_terms, grad_mult);
     return cudaGetLastError();
 }
 
 template <int NP>
 cudaError_t launch_lt(const GroupArgs& g, const GroupIndex& gix, const YetArgs& y, const uint8_t* branch,
-                      const double* gw, double* partial, int num_sms, int max_blocks, double* gt, double* gm,
-                      cudaStream_t s) {
-    if (g.n_layers <= 1) return launch_one<NP, 1>(g, gix, y, branch, gw, partial, num_sms, max_blocks, gt, gm, s);
-    if (g.n_layers <= 2) return launch_one<NP, 2>(g, gix, y, branch, gw, partial, num_sms, max_blocks, gt, gm, s);
-    if (g.n_layers <= 4) return launch_one<NP, 4>(g, gix, y, branch, gw, partial, num_sms, max_blocks, gt, gm, s);
-    return launch_one<NP, 8>(g, gix, y, branch, gw, partial, num_sms, max_blocks, gt, gm, s);
+                      const double* gw, const Scratch& sc, int num_sms, double* gt, double* gm, cudaStream_t s) {
+    if (g.n_layers <= 1) return launch_one<NP, 1>(g, gix, y, branch, gw, sc, num_sms, gt, gm, s);
+    if (g.n_layers <= 2) return launch_one<NP, 2>(g, gix, y, branch, gw, sc, num_sms, gt, gm, s);
+    if (g.n_layers <= 4) return launch_one<NP, 4>(g, gix, y, branch, gw, sc, num_sms, gt, gm, s);
+    return launch_one<NP, 8>(g, gix, y, branch, gw, sc, num_sms, gt, gm, s);
 }
 
 }  // namespace
 
 cudaError_t launch_adjoint_groups(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,
                                   double* grad_terms, double* grad_mult, cudaStream_t s) {
-    // at most 8 CTAs of 256 threads are resident per SM
-    const int max_blocks = p->num_sms * 8;
-    const size_t part_bytes = sizeof(double) * (size_t)max_blocks * (4 * kMaxGroupLayers + kMaxLayerElts);
-    double* partial = nullptr;
-    cudaError_t err = cudaMallocAsync((void**)&partial, part_bytes, s);
+    const size_t C = (size_t)p->catalogue;
+    const size_t mask_bytes = sizeof(uint2) * (C + 1);
+    const size_t bit_bytes = 16 * ((C / 32 + 1 + 3) / 4);
+    const size_t part_bytes = sizeof(double) * (size_t)p->num_sms * (4 * kMaxGroupLayers + kMaxLayerElts);
+    const size_t a1 = (mask_bytes + 255) & ~(size_t)255, a2 = (bit_bytes + 255) & ~(size_t)255;
+    char* w = nullptr;
+    cudaError_t err = cudaMallocAsync((void**)&w, a1 + a2 + part_bytes, s);
     if (err) return err;
+    Scratch sc{reinterpret_cast<uint2*>(w), reinterpret_cast<uint32_t*>(w + a1), reinterpret_cast<double*>(w + a1 + a2)};
     do {
         if ((err = cudaMemsetAsync(grad_terms, 0, sizeof(double) * 4 * p->n_layers, s))) break;
         if ((err = cudaMemsetAsync(grad_mult, 0, sizeof(double) * p->n_elt, s))) break;
         if (y.n_trials == 0) break;
+        // the sentinel row and the padding words stay zero for every group
+        if ((err = cudaMemsetAsync(w, 0, a1 + a2, s))) break;
         for (size_t gi = 0; gi < p->groups.size() && !err; ++gi) {
             const GroupArgs& ga = p->groups[gi];
             GroupIndex gix{};
@@ -338,16 +457,16 @@ cudaError_t launch_adjoint_groups(art_portfolio* p, const YetArgs& y, const uint
             double* gt = grad_terms;
             double* gm = grad_mult;
             switch (p->group_np[gi]) {
-                case 4: err = launch_lt<4>(ga, gix, y, branch, g, partial, ns, max_blocks, gt, gm, s); break;
-                case 8: err = launch_lt<8>(ga, gix, y, branch, g, partial, ns, max_blocks, gt, gm, s); break;
-                case 16: err = launch_lt<16>(ga, gix, y, branch, g, partial, ns, max_blocks, gt, gm, s); break;
-                case 24: err = launch_lt<24>(ga, gix, y, branch, g, partial, ns, max_blocks, gt, gm, s); break;
-                case 32: err = launch_lt<32>(ga, gix, y, branch, g, partial, ns, max_blocks, gt, gm, s); break;
+                case 4: err = launch_lt<4>(ga, gix, y, branch, g, sc, ns, gt, gm, s); break;
+                case 8: err = launch_lt<8>(ga, gix, y, branch, g, sc, ns, gt, gm, s); break;
+                case 16: err = launch_lt<16>(ga, gix, y, branch, g, sc, ns, gt, gm, s); break;
+                case 24: err = launch_lt<24>(ga, gix, y, branch, g, sc, ns, gt, gm, s); break;
+                case 32: err = launch_lt<32>(ga, gix, y, branch, g, sc, ns, gt, gm, s); break;
                 default: err = cudaErrorInvalidValue;
             }
         }
     } while (0);
-    const cudaError_t e2 = cudaFreeAsync(partial, s);
+    const cudaError_t e2 = cudaFreeAsync(w, s);
     return err ? err : e2;
 }
 
