@@ -23,7 +23,8 @@
 //   - the layer counts: per lane, 8-bit counters for the 8 layers packed in
 //     a 64-bit word, incremented by a table lookup of M (and K); reduced
 //     across the warp with integer reductions at the end of the trial (and
-//     every 255 batches), then lane j scales layer j's counts by g_j in FP64;
+//     every 255 batches), then lane j adds layer j's counts times g_j (g_j
+//     rounded to FP32, the product exact) to a compensated FP32 pair;
 //   - the multipliers: for each column k in U_i with M_i non-zero, the lane
 //     adds l_ik * W[M_i & C_k] to its FP32 partial of column k, where C_k is
 //     the set of layers covering column k and W[S] = sum_{j in S} g_j a_j is
@@ -32,9 +33,10 @@
 //     warp and lane k adds the total to its compensated FP32 pair.
 // A trial with no layer on the middle branch costs only its branch codes.
 // The lane values are reduced warp -> CTA -> grid in a fixed order (no
-// atomics: deterministic). Rounding: the per-event products and the W
-// entries are FP32 (a few units in the last place of FP32 per term), the
-// sums compensated or FP64.
+// atomics: deterministic); FP64 arithmetic runs only in that final
+// reduction. Rounding: g is rounded to FP32 once per (layer, trial), and the
+// per-event products and the W entries are FP32 (a few units in the last
+// place of FP32 per term); every sum is compensated or FP64.
 #include <algorithm>
 #include <limits>
 
@@ -134,22 +136,25 @@ __global__ void __launch_bounds__(256) adj_masks_kernel(const GroupArgs g, int32
 // is on its middle branch, the column partials.
 template <int NP, int LT>
 __device__ __forceinline__ void eval_event(const GroupArgs& g, const uint2* __restrict__ masks, uint32_t id,
-                                           const uint64_t* s_spread, const float* s_w, const uint32_t* s_col,
+                                           uint32_t last_row, const uint64_t* s_spread, const float* s_w, const uint32_t* s_col,
                                            uint64_t& cnt_mid, uint64_t& cnt_cap, float (&part)[NP]) {
+    // the row is requested together with the masks (most queued events need
+    // it), so the two gathers overlap; the sentinel C (zero masks) reads the
+    // last row instead, unused
     const uint2 mk = ld_mask(masks + id);
+    const float* row = g.table + (size_t)min(id, last_row) * NP;
+    float v[NP];
+    if constexpr (NP % 8 == 0) {
+#pragma unroll
+        for (int q = 0; q < NP / 8; ++q) ld_row8(row + 8 * q, v + 8 * q);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) ld_row4(row + 4 * q, v + 4 * q);
+    }
     const uint32_t m = mk.x & 0xffu;
     cnt_mid += s_spread[m];
     cnt_cap += s_spread[(mk.x >> 8) & 0xffu];
     if (mk.y != 0u) {  // U is stored only where M is non-zero
-        const float* row = g.table + (size_t)id * NP;
-        float v[NP];
-        if constexpr (NP % 8 == 0) {
-#pragma unroll
-            for (int q = 0; q < NP / 8; ++q) ld_row8(row + 8 * q, v + 8 * q);
-        } else {
-#pragma unroll
-            for (int q = 0; q < NP / 4; ++q) ld_row4(row + 4 * q, v + 4 * q);
-        }
 #pragma unroll
         for (int k = 0; k < NP; ++k)
             if ((mk.y >> k) & 1u) part[k] = __fmaf_rn(v[k], s_w[m & s_col[k]], part[k]);
@@ -210,8 +215,10 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n_warps = (int64_t)gridDim.x * kAgWarps;
 
-    // lane j < LT keeps layer j's four term sums; lane k < NP column k's pair
-    double acc_or = 0.0, acc_ol = 0.0, acc_ar = 0.0, acc_al = 0.0;
+    // lane j < LT keeps layer j's four term sums, lane k < NP column k's sum,
+    // each a compensated FP32 pair (FP64 arithmetic per trial would dominate:
+    // the FP64 pipe of this part is slow)
+    float or_h = 0.0f, or_l = 0.0f, ol_h = 0.0f, ol_l = 0.0f, ar_h = 0.0f, ar_l = 0.0f, al_h = 0.0f, al_l = 0.0f;
     float col_h = 0.0f, col_l = 0.0f;
     int32_t my_layer = -1;
 #pragma unroll
@@ -219,22 +226,22 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
         if (lane == j && j < g.n_layers) my_layer = g.layer[j];
 
     for (int64_t t = (int64_t)blockIdx.x * kAgWarps + wib; t < y.n_trials; t += n_warps) {
-        double gt = 0.0;
+        float gt = 0.0f;  // the layer's weight, rounded to FP32 once
         uint8_t code = 0;
         if (my_layer >= 0) {
             const size_t wi = (size_t)my_layer * (size_t)y.n_trials + (size_t)t;
             code = branch[wi];
-            gt = gw[wi];
+            gt = (float)gw[wi];
         }
-        if (code == 1) acc_ar -= gt;
-        if (code == 2) acc_al += gt;
-        const bool mid_l = code == 1 && gt != 0.0;
+        if (code == 1) two_sum_add(ar_h, ar_l, -gt);
+        if (code == 2) two_sum_add(al_h, al_l, gt);
+        const bool mid_l = code == 1 && gt != 0.0f;
         if (!__ballot_sync(FULL, mid_l)) continue;  // no layer of the group has a middle-branch weight
         // the trial's weight table W[S] = sum_{j in S} g_j a_j
         {
             float ga[LT];
 #pragma unroll
-            for (int j = 0; j < LT; ++j) ga[j] = __shfl_sync(FULL, mid_l ? (float)gt : 0.0f, j);
+            for (int j = 0; j < LT; ++j) ga[j] = __shfl_sync(FULL, mid_l ? gt : 0.0f, j);
             for (int s = lane; s < NW; s += 32) {
                 float w = 0.0f;
 #pragma unroll
@@ -248,15 +255,19 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
         float part[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) part[k] = 0.0f;
-        // lane j adds the warp's counts of layer j, scaled by g_j, and clears them
+        // lane j adds the warp's counts of layer j, scaled by g_j, and clears
+        // them; the products are exact (FMA residual), the sums compensated
         auto flush_counts = [&]() {
 #pragma unroll
             for (int j = 0; j < LT; ++j) {
                 const uint32_t cm = __reduce_add_sync(FULL, (uint32_t)(cnt_mid >> (8 * j)) & 0xffu);
                 const uint32_t cc = __reduce_add_sync(FULL, (uint32_t)(cnt_cap >> (8 * j)) & 0xffu);
                 if (lane == j && mid_l) {
-                    acc_or -= gt * (double)cm;
-                    acc_ol += gt * (double)cc;
+                    const float pm = gt * (float)cm, pc = gt * (float)cc;  // counts < 2^24: exact in FP32
+                    two_sum_add(or_h, or_l, -pm);
+                    or_l -= __fmaf_rn(gt, (float)cm, -pm);
+                    two_sum_add(ol_h, ol_l, pc);
+                    ol_l += __fmaf_rn(gt, (float)cc, -pc);
                 }
             }
             cnt_mid = 0;
@@ -267,27 +278,35 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
         trial_range(y, t, b, e, bad_off);
         int qn = 0;        // warp-uniform, < 32 between chunks
         int batches = 0;   // batches since the counters were cleared (each lane's byte counters < 256)
-        for (int64_t c0 = b; c0 < e; c0 += 32 * E) {
-            uint32_t uid[E];
+        // ids of a chunk of 32 * E events from c0 (the sentinel C past the end)
+        auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
             if constexpr (VEC) {
 #pragma unroll
                 for (int h = 0; h < E / 4; ++h) {
                     const int64_t d = c0 + 128 * h + 4 * lane;
                     int4 w4 = make_int4(-1, -1, -1, -1);
                     if (d < e) w4 = __ldcs(reinterpret_cast<const int4*>(y.ids + d));  // e and d are multiples of 4
-                    uid[4 * h + 0] = min((uint32_t)w4.x, (uint32_t)y.catalogue);
-                    uid[4 * h + 1] = min((uint32_t)w4.y, (uint32_t)y.catalogue);
-                    uid[4 * h + 2] = min((uint32_t)w4.z, (uint32_t)y.catalogue);
-                    uid[4 * h + 3] = min((uint32_t)w4.w, (uint32_t)y.catalogue);
+                    v[4 * h + 0] = (uint32_t)w4.x;
+                    v[4 * h + 1] = (uint32_t)w4.y;
+                    v[4 * h + 2] = (uint32_t)w4.z;
+                    v[4 * h + 3] = (uint32_t)w4.w;
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const int64_t d = c0 + 32 * k + lane;
-                    uid[k] = d < e ? min((uint32_t)ld_stream(y.ids + d), (uint32_t)y.catalogue)
-                                   : (uint32_t)y.catalogue;
+                    v[k] = d < e ? (uint32_t)ld_stream(y.ids + d) : 0xffffffffu;
                 }
             }
+        };
+        uint32_t pre[E];
+        if (b < e) load_ids(b, pre);
+        for (int64_t c0 = b; c0 < e; c0 += 32 * E) {
+            uint32_t uid[E];
+#pragma unroll
+            for (int k = 0; k < E; ++k) uid[k] = min(pre[k], (uint32_t)y.catalogue);
+            // request the trial's next chunk before this one is processed
+            if (c0 + 32 * E < e) load_ids(c0 + 32 * E, pre);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 uint32_t wi = uid[k] >> 5;
@@ -309,7 +328,7 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
                     __syncwarp();
                     q[lane] = carry;  // entries 32 .. qn-1 move to the front
                     qn -= 32;
-                    eval_event<NP, LT>(g, masks, (uint32_t)mine, s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
+                    eval_event<NP, LT>(g, masks, (uint32_t)mine, (uint32_t)y.catalogue - 1u, s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
                     if (++batches == 255) {
                         flush_counts();
                         batches = 0;
@@ -319,7 +338,7 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
             }
         }
         __syncwarp();
-        if (lane < qn) eval_event<NP, LT>(g, masks, (uint32_t)q[lane], s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
+        if (lane < qn) eval_event<NP, LT>(g, masks, (uint32_t)q[lane], (uint32_t)y.catalogue - 1u, s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
         __syncwarp();
         flush_counts();
         // the trial's column partials, summed across the warp, go to lane k's pair
@@ -338,7 +357,10 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
         double v;
         if (i < 4 * LT) {
             const int c = i / LT, j = i % LT;
-            const double mine = c == 0 ? acc_or : c == 1 ? acc_ol : c == 2 ? acc_ar : acc_al;
+            const double mine = c == 0   ? (double)or_h + (double)or_l
+                                : c == 1 ? (double)ol_h + (double)ol_l
+                                : c == 2 ? (double)ar_h + (double)ar_l
+                                         : (double)al_h + (double)al_l;
             v = lane == j ? mine : 0.0;
         } else {
             v = lane == i - 4 * LT ? (double)col_h + (double)col_l : 0.0;

@@ -203,7 +203,9 @@ def test_group_adjoint_many_groups_matches_layer_adjoint_and_oracle():
         assert len({int(x) for x in np.unique(br.cpu().numpy())}) == 3
         gt_g, gm_g = _adjoint(pg, yet, br, g, L, E)
         gt_l, gm_l = _adjoint(pl, yet, br, g, L, E)
-        np.testing.assert_allclose(gt_g, gt_l, rtol=1e-9, atol=1e-12)
+        # the group path rounds each weight g to FP32 once (relative 2^-24 per
+        # term); the per-layer path applies it in FP64
+        np.testing.assert_allclose(gt_g, gt_l, rtol=1e-6, atol=1e-12)
         np.testing.assert_allclose(gm_g, gm_l, rtol=2e-6, atol=1e-9 * np.abs(gm_l).max())
         ot, om, _, _ = oracle.grad(w.oracle_problem(), g_host)
         np.testing.assert_allclose(gt_g, ot, rtol=1e-6, atol=1e-9)
