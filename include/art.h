@@ -356,9 +356,14 @@ typedef struct {
  * art_autotune -- pick the forward variant and the persistent kernels' tile
  * shapes (layer tile: 32, 64 or 128 layers per warp; trials per work unit
  * 1-16; 128 or 256 threads per CTA) by timing each candidate on the first
- * `sample_trials` trials (0: 65,536) of the given YET, and keep the fastest
- * in the portfolio (as art_set_variant would). ylt_dev receives the sample's
- * YLT ([n_layers][sample] FP64; caller-owned scratch). When the environment
+ * `sample_trials` trials (0: 65,536) of the given YET, and keep the one
+ * whose time, extrapolated to n_trials, is least (as art_set_variant would
+ * set it). When n_trials is at least twice the sample, each variant's
+ * fastest shape is also timed on twice the sample, which separates the part
+ * of a call that does not grow with the trials (such as the skip variant's
+ * per-call occurrence tables) from the part that does; otherwise times
+ * scale in proportion. ylt_dev is caller-owned scratch for the timed runs'
+ * YLTs: [n_layers][min(n_trials, 2 * sample)] FP64. When the environment
  * variable ART_AUTOTUNE_CACHE names a file, a shape recorded there for the
  * same device, portfolio shape and YET shape (trials bucketed by powers of
  * two) is applied without timing, and a newly timed shape is appended.

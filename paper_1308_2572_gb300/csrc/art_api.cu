@@ -1056,27 +1056,56 @@ art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event
         }
     }
     const int32_t saved[5] = {p->variant, p->slots, p->trial_tile, p->cta_threads, p->sparse_mapping};
-    float best_ms = -1.0f;
     cudaEvent_t a = nullptr, b = nullptr;
     if ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))) return fail(e);
-    for (const auto& c : cands) {
-        if ((e = apply_shape(p, c.data()))) break;
-        if ((e = run_forward(p, c[0], y, ylt_dev, nullptr, stream))) break;  // warm-up
-        float ms_best = -1.0f;
-        for (int r = 0; r < 2 && !e; ++r) {
+    // best of two timed forwards (after one warm-up) over the first nt trials
+    auto time_shape = [&](const std::array<int32_t, 5>& c, int64_t nt, float& ms_best) -> cudaError_t {
+        YetArgs yt = y;
+        yt.n_trials = nt;
+        cudaError_t err = apply_shape(p, c.data());
+        if (!err) err = run_forward(p, c[0], yt, ylt_dev, nullptr, stream);  // warm-up
+        ms_best = -1.0f;
+        for (int r = 0; r < 2 && !err; ++r) {
             cudaEventRecord(a, stream);
-            e = run_forward(p, c[0], y, ylt_dev, nullptr, stream);
+            err = run_forward(p, c[0], yt, ylt_dev, nullptr, stream);
             cudaEventRecord(b, stream);
-            if (!e) e = cudaEventSynchronize(b);
+            if (!err) err = cudaEventSynchronize(b);
             float ms = 0.0f;
-            if (!e) cudaEventElapsedTime(&ms, a, b);
+            if (!err) cudaEventElapsedTime(&ms, a, b);
             if (ms_best < 0 || ms < ms_best) ms_best = ms;
         }
-        if (e) break;
+        return err;
+    };
+    std::vector<float> sample(cands.size(), -1.0f);
+    for (size_t ci = 0; ci < cands.size() && !e; ++ci) {
+        if ((e = time_shape(cands[ci], ts, sample[ci]))) break;
         ++res.candidates;
-        if (best_ms < 0 || ms_best < best_ms) {
-            best_ms = ms_best;
-            std::copy(c.begin(), c.end(), best);
+    }
+    // A call has a part that does not grow with the trials (the skip
+    // variant's occurrence-table build, launch and fill costs). Per variant,
+    // its fastest shape is timed again on twice the sample, which separates
+    // that part (2 t(s) - t(2s)) from the per-trial part; every candidate is
+    // then ranked by its time extrapolated to n_trials.
+    float fixed[6] = {0, 0, 0, 0, 0, 0};
+    if (!e && n_trials >= 2 * ts) {
+        for (int v = ART_VARIANT_PLAIN; v <= ART_VARIANT_SPARSE && !e; ++v) {
+            int bi = -1;
+            for (size_t ci = 0; ci < cands.size(); ++ci)
+                if (cands[ci][0] == v && (bi < 0 || sample[ci] < sample[bi])) bi = (int)ci;
+            if (bi < 0) continue;
+            float t2 = 0.0f;
+            if ((e = time_shape(cands[bi], 2 * ts, t2))) break;
+            fixed[v] = std::max(0.0f, std::min(sample[bi], 2.0f * sample[bi] - t2));
+        }
+    }
+    float best_ms = -1.0f, best_pred = -1.0f;
+    for (size_t ci = 0; ci < cands.size() && !e; ++ci) {
+        const float f = fixed[cands[ci][0]];
+        const float pred = f + (sample[ci] - f) * (float)((double)n_trials / (double)ts);
+        if (best_pred < 0 || pred < best_pred) {
+            best_pred = pred;
+            best_ms = sample[ci];
+            std::copy(cands[ci].begin(), cands[ci].end(), best);
         }
     }
     cudaEventDestroy(a);

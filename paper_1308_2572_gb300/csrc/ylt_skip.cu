@@ -440,14 +440,23 @@ __global__ void __launch_bounds__(256) build_occ_kernel(const LayerBuildArgs* __
             o[s] = 0.0f;
             if (s < nl) {
                 const LayerBuildArgs& a = s_lb[s];
-                const float4* row = reinterpret_cast<const float4*>(a.table) + i * (a.np / 4);
+                const int nq = a.np / 4;
+                const float4* row = reinterpret_cast<const float4*>(a.table) + i * nq;
+                // every 16-byte piece of the row requested at once, then
+                // summed in ELT order
+                float4 r[kMaxLayerElts / 4];
+#pragma unroll
+                for (int q = 0; q < kMaxLayerElts / 4; ++q)
+                    r[q] = q < nq ? __ldcs(row + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 float x = 0.0f;
-                for (int q = 0; q < a.np / 4; ++q) {
-                    const float4 r = __ldcs(row + q);
-                    x += fin_f32(r.x, a.m[4 * q + 0], a.d[4 * q + 0], a.lim[4 * q + 0]);
-                    x += fin_f32(r.y, a.m[4 * q + 1], a.d[4 * q + 1], a.lim[4 * q + 1]);
-                    x += fin_f32(r.z, a.m[4 * q + 2], a.d[4 * q + 2], a.lim[4 * q + 2]);
-                    x += fin_f32(r.w, a.m[4 * q + 3], a.d[4 * q + 3], a.lim[4 * q + 3]);
+#pragma unroll
+                for (int q = 0; q < kMaxLayerElts / 4; ++q) {
+                    if (q < nq) {
+                        x += fin_f32(r[q].x, a.m[4 * q + 0], a.d[4 * q + 0], a.lim[4 * q + 0]);
+                        x += fin_f32(r[q].y, a.m[4 * q + 1], a.d[4 * q + 1], a.lim[4 * q + 1]);
+                        x += fin_f32(r[q].z, a.m[4 * q + 2], a.d[4 * q + 2], a.lim[4 * q + 2]);
+                        x += fin_f32(r[q].w, a.m[4 * q + 3], a.d[4 * q + 3], a.lim[4 * q + 3]);
+                    }
                 }
                 o[s] = xl_f32(x, a.occ_ret, a.occ_lim);
                 nz |= o[s] > 0.0f;
