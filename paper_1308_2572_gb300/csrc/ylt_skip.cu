@@ -16,21 +16,26 @@
 // evaluation gives, bit for bit: the same operations on the same operands.
 //
 // Mapping of the trial pass: a persistent grid of one CTA per SM. Each CTA
-// copies the bitmap into shared memory (as much of it as fits next to the
-// queues: 1.79M events' bits; the rest is read from global memory), so the
-// per-event test is a shared-memory load. Each warp walks a strided sequence
-// of trials as a stream of chunks of 32 * E events: the next chunk's ids
-// (from the same trial or the next one) are requested before the current
-// chunk is processed, hiding the DRAM latency of the id stream. For groups
-// of 1-2 layers every lane gathers X for its own events whose bit is set
-// (predicated loads, E in flight per lane). For wider groups the ids whose
-// bit is set go to a per-warp queue in shared memory and each time 32 are
-// queued every lane takes one, so the per-event work (one row of LP floats
-// and LT accumulations) runs on full warps. The per-lane, per-layer aggregate
-// is a compensated FP32 pair (Knuth's two-sum: the pair holds the exact sum
-// up to a second-order term of order n u^2), folded into FP64 once per trial,
-// so the FP64 pipe works per trial rather than per event; the warp then
-// reduces the lanes' FP64 partials and applies the aggregate terms in FP64.
+// copies the bitmap into shared memory; when the catalogue's bits do not fit
+// (227 KB hold 1.86M events), word w holds words w and w + S OR-ed together
+// (a superset test: a fold-only hit gathers a row of zeros, which adds
+// exactly 0), so the per-event test is always one shared-memory load for
+// catalogues up to twice that. Each warp walks a strided sequence of trials
+// as a stream of chunks of 32 * E events: the next chunk's ids (from the same
+// trial or the next one) are requested before the current chunk is
+// processed, hiding the DRAM latency of the id stream. Ids outside [0, C)
+// map to the sentinel event C (bit clear, row zero); a per-lane maximum
+// raises the range flag. For groups of 1-2 layers every lane gathers X for
+// its own events whose bit is set (predicated loads, E in flight per lane).
+// For wider groups the ids whose bit is set go to a per-warp
+// queue in shared memory and each time 32 are queued every lane takes one,
+// so the per-event work (one row of LP floats and LT accumulations) runs on
+// full warps. The per-lane, per-layer aggregate is a compensated FP32 pair
+// (Knuth's two-sum: the pair holds the exact sum up to a second-order term),
+// and the warp reduces the lanes' pairs as compensated FP32 pairs too; the
+// FP64 steps (the fold of the pair, the aggregate terms, the branch code)
+// run once per 32 trials for groups of 1-2 layers (lane s keeps trial s) and
+// on lane j for layer j otherwise, so the FP64 pipe is nearly idle.
 #include <algorithm>
 #include <limits>
 
