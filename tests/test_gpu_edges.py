@@ -100,3 +100,82 @@ def test_metrics_edges_and_determinism():
         np.testing.assert_array_equal(a[1], op)
         np.testing.assert_allclose(a[2], ot, rtol=1e-12)
         np.testing.assert_allclose(a[0], om, rtol=1e-12)
+
+
+def test_catalogue_beyond_twice_the_shared_bitmap():
+    """A catalogue of 4,000,037 events: the skip forward's and the group
+    adjoint's bitmaps no longer fold into shared memory, so the upper events'
+    bits are read from global memory. Dense (16-byte id loads) and CSR."""
+    for dense_k, seed in ((64, 511), (None, 512)):
+        w = workloads.random_case(seed, catalogue=4_000_037, n_elt=6, n_layers=5, n_trials=300, max_len=90,
+                                  nnz_frac=0.05, dense_k=dense_k)
+        ids = w.yet.event_ids
+        assert ids.max() > 3_800_000 and ids.min() < 200_000
+        _run_all(w)
+        # the group adjoint against the per-layer adjoint on the same branch codes
+        L, E, T = w.portfolio.n_layers, w.portfolio.n_elt, w.yet.n_trials
+        pg = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_GROUP | art.ART_LAYOUT_LAYER)
+        pl = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_LAYER)
+        try:
+            yet = device_yet(w)
+            dids, off, k, _ = yet
+            ylt = torch.empty((L, T), dtype=torch.float64, device="cuda")
+            br = torch.empty((L, T), dtype=torch.uint8, device="cuda")
+            art.art_set_variant(pl, art.ART_VARIANT_PLAIN)
+            art.art_run_ylt(pl, T, dids, off, k, ylt, br)
+            g = torch.full((L, T), 1.0 / T, dtype=torch.float64, device="cuda")
+            outs = []
+            for p in (pg, pl):
+                gt = torch.empty((L, 4), dtype=torch.float64, device="cuda")
+                gm = torch.empty(E, dtype=torch.float64, device="cuda")
+                art.art_run_ylt_backward(p, T, dids, off, k, br, g, gt, gm)
+                torch.cuda.synchronize()
+                outs.append((gt.cpu().numpy(), gm.cpu().numpy()))
+            np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-6, atol=1e-12)
+            np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=2e-6, atol=1e-9 * np.abs(outs[1][1]).max())
+        finally:
+            pg.close()
+            pl.close()
+
+
+def test_out_of_range_ids_dense_and_backward():
+    """Ids outside [0, C) in a dense YET (16-byte id loads): every forward
+    flags them and counts them as zero loss; both adjoints agree."""
+    w = workloads.random_case(513, catalogue=1_037, n_trials=120, dense_k=40, n_layers=4)
+    ids = w.yet.event_ids.copy()
+    ids[[5, 77, 400, 4799]] = [w.portfolio.catalogue_size, -1, 2 ** 31 - 1, w.portfolio.catalogue_size + 3]
+    bad = workloads.Workload(w.name, w.portfolio, workloads.YET(w.yet.n_trials, ids, 40, None), w.probs)
+    zero_ev = int(np.flatnonzero(w.portfolio.elt_losses.sum(axis=0) == 0)[0])
+    fixed = np.where((ids < 0) | (ids >= w.portfolio.catalogue_size), zero_ev, ids).astype(np.int32)
+    ref, gross, _ = oracle.ylt(dict(w.oracle_problem(), event_ids=fixed))
+    L, E, T = w.portfolio.n_layers, w.portfolio.n_elt, w.yet.n_trials
+    p = art.portfolio_from_workload(w, layouts=ALL)
+    pl = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_LAYER)
+    try:
+        dids, off, k, _ = device_yet(bad)
+        for v in VARIANTS:
+            art.art_set_variant(p, v)
+            y = torch.zeros((L, T), dtype=torch.float64, device="cuda")
+            art.art_run_ylt(p, T, dids, off, k, y)
+            assert art.art_get_device_status(p) == art.ART_EID_RANGE, v
+            assert_ylt_close(y.cpu().numpy(), ref, gross, f"bad dense ids, variant {v}")
+        br = torch.empty((L, T), dtype=torch.uint8, device="cuda")
+        y = torch.empty((L, T), dtype=torch.float64, device="cuda")
+        art.art_set_variant(pl, art.ART_VARIANT_PLAIN)
+        art.art_run_ylt(pl, T, dids, off, k, y, br)
+        art.art_get_device_status(pl)
+        g = torch.full((L, T), 1.0 / T, dtype=torch.float64, device="cuda")
+        outs = []
+        for q in (p, pl):
+            gt = torch.empty((L, 4), dtype=torch.float64, device="cuda")
+            gm = torch.empty(E, dtype=torch.float64, device="cuda")
+            art.art_run_ylt_backward(q, T, dids, off, k, br, g, gt, gm)
+            torch.cuda.synchronize()
+            outs.append((gt.cpu().numpy(), gm.cpu().numpy()))
+        np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=2e-6, atol=1e-12)
+        ot, om, _, _ = oracle.grad(dict(w.oracle_problem(), event_ids=fixed), g.cpu().numpy())
+        np.testing.assert_allclose(outs[0][0], ot, rtol=1e-6, atol=1e-9)
+    finally:
+        p.close()
+        pl.close()
