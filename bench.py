@@ -131,7 +131,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"ylt_plain": "ylt_plain.cu", "ylt_skip": "ylt_skip.cu", "ylt_batched": "ylt_batched.cu",
-                  "ylt_batched_fp64": "ylt_batched.cu", "ylt_sparse": "ylt_sparse.cu"}
+                  "ylt_skip64": "ylt_skip64.cu", "ylt_sparse": "ylt_sparse.cu"}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -227,18 +227,24 @@ def algorithmic_bytes(w, variant: str):
     touched_frac = 1.0 - np.exp(-n_events / C)
     sec = lambda nbytes: 32 * -(-nbytes // 32)
     pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
-    if variant == "skip":
+    if variant in ("skip", "fp64"):
         # one streamed pass over the per-layer tables that writes each
         # occurrence group's table X [C][LP] and its bitmap, then per group
         # and event an id and, where X is non-zero, one sector of X
+        # (the all-FP64 variant: the same with 8-byte entries of X)
         L = port.n_layers
         lp = 1 if L <= 1 else (2 if L <= 2 else (4 if L <= 4 else 8))
+        xb = 8 if variant == "fp64" else 4
         groups = occurrence_groups(port)
-        reads = sum(n_events * occurrence_density(port, lays) * sec(4 * lp) for lays in groups)
-        build = float(sum(4 * pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (C * 4 * lp + C / 8)
+        dens = [occurrence_density(port, lays) for lays in groups]
+        reads = sum(n_events * d * sec(xb * lp) for d in dens)
+        build = float(sum(4 * pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (C * xb * lp + C / 8)
         n_groups = len(groups)
+        # FP64 operations of the all-FP64 variant: per (catalogue event, ELT
+        # of a layer) an FMA and an add, per queued event an add per slot
+        flops = 4.0 * C * float(port.elts_per_layer().sum()) + sum(n_events * d * lp for d in dens)
         return {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
-                "l2": n_groups * ids + build + reads}
+                "l2": n_groups * ids + build + reads, "fp64_flops": flops}
     if variant == "sparse":
         nnz_per_event = float((port.elt_losses != 0).sum(axis=0).mean())
         csr = 4 * (C + 1) + 8 * float((port.elt_losses != 0).sum())
@@ -357,7 +363,7 @@ def main():
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
     # a named variant builds only its own layout (keeps profiling runs small)
     layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_LAYER, "batched": art.ART_LAYOUT_POOL,
-               "fp64": art.ART_LAYOUT_POOL64, "sparse": art.ART_LAYOUT_SPARSE}.get(
+               "fp64": art.ART_LAYOUT_LAYER | art.ART_LAYOUT_OCC64, "sparse": art.ART_LAYOUT_SPARSE}.get(
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
     if args.config == "c3":
         layouts |= art.ART_LAYOUT_GROUP  # the adjoint reads the group tables
@@ -465,7 +471,7 @@ def main():
                   "dram_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 8 << 30, 3),
                   "stream_read_gbs": art.art_probe(art.ART_PROBE_STREAM, 8 << 30, 3),
                   "fp64_add_gflops": art.art_probe(art.ART_PROBE_FP64ADD, 0, 3)}
-    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_batched_fp64", "skip": "ylt_skip",
+    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_skip64", "skip": "ylt_skip",
                    "sparse": "ylt_sparse"}[variant]
     traffic = recorded_traffic(kernel_name, args.config)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -477,6 +483,16 @@ def main():
         roof["l2_gather_peak_gbs"] = probes["l2_gather32_gbs"]
         roof["l2_frac"] = roof["l2_sector_gbs"] / probes["l2_gather32_gbs"]
         roof["probes"] = probes
+    if "fp64_flops" in ab:
+        # the all-FP64 variant is bound by the FP64 pipe: against the probed
+        # FP64 add rate when the probes ran
+        fp64 = ab["fp64_flops"] / secs / 1e9
+        roof["fp64_gflops"] = fp64
+        if probes:
+            roof.update({"bound": "alu", "achieved": fp64, "peak": probes["fp64_add_gflops"], "unit": "GFLOP/s",
+                         "frac": fp64 / probes["fp64_add_gflops"],
+                         "peak_source": "probed FP64 add rate (art_probe), not in MEASURED_PEAKS.json",
+                         "hbm_achieved_gbs": achieved})
 
     # end to end: host buffers through the C ABI (ids H2D in chunks, YLT D2H),
     # then the metrics on a device copy of the YLT and their D2H

@@ -78,7 +78,10 @@ enum {
     ART_VARIANT_AUTO = 0,     /* batched when the pool layout exists, else plain          */
     ART_VARIANT_PLAIN = 1,    /* one launch per layer over a per-layer event-major table  */
     ART_VARIANT_BATCHED = 2,  /* one persistent launch over all layers (pool table)       */
-    ART_VARIANT_FP64 = 3,     /* batched, with FP64 tables and FP64 per-event arithmetic  */
+    ART_VARIANT_FP64 = 3,     /* all-FP64 arithmetic: per call, FP64 occurrence losses of
+                                 every catalogue event, then one trial pass per run of
+                                 <= 8 layers with FP64 sums (ART_LAYOUT_OCC64); else
+                                 batched over the FP64 pool (ART_LAYOUT_POOL64)           */
     ART_VARIANT_SKIP = 4,     /* per call, the occurrence loss of every catalogue event
                                  for every layer (one build launch from the per-layer
                                  tables), then one trial pass per run of <= 8 layers that
@@ -98,8 +101,13 @@ enum {
     ART_LAYOUT_GROUP = 8,     /* per layer group (<= 8 layers, <= 32 ELTs together):
                                  [C][n_pad] FP32 over the group's ELTs plus a C-bit
                                  occupancy bitmap; read by art_run_ylt_backward           */
-    ART_LAYOUT_SPARSE = 16    /* all ELTs: event-major CSR of the non-zero losses
+    ART_LAYOUT_SPARSE = 16,   /* all ELTs: event-major CSR of the non-zero losses
                                  (C + 1 offsets, 8 bytes per non-zero loss)                */
+    ART_LAYOUT_OCC64 = 32     /* with ART_LAYOUT_LAYER: FP64 occurrence-loss tables
+                                 ([C + 1][<= 8] FP64 per run of <= 8 layers) and bitmaps,
+                                 written by the all-FP64 variant on every call; that
+                                 variant then uses them instead of the FP64 pool
+                                 (counted with the pool64 bytes)                           */
 };
 
 /* Flags. */

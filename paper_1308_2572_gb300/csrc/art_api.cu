@@ -318,11 +318,12 @@ cudaError_t upload_layer_build(art_portfolio* p) {
         a.np = p->layer_np[j];
         a.pad_ = 0;
     }
-    for (OccGroupArgs& g : p->ogroups)
-        for (int s = 0; s < g.n_layers; ++s) {
-            g.agg_ret[s] = p->agg_ret[g.layer[s]];
-            g.agg_lim[s] = p->agg_lim[g.layer[s]];
-        }
+    for (std::vector<OccGroupArgs>* v : {&p->ogroups, &p->ogroups64})
+        for (OccGroupArgs& g : *v)
+            for (int s = 0; s < g.n_layers; ++s) {
+                g.agg_ret[s] = p->agg_ret[g.layer[s]];
+                g.agg_lim[s] = p->agg_lim[g.layer[s]];
+            }
     return cudaMemcpy(p->d_lbuild, lb.data(), sizeof(LayerBuildArgs) * lb.size(), cudaMemcpyHostToDevice);
 }
 
@@ -367,6 +368,30 @@ cudaError_t build_occ_groups(art_portfolio* p) {
     if ((e = cudaMalloc(&p->d_lbuild, sizeof(LayerBuildArgs) * L))) return e;
     if ((e = cudaMalloc(&p->d_ogroups, sizeof(OccBuildGroup) * ng))) return e;
     if ((e = cudaMemcpy(p->d_ogroups, bg.data(), sizeof(OccBuildGroup) * ng, cudaMemcpyHostToDevice))) return e;
+    if (p->layouts & ART_LAYOUT_OCC64) {
+        const size_t xb64 = sizeof(double) * ((size_t)p->catalogue + 1) * p->og_lp;
+        p->ogroups64 = p->ogroups;
+        p->og_occ64.assign(ng, nullptr);
+        p->og_bits64.assign(ng, nullptr);
+        std::vector<OccBuildGroup> bg64 = bg;
+        for (int32_t gi = 0; gi < ng && !e; ++gi) {
+            if ((e = cudaMalloc(&p->og_occ64[gi], xb64))) break;
+            if ((e = cudaMalloc(&p->og_bits64[gi], bb))) break;
+            if ((e = cudaMemset(p->og_occ64[gi], 0, xb64))) break;
+            if ((e = cudaMemset(p->og_bits64[gi], 0, bb))) break;
+            p->occ64_bytes += (int64_t)(xb64 + bb);
+            p->ogroups64[gi].occ = nullptr;
+            p->ogroups64[gi].occ64 = p->og_occ64[gi];
+            p->ogroups64[gi].occ_bits = p->og_bits64[gi];
+            bg64[gi].occ = nullptr;
+            bg64[gi].occ_bits = p->og_bits64[gi];
+        }
+        if (e) return e;
+        if ((e = cudaMalloc(&p->d_ogroups64, sizeof(OccBuildGroup) * ng))) return e;
+        if ((e = cudaMemcpy(p->d_ogroups64, bg64.data(), sizeof(OccBuildGroup) * ng, cudaMemcpyHostToDevice))) return e;
+        if ((e = cudaMalloc(&p->d_occ64_ptrs, sizeof(double*) * ng))) return e;
+        if ((e = cudaMemcpy(p->d_occ64_ptrs, p->og_occ64.data(), sizeof(double*) * ng, cudaMemcpyHostToDevice))) return e;
+    }
     return upload_layer_build(p);
 }
 
@@ -431,6 +456,10 @@ void free_portfolio(art_portfolio* p) {
     for (uint32_t* b : p->og_bits) cudaFree(b);
     cudaFree(p->d_lbuild);
     cudaFree(p->d_ogroups);
+    for (double* t : p->og_occ64) cudaFree(t);
+    for (uint32_t* b : p->og_bits64) cudaFree(b);
+    cudaFree(p->d_ogroups64);
+    cudaFree(p->d_occ64_ptrs);
     cudaFree(p->pool);
     cudaFree(p->pool64);
     cudaFree(p->d_elt_terms);
@@ -475,7 +504,9 @@ bool variant_available(const art_portfolio* p, int v) {
     if (v == ART_VARIANT_SKIP) return !p->ogroups.empty();
     if (v == ART_VARIANT_SPARSE) return p->sp_ptr != nullptr && p->n_tiles > 0 && sparse_smem(p, 1) <= 200 * 1024;
     if (v == ART_VARIANT_BATCHED) return p->pool != nullptr && p->n_tiles > 0 && batched_smem(p, false) <= 200 * 1024;
-    if (v == ART_VARIANT_FP64) return p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024;
+    if (v == ART_VARIANT_FP64)
+        return !p->ogroups64.empty() ||
+               (p->pool64 != nullptr && p->n_tiles > 0 && batched_smem(p, true) <= 200 * 1024);
     return false;
 }
 
@@ -492,6 +523,7 @@ cudaError_t run_forward(art_portfolio* p, int variant, const YetArgs& y, double*
     if (variant == ART_VARIANT_PLAIN) return launch_plain(p, y, ylt, branch, s);
     if (variant == ART_VARIANT_SKIP) return launch_skip(p, y, ylt, branch, s);
     if (variant == ART_VARIANT_SPARSE) return launch_sparse(p, y, ylt, branch, s);
+    if (variant == ART_VARIANT_FP64 && !p->ogroups64.empty()) return launch_skip64(p, y, ylt, branch, s);
     return launch_batched(p, y, ylt, branch, variant == ART_VARIANT_FP64, s);
 }
 
@@ -930,7 +962,7 @@ art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64
     if (group_bytes) *group_bytes = p->group_bytes;
     if (layer_bytes) *layer_bytes = p->layer_bytes + p->occ_bytes;
     if (pool_bytes) *pool_bytes = p->pool_bytes;
-    if (pool64_bytes) *pool64_bytes = p->pool64_bytes;
+    if (pool64_bytes) *pool64_bytes = p->pool64_bytes + p->occ64_bytes;
     return ART_OK;
 }
 

@@ -145,8 +145,9 @@ struct GroupArgs {
 // trial pass then reads those. Passed by value.
 constexpr int kMaxOccLayers = 8;
 struct OccGroupArgs {
-    const float* occ;          // [C][lt_pad] FP32
-    const uint32_t* occ_bits;  // [ceil(C / 128) * 4] (zero-padded to 16-byte groups)
+    const float* occ;          // [C + 1][lt_pad] FP32
+    const double* occ64;       // [C + 1][lt_pad] FP64 (the all-FP64 tables)
+    const uint32_t* occ_bits;  // bits 0 .. C, zero-padded to whole 16-byte groups
     int32_t layer[kMaxOccLayers];
     double agg_ret[kMaxOccLayers], agg_lim[kMaxOccLayers];
     int32_t n_layers;
@@ -215,6 +216,13 @@ struct art_portfolio {
     art::LayerBuildArgs* d_lbuild = nullptr;    // [n_layers]
     art::OccBuildGroup* d_ogroups = nullptr;    // [n_ogroups]
     int64_t occ_bytes = 0;
+    // ART_LAYOUT_OCC64: the same groups with FP64 tables and their own bitmaps
+    std::vector<art::OccGroupArgs> ogroups64;
+    std::vector<double*> og_occ64;
+    std::vector<uint32_t*> og_bits64;
+    art::OccBuildGroup* d_ogroups64 = nullptr;  // bitmaps of the FP64 tables
+    double** d_occ64_ptrs = nullptr;            // [n_ogroups]
+    int64_t occ64_bytes = 0;
     int64_t group_bytes = 0;
 
     // ART_LAYOUT_SPARSE: event-major CSR of the non-zero losses
@@ -264,6 +272,7 @@ cudaError_t launch_payouts(art_portfolio* p, int32_t j, const YetArgs& y, double
 cudaError_t launch_sparse(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
 cudaError_t build_sparse(art_portfolio* p, const float* src, cudaStream_t s);
 cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
 cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np, uint32_t* bitmap, cudaStream_t s);
 // Write every occurrence group's X and bitmap (one launch) from the layer tables.
 cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s);

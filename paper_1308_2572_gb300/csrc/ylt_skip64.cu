@@ -1,0 +1,316 @@
+// ylt_skip64.cu -- the all-FP64 forward over occurrence tables (Section II,
+// Algorithm 1), for the precision study: every step in FP64.
+//
+// As in the skip variant, steps 2-3 (financial terms, ELT sum, occurrence
+// terms) depend on the event id alone, so each call evaluates them once per
+// catalogue event, here in FP64: X[i][s] = O_j(sum_{e in layer j} F_e(l_e[i]))
+// for the layer j in slot s of each occurrence group (up to 8 consecutive
+// layers), with F_e(y) = min(max(m_e y - D_e, 0), Lim_e) as one FP64 FMA and
+// the terms (stored rounded to FP32) widened exactly; the sum follows the
+// layer's ELT order. A bitmap marks the events with some X[i][s] > 0 (bit C,
+// the sentinel for ids outside [0, C), is clear and row C is zero).
+//
+// The trial pass: a persistent grid of one 1024-thread CTA per SM, the bitmap
+// in shared memory (folded once when it does not fit: a superset test, a
+// fold-only hit gathers a zero row), a warp per trial streaming its ids with
+// the next chunk requested before the current one is processed, and a
+// per-warp queue of the events whose bit is set, evaluated 32 at a time (lane
+// = event): one row of X (8 * LP bytes) and an FP64 add per layer. The lanes'
+// FP64 sums are reduced across the warp (xor shuffles, so every lane holds
+// every layer's total) and lane j applies layer j's aggregate terms in FP64.
+// The FP64 pipe of this part (about 0.53 TFLOP/s for adds) bounds it: this is
+// the reference-precision path, not the throughput path.
+#include <algorithm>
+#include <limits>
+
+#include "art_internal.cuh"
+
+namespace art {
+
+namespace {
+
+constexpr int k64Threads = 1024;
+constexpr int k64Warps = k64Threads / 32;
+constexpr int k64Ids = 8;     // ids per lane per chunk
+constexpr int k64Queue = 64;  // per-warp queue entries
+
+__device__ __forceinline__ uint32_t ld_bits_global(const uint32_t* p) {
+    uint32_t v;
+    asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Row id of X: LP doubles (LP = 1, 2, 4 or 8), 16-byte loads not kept in L1.
+template <int LP>
+__device__ __forceinline__ void ld_row64(const double* x, uint32_t id, double (&o)[LP]) {
+    const double* p = x + (size_t)id * LP;
+    if constexpr (LP == 1) {
+        asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(o[0]) : "l"(p));
+    } else {
+#pragma unroll
+        for (int q = 0; q < LP / 2; ++q)
+            asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(o[2 * q]), "=d"(o[2 * q + 1]) : "l"(p + 2 * q));
+    }
+}
+
+// Block (x, y): 256 events of occurrence group y; thread i reads row i of
+// each of the group's layer tables and writes X[i][0..LP) in FP64.
+template <int LP>
+__global__ void __launch_bounds__(256) build_occ64_kernel(const LayerBuildArgs* __restrict__ lbuild,
+                                                          const OccBuildGroup* __restrict__ groups,
+                                                          double* const* __restrict__ occ64, int32_t catalogue,
+                                                          int32_t words) {
+    __shared__ LayerBuildArgs s_lb[LP];
+    const OccBuildGroup& grp = groups[blockIdx.y];
+    const int nl = grp.n_layers;
+    for (int w = threadIdx.x; w < nl * (int)(sizeof(LayerBuildArgs) / 4); w += blockDim.x) {
+        const int s = w / (int)(sizeof(LayerBuildArgs) / 4), o = w % (int)(sizeof(LayerBuildArgs) / 4);
+        reinterpret_cast<uint32_t*>(&s_lb[s])[o] = reinterpret_cast<const uint32_t*>(&lbuild[grp.layer[s]])[o];
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool nz = false;
+    if (i < catalogue) {
+        double o[LP];
+#pragma unroll
+        for (int s = 0; s < LP; ++s) {
+            o[s] = 0.0;
+            if (s < nl) {
+                const LayerBuildArgs& a = s_lb[s];
+                const int nq = a.np / 4;
+                const float4* row = reinterpret_cast<const float4*>(a.table) + i * nq;
+                float4 r[kMaxLayerElts / 4];
+#pragma unroll
+                for (int q = 0; q < kMaxLayerElts / 4; ++q)
+                    r[q] = q < nq ? __ldcs(row + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                double x = 0.0;
+#pragma unroll
+                for (int q = 0; q < kMaxLayerElts / 4; ++q) {
+                    if (q < nq) {
+                        x += fin_f64(r[q].x, a.m[4 * q + 0], a.d[4 * q + 0], a.lim[4 * q + 0]);
+                        x += fin_f64(r[q].y, a.m[4 * q + 1], a.d[4 * q + 1], a.lim[4 * q + 1]);
+                        x += fin_f64(r[q].z, a.m[4 * q + 2], a.d[4 * q + 2], a.lim[4 * q + 2]);
+                        x += fin_f64(r[q].w, a.m[4 * q + 3], a.d[4 * q + 3], a.lim[4 * q + 3]);
+                    }
+                }
+                o[s] = xl_f64(x, a.occ_ret, a.occ_lim);
+                nz |= o[s] > 0.0;
+            }
+        }
+        double* dst = occ64[blockIdx.y] + i * LP;
+        if constexpr (LP == 1) dst[0] = o[0];
+        else {
+#pragma unroll
+            for (int q = 0; q < LP / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(o[2 * q], o[2 * q + 1]);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
+}
+
+template <int LT, bool VEC, bool FOLD>
+__global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGroupArgs g, const YetArgs y,
+                                                                  const int32_t smem_words, const bool early_exit,
+                                                                  double* __restrict__ ylt,
+                                                                  uint8_t* __restrict__ branch,
+                                                                  int* __restrict__ flags) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int E = k64Ids;
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    int32_t* s_queue = reinterpret_cast<int32_t*>(s_dyn);  // [k64Warps][k64Queue]
+    uint32_t* s_bits = s_dyn + k64Warps * k64Queue;
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(g.occ_bits);
+        uint4* dst = reinterpret_cast<uint4*>(s_bits);
+        const int words = (y.catalogue >> 5) + 1;  // bits 0 .. C (C: the sentinel)
+        for (int i = threadIdx.x; i < smem_words / 4; i += blockDim.x) {
+            uint4 v = src[i];
+            if (FOLD && 4 * i + smem_words < words) {  // the bitmap is zero-padded to whole uint4
+                const uint4 u = src[i + smem_words / 4];
+                v.x |= u.x;
+                v.y |= u.y;
+                v.z |= u.z;
+                v.w |= u.w;
+            }
+            dst[i] = v;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t* q = s_queue + wib * k64Queue;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n_warps = (int64_t)gridDim.x * k64Warps;
+    uint32_t max_id = 0;  // largest id seen (an id >= C raises the range flag)
+    bool bad_off_seen = false;
+    int32_t my_layer = 0;
+    double my_ret = 0.0, my_lim = 0.0;
+#pragma unroll
+    for (int j = 0; j < LT; ++j)
+        if (lane == j) {
+            my_layer = g.layer[j];
+            my_ret = g.agg_ret[j];
+            my_lim = g.agg_lim[j];
+        }
+
+    for (int64_t t = (int64_t)blockIdx.x * k64Warps + wib; t < y.n_trials; t += n_warps) {
+        int64_t b, e;
+        bool bo;
+        trial_range(y, t, b, e, bo);
+        bad_off_seen |= bo;
+        double sum[LT];
+#pragma unroll
+        for (int j = 0; j < LT; ++j) sum[j] = 0.0;
+        auto add_row = [&](uint32_t id) {
+            double o[LT];
+            ld_row64<LT>(g.occ64, id, o);
+#pragma unroll
+            for (int j = 0; j < LT; ++j) sum[j] += o[j];
+        };
+        // ids of a chunk of 32 * E events from c0; empty slots read as -1
+        auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
+            if constexpr (VEC) {
+#pragma unroll
+                for (int h = 0; h < E / 4; ++h) {
+                    const int64_t d = c0 + 128 * h + 4 * lane;
+                    int4 w4 = make_int4(-1, -1, -1, -1);
+                    if (d < e) w4 = __ldcs(reinterpret_cast<const int4*>(y.ids + d));  // e and d are multiples of 4
+                    v[4 * h + 0] = (uint32_t)w4.x;
+                    v[4 * h + 1] = (uint32_t)w4.y;
+                    v[4 * h + 2] = (uint32_t)w4.z;
+                    v[4 * h + 3] = (uint32_t)w4.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int64_t d = c0 + 32 * k + lane;
+                    v[k] = d < e ? (uint32_t)ld_stream(y.ids + d) : 0xffffffffu;
+                }
+            }
+        };
+        int qn = 0;  // warp-uniform, < 32 between chunks
+        bool capped_exit = false;
+        uint32_t pre[E];
+        if (b < e) load_ids(b, pre);
+        for (int64_t c0 = b; c0 < e; c0 += 32 * E) {
+            uint32_t uid[E];
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                // slot k's position in the trial (empty slots hold -1: no flag)
+                const int64_t d = VEC ? c0 + 128 * (k >> 2) + 4 * lane + (k & 3) : c0 + 32 * k + lane;
+                if (d < e) max_id = max(max_id, pre[k]);
+                uid[k] = min(pre[k], (uint32_t)y.catalogue);
+            }
+            if (c0 + 32 * E < e) load_ids(c0 + 32 * E, pre);
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                uint32_t wi = uid[k] >> 5;
+                uint32_t w;
+                if constexpr (FOLD) {
+                    wi = wi >= (uint32_t)smem_words ? wi - (uint32_t)smem_words : wi;
+                    w = s_bits[wi];
+                } else {
+                    w = wi < (uint32_t)smem_words ? s_bits[wi] : ld_bits_global(g.occ_bits + wi);
+                }
+                const bool nz = (w >> (uid[k] & 31)) & 1u;
+                const unsigned mm = __ballot_sync(FULL, nz);
+                if (nz) q[qn + __popc(mm & lt_mask)] = (int32_t)uid[k];
+                qn += __popc(mm);
+                if (qn >= 32) {
+                    __syncwarp();
+                    const int32_t mine = q[lane];
+                    const int32_t carry = q[32 + lane];
+                    __syncwarp();
+                    q[lane] = carry;  // entries 32 .. qn-1 move to the front
+                    qn -= 32;
+                    add_row((uint32_t)mine);
+                    __syncwarp();
+                }
+            }
+            if (early_exit) {
+                // every layer capped: the aggregate never decreases, the loss is AggL
+                bool all = true;
+#pragma unroll
+                for (int j = 0; j < LT; ++j) {
+                    double v = sum[j];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                    if (j < g.n_layers) all = all && (v - g.agg_ret[j] >= g.agg_lim[j]);
+                }
+                if (all) {
+                    qn = 0;
+                    capped_exit = true;
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < qn) add_row((uint32_t)q[lane]);
+        __syncwarp();
+        double mine = 0.0;
+#pragma unroll
+        for (int j = 0; j < LT; ++j) {
+            double v = sum[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+            if (lane == j) mine = v;
+        }
+        if (lane < g.n_layers) {
+            const size_t wi = (size_t)my_layer * (size_t)y.n_trials + (size_t)t;
+            ylt[wi] = capped_exit ? my_lim : xl_f64(mine, my_ret, my_lim);
+            if (branch) branch[wi] = capped_exit ? (uint8_t)2 : agg_branch(mine, my_ret, my_lim);
+        }
+    }
+    if (max_id >= (uint32_t)y.catalogue) atomicOr(flags + kFlagIdRange, 1);
+    if (lane == 0 && bad_off_seen) atomicOr(flags + kFlagBadOffsets, 1);
+}
+
+template <int LT>
+cudaError_t launch_group64(const OccGroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
+                           double* ylt, uint8_t* branch, int* flags, cudaStream_t s) {
+    int dev = 0, max_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    const int queue_bytes = k64Warps * k64Queue * 4;
+    const int words = (catalogue >> 5) + 1;  // bits 0 .. C (C: the sentinel)
+    const int smem_words = std::max(4, std::min((words + 3) & ~3, (max_optin - queue_bytes) / 4) & ~3);
+    const int smem = queue_bytes + smem_words * 4;
+    const bool fold = words <= 2 * smem_words;
+    const bool vec = !y.off && y.k % 4 == 0 && (reinterpret_cast<uintptr_t>(y.ids) & 15) == 0;
+    auto kern = vec ? (fold ? ylt_skip64_kernel<LT, true, true> : ylt_skip64_kernel<LT, true, false>)
+                    : (fold ? ylt_skip64_kernel<LT, false, true> : ylt_skip64_kernel<LT, false, false>);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    const int64_t grid = std::min<int64_t>(num_sms, (y.n_trials + k64Warps - 1) / k64Warps);
+    kern<<<(unsigned)std::max<int64_t>(1, grid), k64Threads, smem, s>>>(g, y, smem_words, early, ylt, branch, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s) {
+    const bool early = (p->flags & ART_FLAG_EARLY_EXIT) != 0;
+    const int32_t words = (int32_t)(((int64_t)p->catalogue + 31) / 32);
+    const dim3 grid((unsigned)(((int64_t)words * 32 + 255) / 256), (unsigned)p->ogroups64.size());
+    switch (p->og_lp) {
+        case 1: build_occ64_kernel<1><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        case 2: build_occ64_kernel<2><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        case 4: build_occ64_kernel<4><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        case 8: build_occ64_kernel<8><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || y.n_trials == 0) return err;
+    for (const OccGroupArgs& g : p->ogroups64) {
+        switch (p->og_lp) {
+            case 1: err = launch_group64<1>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 2: err = launch_group64<2>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 4: err = launch_group64<4>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            case 8: err = launch_group64<8>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
+            default: err = cudaErrorInvalidValue;
+        }
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace art

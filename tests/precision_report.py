@@ -1,6 +1,7 @@
 """Precision report for the 128-layer, 512-ELT workload (mixed vs all-FP64).
 
-Runs every forward variant through the C ABI on the first N trials of the
+Runs every forward variant (the all-FP64 one over FP64 occurrence tables
+and over the FP64 pool) through the C ABI on the first N trials of the
 precision workload (lognormal(13, 2.5) pool, 1,000 events per trial), and
 the FP64 oracle on the same trials, then reports per variant:
   - max over (layer, trial) of |dY| / G (G = the trial's gross loss; the
@@ -31,8 +32,11 @@ import numpy as np  # noqa: E402
 import oracle  # noqa: E402
 from paper_1308_2572_gb300 import art, workloads  # noqa: E402
 
-VARIANTS = {"batched (FP32 + FP64 aggregate)": "ART_VARIANT_BATCHED", "sparse": "ART_VARIANT_SPARSE",
-            "skip": "ART_VARIANT_SKIP", "plain": "ART_VARIANT_PLAIN", "all-FP64": "ART_VARIANT_FP64"}
+MIXED = (1 | 2 | 8 | 16)  # layer, pool, group and CSR layouts (ART_LAYOUT_*)
+VARIANTS = {"batched (FP32 + FP64 aggregate)": ("ART_VARIANT_BATCHED", MIXED), "sparse": ("ART_VARIANT_SPARSE", MIXED),
+            "skip": ("ART_VARIANT_SKIP", MIXED), "plain": ("ART_VARIANT_PLAIN", MIXED),
+            "all-FP64 (occurrence tables)": ("ART_VARIANT_FP64", 1 | 32),
+            "all-FP64 (FP64 pool)": ("ART_VARIANT_FP64", 4)}
 
 
 def report(config: str = "c4", n_trials: int = 20000) -> dict:
@@ -43,15 +47,13 @@ def report(config: str = "c4", n_trials: int = 20000) -> dict:
     ref, gross, _ = oracle.ylt(w.oracle_problem())
     t_oracle = time.perf_counter() - t0
     om, op, ot = oracle.metrics(ref, probs)
-    layouts = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_POOL64 | art.ART_LAYOUT_GROUP
-               | art.ART_LAYOUT_SPARSE)
-    p = art.portfolio_from_workload(w, layouts=layouts)
     ids = torch.from_numpy(w.yet.event_ids).cuda()
     off = None if w.yet.trial_off is None else torch.from_numpy(w.yet.trial_off).cuda()
     L, T, K = w.portfolio.n_layers, w.yet.n_trials, w.yet.events_per_trial
     out = {"config": config, "trials": T, "layers": L, "probs": probs, "oracle_seconds": t_oracle,
            "oracle_threads": oracle.num_threads(), "variants": {}}
-    for name, v in VARIANTS.items():
+    for name, (v, layouts) in VARIANTS.items():
+        p = art.portfolio_from_workload(w, layouts=layouts)
         art.art_set_variant(p, getattr(art, v))
         ylt = torch.empty((L, T), dtype=torch.float64, device="cuda")
         art.art_run_ylt(p, T, ids, off, K, ylt)
@@ -78,7 +80,7 @@ def report(config: str = "c4", n_trials: int = 20000) -> dict:
             "mean_rel_err": relerr(mean, om),
             "forward_ms": e0.elapsed_time(e1),
         }
-    p.close()
+        p.close()
     return out
 
 

@@ -33,6 +33,19 @@ def _run_all(w):
             assert_ylt_close(y.cpu().numpy(), ref, gross, f"variant {v}")
     finally:
         p.close()
+    # the all-FP64 variant over FP64 occurrence tables
+    p = art.portfolio_from_workload(w, layouts=art.ART_LAYOUT_LAYER | art.ART_LAYOUT_OCC64)
+    try:
+        ids, off, k, T = device_yet(w)
+        L = w.portfolio.n_layers
+        art.art_set_variant(p, art.ART_VARIANT_FP64)
+        y = torch.full((L, T), -5.0, dtype=torch.float64, device="cuda")
+        art.art_run_ylt(p, T, ids, off, k, y)
+        torch.cuda.synchronize()
+        assert art.art_get_device_status(p) == art.ART_OK
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * np.maximum(gross, 1.0))
+    finally:
+        p.close()
     return ref
 
 

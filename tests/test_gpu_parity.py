@@ -20,6 +20,21 @@ VARIANTS = [art.ART_VARIANT_PLAIN, art.ART_VARIANT_BATCHED, art.ART_VARIANT_FP64
             art.ART_VARIANT_SPARSE]
 ALL_LAYOUTS = (art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_POOL64 | art.ART_LAYOUT_GROUP
                | art.ART_LAYOUT_SPARSE)
+# the all-FP64 variant over FP64 occurrence tables (without them it runs over
+# the FP64 pool, as in ALL_LAYOUTS)
+OCC64_LAYOUTS = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_OCC64
+FP64_TOL = 1e-12  # |dY| <= 1e-12 G: FP64 arithmetic, only the summation order differs from the oracle
+
+
+def _check_fp64_occ(w, ref, gross, what, trials=None):
+    p = art.portfolio_from_workload(w, layouts=OCC64_LAYOUTS)
+    try:
+        ylt, _ = run_ylt(p, w, art.ART_VARIANT_FP64)
+        y = ylt.cpu().numpy() if trials is None else ylt[:, torch.from_numpy(trials).cuda()].cpu().numpy()
+        err = np.abs(y - ref)
+        assert np.all(err <= FP64_TOL * np.maximum(gross, 1.0)), f"{what}: FP64 occurrence tables, max {err.max()}"
+    finally:
+        p.close()
 
 
 def _small_cases():
@@ -53,6 +68,7 @@ def test_small_cases_all_variants(case):
             assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"{case} variant {v}")
     finally:
         p.close()
+    _check_fp64_occ(w, ref, gross, case)
 
 
 @pytest.mark.parametrize("name", ["c0", "c0u"])
@@ -261,6 +277,7 @@ def test_multilayer_workloads_sampled(name, n_sample):
             del ylt
     finally:
         p.close()
+    _check_fp64_occ(w, ref, gross, name, trials)
 
 
 @pytest.mark.parametrize("name,n", [("c0", None), ("c0u", None), ("c1", 40000), ("c3", 8000)])
