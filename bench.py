@@ -176,10 +176,10 @@ def layer_groups(port, with_layers: bool = False):
     return groups if with_layers else [g for g, _ in groups]
 
 
-def occurrence_groups(port):
-    """The skip variant's occurrence groups: runs of up to 8 consecutive
-    layers, as lists of layer ids."""
-    return [list(range(j, min(j + 8, port.n_layers))) for j in range(0, port.n_layers, 8)]
+def occurrence_groups(port, per: int = 8):
+    """The skip variant's occurrence groups: runs of up to 8 (the all-FP64
+    variant's: 4) consecutive layers, as lists of layer ids."""
+    return [list(range(j, min(j + per, port.n_layers))) for j in range(0, port.n_layers, per)]
 
 
 def occurrence_density(port, layers) -> float:
@@ -233,16 +233,19 @@ def algorithmic_bytes(w, variant: str):
         # and event an id and, where X is non-zero, one sector of X
         # (the all-FP64 variant: the same with 8-byte entries of X)
         L = port.n_layers
-        lp = 1 if L <= 1 else (2 if L <= 2 else (4 if L <= 4 else 8))
+        per = 4 if variant == "fp64" else 8  # layers per occurrence group (FP64 tables: 4)
+        lp = 1 if L <= 1 else (2 if L <= 2 else (4 if (L <= 4 or per == 4) else 8))
         xb = 8 if variant == "fp64" else 4
-        groups = occurrence_groups(port)
+        groups = occurrence_groups(port, per)
         dens = [occurrence_density(port, lays) for lays in groups]
         reads = sum(n_events * d * sec(xb * lp) for d in dens)
         build = float(sum(4 * pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (C * xb * lp + C / 8)
         n_groups = len(groups)
-        # FP64 operations of the all-FP64 variant: per (catalogue event, ELT
-        # of a layer) an FMA and an add, per queued event an add per slot
-        flops = 4.0 * C * float(port.elts_per_layer().sum()) + sum(n_events * d * lp for d in dens)
+        # FP64 operations of the all-FP64 variant: its CSR build costs an FMA
+        # per non-zero loss and an add per (loss, layer holding it); the trial
+        # pass an add per slot of every queued event
+        nnz = float((port.elt_losses != 0).sum())
+        flops = 2.0 * nnz + nnz * float(port.elts_per_layer().sum()) / port.n_elt + sum(n_events * d * lp for d in dens)
         return {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
                 "l2": n_groups * ids + build + reads, "fp64_flops": flops}
     if variant == "sparse":
@@ -363,7 +366,8 @@ def main():
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
     # a named variant builds only its own layout (keeps profiling runs small)
     layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_LAYER, "batched": art.ART_LAYOUT_POOL,
-               "fp64": art.ART_LAYOUT_LAYER | art.ART_LAYOUT_OCC64, "sparse": art.ART_LAYOUT_SPARSE}.get(
+               "fp64": art.ART_LAYOUT_LAYER | art.ART_LAYOUT_OCC64 | art.ART_LAYOUT_SPARSE,
+               "sparse": art.ART_LAYOUT_SPARSE}.get(
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
     if args.config == "c3":
         layouts |= art.ART_LAYOUT_GROUP  # the adjoint reads the group tables
@@ -543,16 +547,18 @@ def main():
         cpu = cpu_baseline(args, w)
 
     # kernels of ours launched per step: forward (one per layer for the plain
-    # variant, one occurrence-table build plus a trial pass per occurrence
-    # group for the skip variant, one persistent launch otherwise) + metrics (state init, 6 x
-    # (histogram + select), tail sums, finalize)
+    # variant; one occurrence-table build plus a trial pass per occurrence
+    # group for the skip and all-FP64 variants; one persistent launch
+    # otherwise) + metrics (state init, 6 x (histogram + select), tail sums,
+    # finalize)
     n_groups = len(layer_groups(port))
-    launches = {"plain": L, "skip": 1 + len(occurrence_groups(port))}.get(variant, 1) + 15
+    launches = {"plain": L, "skip": 1 + len(occurrence_groups(port)),
+                "fp64": 1 + len(occurrence_groups(port, 4))}.get(variant, 1) + 15
     if with_grad:
-        # metrics backward (count, weights, grad) + the adjoint: per group a
-        # pass and its reduction (group tables), else per layer a pass and its
-        # reduction plus one scatter
-        launches += 3 + (2 * n_groups if layouts & art.ART_LAYOUT_GROUP else 2 * L + 1)
+        # metrics backward (count, weights, grad) + the adjoint: per group the
+        # event masks, a pass and its reduction (group tables), else per layer
+        # a pass and its reduction plus one scatter
+        launches += 3 + (3 * n_groups if layouts & art.ART_LAYOUT_GROUP else 2 * L + 1)
     if rank == 0:
         line = {
             "metric": "trial-events x ELTs per second", "value": value, "unit": "trial-events*ELTs/s",

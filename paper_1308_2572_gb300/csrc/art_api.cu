@@ -369,28 +369,51 @@ cudaError_t build_occ_groups(art_portfolio* p) {
     if ((e = cudaMalloc(&p->d_ogroups, sizeof(OccBuildGroup) * ng))) return e;
     if ((e = cudaMemcpy(p->d_ogroups, bg.data(), sizeof(OccBuildGroup) * ng, cudaMemcpyHostToDevice))) return e;
     if (p->layouts & ART_LAYOUT_OCC64) {
-        const size_t xb64 = sizeof(double) * ((size_t)p->catalogue + 1) * p->og_lp;
-        p->ogroups64 = p->ogroups;
-        p->og_occ64.assign(ng, nullptr);
-        p->og_bits64.assign(ng, nullptr);
-        std::vector<OccBuildGroup> bg64 = bg;
-        for (int32_t gi = 0; gi < ng && !e; ++gi) {
+        // FP64 groups hold up to 4 layers, so that one group's table
+        // ([C + 1][4] FP64: 64 MB for 2M events) stays in L2 during its pass
+        const int32_t per64 = std::min(L, kMaxOcc64Layers);
+        p->og_lp64 = per64 <= 1 ? 1 : per64 <= 2 ? 2 : 4;
+        const int32_t ng64 = (L + kMaxOcc64Layers - 1) / kMaxOcc64Layers;
+        const size_t xb64 = sizeof(double) * ((size_t)p->catalogue + 1) * p->og_lp64;
+        p->ogroups64.assign(ng64, OccGroupArgs{});
+        p->og_occ64.assign(ng64, nullptr);
+        p->og_bits64.assign(ng64, nullptr);
+        std::vector<OccBuildGroup> bg64(ng64);
+        for (int32_t gi = 0; gi < ng64 && !e; ++gi) {
             if ((e = cudaMalloc(&p->og_occ64[gi], xb64))) break;
             if ((e = cudaMalloc(&p->og_bits64[gi], bb))) break;
             if ((e = cudaMemset(p->og_occ64[gi], 0, xb64))) break;
             if ((e = cudaMemset(p->og_bits64[gi], 0, bb))) break;
             p->occ64_bytes += (int64_t)(xb64 + bb);
-            p->ogroups64[gi].occ = nullptr;
-            p->ogroups64[gi].occ64 = p->og_occ64[gi];
-            p->ogroups64[gi].occ_bits = p->og_bits64[gi];
-            bg64[gi].occ = nullptr;
+            OccGroupArgs& g = p->ogroups64[gi];
+            g.occ64 = p->og_occ64[gi];
+            g.occ_bits = p->og_bits64[gi];
+            g.n_layers = std::min(kMaxOcc64Layers, L - gi * kMaxOcc64Layers);
             bg64[gi].occ_bits = p->og_bits64[gi];
+            bg64[gi].n_layers = g.n_layers;
+            for (int s = 0; s < kMaxOccLayers; ++s) {
+                const bool real = s < g.n_layers;
+                g.layer[s] = real ? gi * kMaxOcc64Layers + s : 0;
+                bg64[gi].layer[s] = g.layer[s];
+            }
         }
         if (e) return e;
-        if ((e = cudaMalloc(&p->d_ogroups64, sizeof(OccBuildGroup) * ng))) return e;
-        if ((e = cudaMemcpy(p->d_ogroups64, bg64.data(), sizeof(OccBuildGroup) * ng, cudaMemcpyHostToDevice))) return e;
-        if ((e = cudaMalloc(&p->d_occ64_ptrs, sizeof(double*) * ng))) return e;
-        if ((e = cudaMemcpy(p->d_occ64_ptrs, p->og_occ64.data(), sizeof(double*) * ng, cudaMemcpyHostToDevice))) return e;
+        if (p->pool_np > 0) {  // slots of each FP64 group holding each pool ELT (for the CSR build)
+            std::vector<uint8_t> sm((size_t)ng64 * p->pool_np, 0);
+            for (int32_t gi = 0; gi < ng64; ++gi)
+                for (int s = 0; s < p->ogroups64[gi].n_layers; ++s) {
+                    const int32_t j = p->ogroups64[gi].layer[s];
+                    for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
+                        sm[(size_t)gi * p->pool_np + p->lids[c]] |= (uint8_t)(1u << s);
+                }
+            if ((e = cudaMalloc(&p->d_slotmask64, sm.size()))) return e;
+            if ((e = cudaMemcpy(p->d_slotmask64, sm.data(), sm.size(), cudaMemcpyHostToDevice))) return e;
+        }
+        if ((e = cudaMalloc(&p->d_ogroups64, sizeof(OccBuildGroup) * ng64))) return e;
+        if ((e = cudaMemcpy(p->d_ogroups64, bg64.data(), sizeof(OccBuildGroup) * ng64, cudaMemcpyHostToDevice))) return e;
+        if ((e = cudaMalloc(&p->d_occ64_ptrs, sizeof(double*) * ng64))) return e;
+        if ((e = cudaMemcpy(p->d_occ64_ptrs, p->og_occ64.data(), sizeof(double*) * ng64, cudaMemcpyHostToDevice)))
+            return e;
     }
     return upload_layer_build(p);
 }
@@ -460,6 +483,7 @@ void free_portfolio(art_portfolio* p) {
     for (uint32_t* b : p->og_bits64) cudaFree(b);
     cudaFree(p->d_ogroups64);
     cudaFree(p->d_occ64_ptrs);
+    cudaFree(p->d_slotmask64);
     cudaFree(p->pool);
     cudaFree(p->pool64);
     cudaFree(p->d_elt_terms);
@@ -631,7 +655,6 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
                                       stream);
             }
             if (e) break;
-            if ((e = build_occ_groups(p))) break;
         }
         if ((p->layouts & (ART_LAYOUT_POOL | ART_LAYOUT_POOL64 | ART_LAYOUT_SPARSE)) && n_elt <= kMaxPoolElts) {
             int epl = 1;
@@ -656,6 +679,9 @@ art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, const flo
                 (e = build_sparse(p, elt_losses_dev, stream)))
                 break;
         }
+        // occurrence groups of the skip (and all-FP64) variants, after the
+        // pool width is known (the FP64 tables' CSR build masks span it)
+        if ((p->layouts & ART_LAYOUT_LAYER) && (e = build_occ_groups(p))) break;
         if ((p->layouts & ART_LAYOUT_GROUP) && (e = build_groups(p, elt_losses_dev, stream))) break;
         if (p->flags & ART_FLAG_L2_PERSIST) {
             int persist_max = 0;

@@ -100,6 +100,12 @@ struct BatchedArgs {
     int32_t slots;
 };
 
+// One entry of the event-major CSR of the non-zero losses (ART_LAYOUT_SPARSE).
+struct SparseEntry {
+    float loss;
+    int32_t elt;
+};
+
 // Compressed layout description (event-major CSR of the non-zero losses).
 struct SparseArgs {
     const uint32_t* ptr;       // [C + 1]
@@ -144,6 +150,7 @@ struct GroupArgs {
 // group's layers hold 0) and its bitmap (bit i set if any X[i][s] > 0); the
 // trial pass then reads those. Passed by value.
 constexpr int kMaxOccLayers = 8;
+constexpr int kMaxOcc64Layers = 4;  // layers per FP64 occurrence group
 struct OccGroupArgs {
     const float* occ;          // [C + 1][lt_pad] FP32
     const double* occ64;       // [C + 1][lt_pad] FP64 (the all-FP64 tables)
@@ -221,7 +228,9 @@ struct art_portfolio {
     std::vector<double*> og_occ64;
     std::vector<uint32_t*> og_bits64;
     art::OccBuildGroup* d_ogroups64 = nullptr;  // bitmaps of the FP64 tables
-    double** d_occ64_ptrs = nullptr;            // [n_ogroups]
+    double** d_occ64_ptrs = nullptr;            // [n_ogroups64]
+    int32_t og_lp64 = 0;                        // slots per row of the FP64 tables (1, 2 or 4)
+    uint8_t* d_slotmask64 = nullptr;            // [n_ogroups64][pool_np]: slots of the group holding the ELT
     int64_t occ64_bytes = 0;
     int64_t group_bytes = 0;
 

@@ -4,11 +4,17 @@
 // As in the skip variant, steps 2-3 (financial terms, ELT sum, occurrence
 // terms) depend on the event id alone, so each call evaluates them once per
 // catalogue event, here in FP64: X[i][s] = O_j(sum_{e in layer j} F_e(l_e[i]))
-// for the layer j in slot s of each occurrence group (up to 8 consecutive
-// layers), with F_e(y) = min(max(m_e y - D_e, 0), Lim_e) as one FP64 FMA and
-// the terms (stored rounded to FP32) widened exactly; the sum follows the
-// layer's ELT order. A bitmap marks the events with some X[i][s] > 0 (bit C,
-// the sentinel for ids outside [0, C), is clear and row C is zero).
+// for the layer j in slot s of each FP64 occurrence group (up to 4
+// consecutive layers, so that a group's table stays in L2), with F_e(y) =
+// min(max(m_e y - D_e, 0), Lim_e) as one FP64 FMA and the terms (stored
+// rounded to FP32) widened exactly. With the CSR of the non-zero losses
+// (ART_LAYOUT_SPARSE) the tables are built from it: per event, F_e of each
+// non-zero loss once, added to the slots of the layers holding ELT e, each
+// layer's sum in ELT id order, so the FP64 work scales with the non-zero
+// losses. Otherwise they come from the per-layer tables (the layer's ELT
+// order; rows without losses give x = 0, o = 0 and skip the arithmetic). A
+// bitmap marks the events with some X[i][s] > 0 (bit C, the sentinel for ids
+// outside [0, C), is clear and row C is zero).
 //
 // The trial pass: a persistent grid of one 1024-thread CTA per SM, the bitmap
 // in shared memory (folded once when it does not fit: a superset test, a
@@ -83,6 +89,13 @@ __global__ void __launch_bounds__(256) build_occ64_kernel(const LayerBuildArgs* 
 #pragma unroll
                 for (int q = 0; q < kMaxLayerElts / 4; ++q)
                     r[q] = q < nq ? __ldcs(row + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                // a row without losses gives x = 0 (F(0) = 0: D >= 0) and
+                // o = 0 (OccR >= 0): its FP64 arithmetic is skipped
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < kMaxLayerElts / 4; ++q)
+                    any |= (r[q].x != 0.0f) | (r[q].y != 0.0f) | (r[q].z != 0.0f) | (r[q].w != 0.0f);
+                if (!any) continue;
                 double x = 0.0;
 #pragma unroll
                 for (int q = 0; q < kMaxLayerElts / 4; ++q) {
@@ -94,6 +107,59 @@ __global__ void __launch_bounds__(256) build_occ64_kernel(const LayerBuildArgs* 
                     }
                 }
                 o[s] = xl_f64(x, a.occ_ret, a.occ_lim);
+                nz |= o[s] > 0.0;
+            }
+        }
+        double* dst = occ64[blockIdx.y] + i * LP;
+        if constexpr (LP == 1) dst[0] = o[0];
+        else {
+#pragma unroll
+            for (int q = 0; q < LP / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(o[2 * q], o[2 * q + 1]);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
+}
+
+// The same tables from the event-major CSR of the non-zero losses: thread i
+// walks event i's entries (in ELT order) and adds F_e in FP64 to the slots of
+// the group's layers that hold ELT e (a per-group mask per ELT). Only the
+// events' non-zero losses are touched, so the FP64 work is per non-zero loss
+// rather than per table column; each layer's sum follows ELT id order.
+template <int LP>
+__global__ void __launch_bounds__(256) build_occ64_csr_kernel(const uint32_t* __restrict__ ptr,
+                                                              const SparseEntry* __restrict__ entries,
+                                                              const double* __restrict__ terms64, int32_t np,
+                                                              const uint8_t* __restrict__ slotmask,
+                                                              const float* __restrict__ occ_terms,
+                                                              const OccBuildGroup* __restrict__ groups,
+                                                              double* const* __restrict__ occ64, int32_t catalogue,
+                                                              int32_t words) {
+    const OccBuildGroup& grp = groups[blockIdx.y];
+    const uint8_t* sm = slotmask + (size_t)blockIdx.y * np;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool nz = false;
+    if (i < catalogue) {
+        double x[LP];
+#pragma unroll
+        for (int s = 0; s < LP; ++s) x[s] = 0.0;
+        const uint32_t k1 = ptr[i + 1];
+        for (uint32_t k = ptr[i]; k < k1; ++k) {
+            const SparseEntry en = entries[k];
+            const uint32_t mask = sm[en.elt];
+            if (!mask) continue;
+            const double f = fin_f64((double)en.loss, terms64[en.elt], terms64[np + en.elt], terms64[2 * np + en.elt]);
+#pragma unroll
+            for (int s = 0; s < LP; ++s)
+                if ((mask >> s) & 1u) x[s] += f;
+        }
+        double o[LP];
+#pragma unroll
+        for (int s = 0; s < LP; ++s) {
+            o[s] = 0.0;
+            if (s < grp.n_layers) {
+                const int32_t j = grp.layer[s];
+                o[s] = xl_f64(x[s], (double)occ_terms[2 * j], (double)occ_terms[2 * j + 1]);
                 nz |= o[s] > 0.0;
             }
         }
@@ -157,14 +223,24 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
         bool bo;
         trial_range(y, t, b, e, bo);
         bad_off_seen |= bo;
-        double sum[LT];
+        // two partial sums per layer, alternating by batch, halve the chains
+        // of dependent FP64 adds (the FP64 unit's latency is long)
+        double sum[LT], sum2[LT];
+        bool odd = false;
 #pragma unroll
-        for (int j = 0; j < LT; ++j) sum[j] = 0.0;
+        for (int j = 0; j < LT; ++j) {
+            sum[j] = 0.0;
+            sum2[j] = 0.0;
+        }
         auto add_row = [&](uint32_t id) {
             double o[LT];
             ld_row64<LT>(g.occ64, id, o);
 #pragma unroll
-            for (int j = 0; j < LT; ++j) sum[j] += o[j];
+            for (int j = 0; j < LT; ++j) {
+                if (odd) sum2[j] += o[j];
+                else sum[j] += o[j];
+            }
+            odd = !odd;
         };
         // ids of a chunk of 32 * E events from c0; empty slots read as -1
         auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
@@ -231,7 +307,7 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
                 bool all = true;
 #pragma unroll
                 for (int j = 0; j < LT; ++j) {
-                    double v = sum[j];
+                    double v = sum[j] + sum2[j];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
                     if (j < g.n_layers) all = all && (v - g.agg_ret[j] >= g.agg_lim[j]);
@@ -249,7 +325,7 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
         double mine = 0.0;
 #pragma unroll
         for (int j = 0; j < LT; ++j) {
-            double v = sum[j];
+            double v = sum[j] + sum2[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
             if (lane == j) mine = v;
@@ -291,21 +367,29 @@ cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8
     const bool early = (p->flags & ART_FLAG_EARLY_EXIT) != 0;
     const int32_t words = (int32_t)(((int64_t)p->catalogue + 31) / 32);
     const dim3 grid((unsigned)(((int64_t)words * 32 + 255) / 256), (unsigned)p->ogroups64.size());
-    switch (p->og_lp) {
+    // from the CSR of the non-zero losses where it exists, else from the
+    // per-layer tables
+    const bool csr = p->sp_ptr && p->d_slotmask64 && p->d_elt_terms64 && p->d_occ;
+    const SparseEntry* en = reinterpret_cast<const SparseEntry*>(p->sp_entries);
+    if (csr) switch (p->og_lp64) {
+        case 1: build_occ64_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        case 2: build_occ64_csr_kernel<2><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        case 4: build_occ64_csr_kernel<4><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+        default: return cudaErrorInvalidValue;
+    }
+    else switch (p->og_lp64) {
         case 1: build_occ64_kernel<1><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
         case 2: build_occ64_kernel<2><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
         case 4: build_occ64_kernel<4><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        case 8: build_occ64_kernel<8><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || y.n_trials == 0) return err;
     for (const OccGroupArgs& g : p->ogroups64) {
-        switch (p->og_lp) {
+        switch (p->og_lp64) {
             case 1: err = launch_group64<1>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
             case 2: err = launch_group64<2>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
             case 4: err = launch_group64<4>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
-            case 8: err = launch_group64<8>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
             default: err = cudaErrorInvalidValue;
         }
         if (err != cudaSuccess) return err;

@@ -43,10 +43,6 @@ namespace {
 
 constexpr int kSparseThreads = 256;
 
-struct SparseEntry {
-    float loss;
-    int32_t elt;
-};
 
 __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
     const float t = s + v;

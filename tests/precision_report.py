@@ -35,7 +35,7 @@ from paper_1308_2572_gb300 import art, workloads  # noqa: E402
 MIXED = (1 | 2 | 8 | 16)  # layer, pool, group and CSR layouts (ART_LAYOUT_*)
 VARIANTS = {"batched (FP32 + FP64 aggregate)": ("ART_VARIANT_BATCHED", MIXED), "sparse": ("ART_VARIANT_SPARSE", MIXED),
             "skip": ("ART_VARIANT_SKIP", MIXED), "plain": ("ART_VARIANT_PLAIN", MIXED),
-            "all-FP64 (occurrence tables)": ("ART_VARIANT_FP64", 1 | 32),
+            "all-FP64 (occurrence tables)": ("ART_VARIANT_FP64", 1 | 16 | 32),
             "all-FP64 (FP64 pool)": ("ART_VARIANT_FP64", 4)}
 
 

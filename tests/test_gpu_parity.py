@@ -27,14 +27,17 @@ FP64_TOL = 1e-12  # |dY| <= 1e-12 G: FP64 arithmetic, only the summation order d
 
 
 def _check_fp64_occ(w, ref, gross, what, trials=None):
-    p = art.portfolio_from_workload(w, layouts=OCC64_LAYOUTS)
-    try:
-        ylt, _ = run_ylt(p, w, art.ART_VARIANT_FP64)
-        y = ylt.cpu().numpy() if trials is None else ylt[:, torch.from_numpy(trials).cuda()].cpu().numpy()
-        err = np.abs(y - ref)
-        assert np.all(err <= FP64_TOL * np.maximum(gross, 1.0)), f"{what}: FP64 occurrence tables, max {err.max()}"
-    finally:
-        p.close()
+    # tables built from the layer tables, and from the CSR of the non-zero losses
+    for layouts in (OCC64_LAYOUTS, OCC64_LAYOUTS | art.ART_LAYOUT_SPARSE):
+        p = art.portfolio_from_workload(w, layouts=layouts)
+        try:
+            ylt, _ = run_ylt(p, w, art.ART_VARIANT_FP64)
+            y = ylt.cpu().numpy() if trials is None else ylt[:, torch.from_numpy(trials).cuda()].cpu().numpy()
+            err = np.abs(y - ref)
+            assert np.all(err <= FP64_TOL * np.maximum(gross, 1.0)), \
+                f"{what}: FP64 occurrence tables (layouts {layouts}), max {err.max()}"
+        finally:
+            p.close()
 
 
 def _small_cases():
