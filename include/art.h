@@ -114,7 +114,8 @@ enum {
 enum {
     ART_FLAG_L2_PERSIST = 1,  /* set a persisting L2 access-policy window over the hot
                                  table on the stream passed to each run call          */
-    ART_FLAG_GRAPH = 2,       /* batched runs replay a cached CUDA graph of the launch */
+    ART_FLAG_GRAPH = 2,       /* art_run_ylt captures its launches (any variant) in a CUDA
+                                 graph once per argument set and replays it            */
     ART_FLAG_EARLY_EXIT = 4   /* skip variant: stop reading a trial once every layer of the
                                  group has reached its aggregate cap (the aggregate never
                                  decreases, so the loss is AggL); same results within FP32

@@ -147,6 +147,40 @@ def test_literal_config1_caps_every_trial():
         p.close()
 
 
+@pytest.mark.parametrize("variant,layouts", [
+    ("ART_VARIANT_PLAIN", ALL_LAYOUTS), ("ART_VARIANT_BATCHED", ALL_LAYOUTS), ("ART_VARIANT_SKIP", ALL_LAYOUTS),
+    ("ART_VARIANT_SPARSE", ALL_LAYOUTS), ("ART_VARIANT_FP64", ALL_LAYOUTS),
+    ("ART_VARIANT_FP64", OCC64_LAYOUTS | art.ART_LAYOUT_SPARSE)])
+def test_graph_replay_every_variant(variant, layouts):
+    """ART_FLAG_GRAPH: the captured launches of each variant replay to the
+    same bits as the direct call, and a new argument set re-captures."""
+    w = workloads.random_case(204, catalogue=3001, n_elt=30, n_layers=21, n_trials=2500, max_len=80)
+    v = getattr(art, variant)
+    p = art.portfolio_from_workload(w, layouts=layouts)
+    g = art.portfolio_from_workload(w, layouts=layouts, flags=art.ART_FLAG_GRAPH)
+    try:
+        ids, off, k, T = device_yet(w)
+        L = w.portfolio.n_layers
+        ref, _ = run_ylt(p, w, v)
+        art.art_set_variant(g, v)
+        for _ in range(3):
+            y = torch.full((L, T), -1.0, dtype=torch.float64, device="cuda")
+            art.art_run_ylt(g, T, ids, off, k, y)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref)
+        # another YLT buffer and a shorter prefix: a new graph
+        half = T // 2
+        y2 = torch.full((L, half), -1.0, dtype=torch.float64, device="cuda")
+        art.art_run_ylt(g, half, ids, None if off is None else off[:half + 1], k, y2)
+        art.art_run_ylt(p, half, ids, None if off is None else off[:half + 1], k, y)
+        torch.cuda.synchronize()
+        # both calls wrote a [L][half] YLT; the direct one into the first L * half doubles of y
+        assert torch.equal(y2.flatten(), y.flatten()[:L * half])
+    finally:
+        p.close()
+        g.close()
+
+
 def test_determinism_and_graph_replay():
     w = workloads.random_case(201, catalogue=2000, n_elt=20, n_layers=40, n_trials=3000, max_len=90)
     p = art.portfolio_from_workload(w)
