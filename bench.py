@@ -549,11 +549,11 @@ def main():
     # kernels of ours launched per step: forward (one per layer for the plain
     # variant; one occurrence-table build plus a trial pass per occurrence
     # group for the skip and all-FP64 variants; one persistent launch
-    # otherwise) + metrics (state init, 6 x (histogram + select), tail sums,
-    # finalize)
+    # otherwise) + metrics (6 radix passes, each fused with its digit pick,
+    # and the tail sums fused with the final reduction)
     n_groups = len(layer_groups(port))
     launches = {"plain": L, "skip": 1 + len(occurrence_groups(port)),
-                "fp64": 1 + len(occurrence_groups(port, 4))}.get(variant, 1) + 15
+                "fp64": 1 + len(occurrence_groups(port, 4))}.get(variant, 1) + 7
     if with_grad:
         # metrics backward (count, weights, grad) + the adjoint: per group the
         # event masks, a pass and its reduction (group tables), else per layer

@@ -9,13 +9,17 @@
 // pattern (sign cleared, which also folds -0 onto +0) orders like the value.
 // A most-significant-digit radix select over 63 bits in six passes (digits of
 // 11, 11, 11, 11, 11 and 8 bits) narrows, for every (layer, probability)
-// problem at once, the prefix of the k-th largest key: each pass histograms
-// the keys that match the prefix found so far (shared-memory histograms,
-// flushed to global with atomics), and a one-CTA-per-problem kernel picks the
-// digit where the count from the top crosses the remaining rank. A last pass
-// sums the values strictly above the k-th largest; TVaR adds the tied
-// remainder: (sum_gt + (k - count_gt) * PML) / k. Sums are FP64 and
-// deterministic (per-thread, per-block, then per-problem in a fixed order).
+// problem at once, the prefix of the k-th largest key. Each pass is one
+// launch: its blocks histogram the keys that match the prefix found so far
+// (shared-memory histograms with warp-aggregated atomics: lanes holding the
+// same digit add once; flushed to global with atomics), and the last block of
+// each layer to finish (a ticket counter after a fence; no block waits for
+// another) picks the digit where the count from the top crosses the
+// remaining rank. A last launch sums the values strictly above the k-th
+// largest, and its last block reduces the partials: TVaR adds the tied
+// remainder, (sum_gt + (k - count_gt) * PML) / k. Seven launches in all. Sums
+// are FP64 and deterministic (per-thread, per-block, then per-problem in a
+// fixed order).
 #include <algorithm>
 #include <cmath>
 
@@ -26,6 +30,7 @@ namespace art {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kUnroll = 4;  // values per thread whose loads are in flight together
 constexpr int kMaxBins = 2048;
 constexpr int kPasses = 6;
 __host__ __device__ constexpr int pass_shift(int i) { return i < 5 ? 52 - 11 * i : 0; }
@@ -69,177 +74,6 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
     return r;
-}
-
-__global__ void init_state_kernel(SelState* st, int n_problems, int n_p, const KParams kq) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_problems) {
-        st[i].prefix = 0;
-        st[i].mask = 0;
-        st[i].k = kq.k[i % n_p];
-        st[i].krem = kq.k[i % n_p];
-    }
-}
-
-// One pass: grid (blocks_per_layer, n_layers). The first pass also writes
-// the block's partial sum of the layer's values (for the mean).
-__global__ void __launch_bounds__(kThreads) hist_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
-                                                        const SelState* __restrict__ st, int shift, int bits,
-                                                        unsigned int* __restrict__ ghist,
-                                                        double* __restrict__ part_sum) {
-    extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
-    __shared__ double sh_red[32];
-    const int nb = 1 << bits;
-    const int j = blockIdx.y;
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
-    unsigned long long pre[kMaxProbs], msk[kMaxProbs];
-#pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) {
-        pre[q] = q < n_p ? st[j * n_p + q].prefix : 1ULL;  // unused slots never match
-        msk[q] = q < n_p ? st[j * n_p + q].mask : 0ULL;
-    }
-    __syncthreads();
-    const double* row = ylt + (size_t)j * (size_t)n;
-    double sum = 0.0;
-    const unsigned dmask = (unsigned)nb - 1u;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = row[i];
-        if (part_sum) sum += v;
-        const unsigned long long key = key_of(v);
-        const unsigned dig = (unsigned)(key >> shift) & dmask;
-#pragma unroll
-        for (int q = 0; q < kMaxProbs; ++q)
-            if (q < n_p && (key & msk[q]) == pre[q]) atomicAdd(&sh_hist[q * nb + dig], 1u);
-    }
-    if (part_sum) {
-        const double r = block_sum(sum, sh_red);
-        if (threadIdx.x == 0) part_sum[(size_t)j * gridDim.x + blockIdx.x] = r;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
-        const unsigned c = sh_hist[i];
-        if (c) atomicAdd(&ghist[((size_t)j * n_p) * kMaxBins + (size_t)(i / nb) * kMaxBins + (i % nb)], c);
-    }
-}
-
-// One CTA per (layer, probability): find the digit where the count of keys
-// from the top reaches the remaining rank, extend the prefix, clear the bins.
-__global__ void __launch_bounds__(kThreads) select_kernel(SelState* st, unsigned int* ghist, int shift, int bits) {
-    __shared__ unsigned long long sh_scan[kThreads];
-    __shared__ int sh_bin;
-    __shared__ unsigned long long sh_above;
-    const int pidx = blockIdx.x;
-    const int nb = 1 << bits;
-    const int per = nb / kThreads > 0 ? nb / kThreads : 1;
-    unsigned int* h = ghist + (size_t)pidx * kMaxBins;
-    const long long krem = st[pidx].krem;
-    // thread i covers descending ranks [i*per, (i+1)*per): bins nb-1-i*per downwards
-    unsigned long long local = 0;
-    if (threadIdx.x * per < nb)
-        for (int r = 0; r < per; ++r) local += h[nb - 1 - (threadIdx.x * per + r)];
-    sh_scan[threadIdx.x] = local;
-    if (threadIdx.x == 0) sh_bin = -1;
-    __syncthreads();
-    // inclusive scan (Hillis-Steele) over the 256 chunk counts, descending bins
-    for (int o = 1; o < kThreads; o <<= 1) {
-        const unsigned long long add = threadIdx.x >= (unsigned)o ? sh_scan[threadIdx.x - o] : 0ULL;
-        __syncthreads();
-        sh_scan[threadIdx.x] += add;
-        __syncthreads();
-    }
-    const unsigned long long incl = sh_scan[threadIdx.x];
-    const unsigned long long excl = incl - local;
-    if (threadIdx.x * per < nb && (long long)excl < krem && krem <= (long long)incl) {
-        unsigned long long run = excl;
-        for (int r = 0; r < per; ++r) {
-            const int bin = nb - 1 - (threadIdx.x * per + r);
-            const unsigned c = h[bin];
-            if ((long long)(run + c) >= krem) {
-                sh_bin = bin;
-                sh_above = run;
-                break;
-            }
-            run += c;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int bin = sh_bin < 0 ? 0 : sh_bin;  // unreachable when counts are consistent
-        st[pidx].prefix |= (unsigned long long)bin << shift;
-        st[pidx].mask |= (unsigned long long)(nb - 1) << shift;
-        st[pidx].krem = krem - (long long)(sh_bin < 0 ? 0 : sh_above);
-    }
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
-}
-
-// Per block and problem: count and sum of values strictly above the k-th key.
-__global__ void __launch_bounds__(kThreads) tail_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
-                                                        const SelState* __restrict__ st,
-                                                        unsigned long long* __restrict__ part_cnt,
-                                                        double* __restrict__ part_sum) {
-    __shared__ double sh_red[32];
-    __shared__ unsigned long long sh_red_u[32];
-    const int j = blockIdx.y;
-    unsigned long long thr[kMaxProbs];
-#pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
-    const double* row = ylt + (size_t)j * (size_t)n;
-    double s[kMaxProbs];
-    unsigned long long c[kMaxProbs];
-    for (int q = 0; q < kMaxProbs; ++q) {
-        s[q] = 0.0;
-        c[q] = 0;
-    }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = row[i];
-        const unsigned long long key = key_of(v);
-#pragma unroll
-        for (int q = 0; q < kMaxProbs; ++q)
-            if (q < n_p && key > thr[q]) {
-                s[q] += v;
-                c[q] += 1;
-            }
-    }
-#pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) {
-        if (q >= n_p) break;
-        const double rs = block_sum(s[q], sh_red);
-        const unsigned long long rc = block_sum_u64(c[q], sh_red_u);
-        if (threadIdx.x == 0) {
-            const size_t w = ((size_t)j * n_p + q) * gridDim.x + blockIdx.x;
-            part_sum[w] = rs;
-            part_cnt[w] = rc;
-        }
-    }
-}
-
-// One warp per (layer, probability): the per-block partials summed by lane
-// stride, then a fixed shuffle tree (deterministic).
-__global__ void finalize_kernel(const SelState* __restrict__ st, int n_layers, int n_p, int nblk, int64_t n,
-                                const double* __restrict__ mean_part, const unsigned long long* __restrict__ tail_cnt,
-                                const double* __restrict__ tail_sum, double* mean, double* pml, double* tvar) {
-    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= n_layers * n_p) return;  // whole warp
-    const int j = i / n_p, q = i % n_p;
-    double m = 0.0, sgt = 0.0;
-    unsigned long long cgt = 0;
-    for (int b = lane; b < nblk; b += 32) {
-        if (q == 0) m += mean_part[(size_t)j * nblk + b];
-        sgt += tail_sum[(size_t)i * nblk + b];
-        cgt += tail_cnt[(size_t)i * nblk + b];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        m += __shfl_xor_sync(0xffffffffu, m, o);
-        sgt += __shfl_xor_sync(0xffffffffu, sgt, o);
-        cgt += __shfl_xor_sync(0xffffffffu, cgt, o);
-    }
-    if (lane != 0) return;
-    if (q == 0 && mean) mean[j] = m / (double)n;
-    const double v = __longlong_as_double((long long)st[i].prefix);
-    const long long k = st[i].k;
-    if (pml) pml[i] = v;
-    if (tvar) tvar[i] = (sgt + (double)(k - (long long)cgt) * v) / (double)k;
 }
 
 // Backward: counts of values above and equal to each PML, then the weights.
@@ -326,10 +160,277 @@ __global__ void __launch_bounds__(kThreads) grad_ylt_kernel(const double* __rest
     }
 }
 
+// Digit pick of one (layer, probability) problem by the whole block: the
+// digit where the count of keys from the top reaches the remaining rank;
+// extends the prefix, clears the problem's bins. Histogram reads bypass L1
+// (the bins were filled by other blocks' atomics).
+__device__ void select_block(SelState* __restrict__ st, unsigned int* __restrict__ h, int shift, int bits,
+                             bool first, long long k0) {
+    __shared__ unsigned int sh_bins[kMaxBins];
+    __shared__ unsigned long long sh_scan[kThreads];
+    __shared__ int sh_bin;
+    __shared__ unsigned long long sh_above;
+    const int nb = 1 << bits;
+    const int per = nb / kThreads > 0 ? nb / kThreads : 1;
+    const long long krem = first ? k0 : st->krem;
+    // every bin requested at once (8 per thread), then cleared for the next pass
+#pragma unroll
+    for (int r = 0; r < kMaxBins / kThreads; ++r) {
+        const int i = r * kThreads + threadIdx.x;
+        if (i < nb) sh_bins[i] = __ldcg(h + i);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+    // thread i covers descending ranks [i*per, (i+1)*per): bins nb-1-i*per downwards
+    unsigned long long local = 0;
+    if (threadIdx.x * per < nb)
+        for (int r = 0; r < per; ++r) local += sh_bins[nb - 1 - (threadIdx.x * per + r)];
+    sh_scan[threadIdx.x] = local;
+    if (threadIdx.x == 0) sh_bin = -1;
+    __syncthreads();
+    for (int o = 1; o < kThreads; o <<= 1) {
+        const unsigned long long add = threadIdx.x >= (unsigned)o ? sh_scan[threadIdx.x - o] : 0ULL;
+        __syncthreads();
+        sh_scan[threadIdx.x] += add;
+        __syncthreads();
+    }
+    const unsigned long long incl = sh_scan[threadIdx.x];
+    const unsigned long long excl = incl - local;
+    if (threadIdx.x * per < nb && (long long)excl < krem && krem <= (long long)incl) {
+        unsigned long long run = excl;
+        for (int r = 0; r < per; ++r) {
+            const int bin = nb - 1 - (threadIdx.x * per + r);
+            const unsigned c = sh_bins[bin];
+            if ((long long)(run + c) >= krem) {
+                sh_bin = bin;
+                sh_above = run;
+                break;
+            }
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int bin = sh_bin < 0 ? 0 : sh_bin;  // unreachable when counts are consistent
+        const unsigned long long prefix = first ? 0ULL : st->prefix, mask = first ? 0ULL : st->mask;
+        st->prefix = prefix | (unsigned long long)bin << shift;
+        st->mask = mask | (unsigned long long)(nb - 1) << shift;
+        st->krem = krem - (long long)(sh_bin < 0 ? 0 : sh_above);
+        if (first) st->k = k0;
+    }
+    __syncthreads();
+}
+
+// One radix pass fused with its digit pick: grid (blocks_per_layer,
+// n_layers). Every block histograms its keys (as hist_kernel) and flushes
+// them with atomics; the last block of a layer to finish (a ticket counter,
+// after a fence: no block waits for another) picks the digits of the
+// layer's problems and resets the counter. The first pass matches every key
+// (it starts the state from k) and writes the blocks' partial sums (mean).
+__global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                               SelState* __restrict__ st, int shift, int bits,
+                                                               bool first, const KParams kq,
+                                                               unsigned int* __restrict__ ghist,
+                                                               double* __restrict__ part_sum,
+                                                               unsigned int* __restrict__ tickets) {
+    extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
+    __shared__ double sh_red[32];
+    __shared__ bool sh_last;
+    const int nb = 1 << bits;
+    const int j = blockIdx.y;
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
+    unsigned long long pre[kMaxProbs], msk[kMaxProbs];
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) {
+        pre[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].prefix) : 1ULL;  // unused slots never match
+        msk[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].mask) : 0ULL;
+    }
+    __syncthreads();
+    const double* row = ylt + (size_t)j * (size_t)n;
+    double sum = 0.0;
+    const unsigned dmask = (unsigned)nb - 1u;
+    const unsigned lane = threadIdx.x & 31;
+    // kUnroll values per thread per step, their loads issued together
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
+         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+        double v[kUnroll];
+        bool valid[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+            valid[u] = i < n;
+            v[u] = valid[u] ? row[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (first) sum += v[u];
+            const unsigned long long key = key_of(v[u]);
+            const unsigned dig = (unsigned)(key >> shift) & dmask;
+#pragma unroll
+            for (int q = 0; q < kMaxProbs; ++q) {
+                if (q < n_p) {
+                    // lanes with the same digit add once (losses cluster:
+                    // many trials share a value, such as a capped layer's AggL)
+                    const bool hit = valid[u] && (key & msk[q]) == pre[q];
+                    const unsigned peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
+                    if (hit && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh_hist[q * nb + dig], __popc(peers));
+                }
+            }
+        }
+    }
+    if (first) {
+        const double r = block_sum(sum, sh_red);
+        if (threadIdx.x == 0) part_sum[(size_t)j * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
+    unsigned int* gh = ghist + ((size_t)j * n_p) * kMaxBins;
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
+        const unsigned c = sh_hist[i];
+        if (c) atomicAdd(&gh[(size_t)(i / nb) * kMaxBins + (i % nb)], c);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(&tickets[j], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    for (int q = 0; q < n_p; ++q)
+        select_block(&st[j * n_p + q], gh + (size_t)q * kMaxBins, shift, bits, first, kq.k[q]);
+    if (threadIdx.x == 0) tickets[j] = 0;
+}
+
+// The tail sums fused with the final reduction: every block writes its
+// partial count and sum of values strictly above each problem's k-th key;
+// the last block of the grid (ticket counter) sums the partials of every
+// problem in a fixed order (one warp per problem) and writes mean, PML and
+// TVaR.
+__global__ void __launch_bounds__(kThreads) tail_final_kernel(const double* __restrict__ ylt, int64_t n, int n_layers,
+                                                              int n_p, const SelState* __restrict__ st,
+                                                              const double* __restrict__ mean_part,
+                                                              unsigned long long* __restrict__ part_cnt,
+                                                              double* __restrict__ part_sum,
+                                                              unsigned int* __restrict__ ticket, double* mean,
+                                                              double* pml, double* tvar) {
+    __shared__ double sh_red[32];
+    __shared__ unsigned long long sh_red_u[32];
+    __shared__ bool sh_last;
+    const int j = blockIdx.y;
+    const int nblk = gridDim.x;
+    unsigned long long thr[kMaxProbs];
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
+    const double* row = ylt + (size_t)j * (size_t)n;
+    double s[kMaxProbs];
+    unsigned long long c[kMaxProbs];
+    for (int q = 0; q < kMaxProbs; ++q) {
+        s[q] = 0.0;
+        c[q] = 0;
+    }
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
+         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+        double v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+            v[u] = i < n ? row[i] : -1.0;  // below every key: never counted
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const unsigned long long key = v[u] < 0.0 ? 0ULL : key_of(v[u]);
+#pragma unroll
+            for (int q = 0; q < kMaxProbs; ++q)
+                if (q < n_p && key > thr[q]) {
+                    s[q] += v[u];
+                    c[q] += 1;
+                }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxProbs; ++q) {
+        if (q >= n_p) break;
+        const double rs = block_sum(s[q], sh_red);
+        const unsigned long long rc = block_sum_u64(c[q], sh_red_u);
+        if (threadIdx.x == 0) {
+            const size_t w = ((size_t)j * n_p + q) * nblk + blockIdx.x;
+            part_sum[w] = rs;
+            part_cnt[w] = rc;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = wib; i < n_layers * n_p; i += kThreads / 32) {
+        const int jj = i / n_p, q = i % n_p;
+        double m = 0.0, sgt = 0.0;
+        unsigned long long cgt = 0;
+        for (int b0 = 0; b0 < nblk; b0 += 32 * 8) {
+            // eight partials per lane requested at once, then summed in order
+            double pm[8], ps[8];
+            unsigned long long pc[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int b = b0 + r * 32 + lane;
+                const bool ok = b < nblk;
+                pm[r] = ok && q == 0 ? __ldcg(mean_part + (size_t)jj * nblk + b) : 0.0;
+                ps[r] = ok ? __ldcg(part_sum + (size_t)i * nblk + b) : 0.0;
+                pc[r] = ok ? __ldcg(part_cnt + (size_t)i * nblk + b) : 0ULL;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                m += pm[r];
+                sgt += ps[r];
+                cgt += pc[r];
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_xor_sync(0xffffffffu, m, o);
+            sgt += __shfl_xor_sync(0xffffffffu, sgt, o);
+            cgt += __shfl_xor_sync(0xffffffffu, cgt, o);
+        }
+        if (lane == 0) {
+            if (q == 0 && mean) mean[jj] = m / (double)n;
+            const double v = __longlong_as_double((long long)__ldcg(&st[i].prefix));
+            const long long k = __ldcg(&st[i].k);
+            if (pml) pml[i] = v;
+            if (tvar) tvar[i] = (sgt + (double)(k - (long long)cgt) * v) / (double)k;
+        }
+    }
+    if (threadIdx.x == 0) *ticket = 0;
+}
+
+// The metric kernels over caller-provided scratch: six fused radix passes,
+// then the fused tail and final reduction (seven launches). hist and the
+// tickets (contiguous, n_layers + 1 counters after the bins) must be zero.
+cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers, int32_t n_p, const KParams& kq,
+                                  int nblk, SelState* st, unsigned int* hist, unsigned int* tickets, double* msum,
+                                  unsigned long long* tcnt, double* tsum, double* mean, double* pml, double* tvar,
+                                  cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < kPasses && !err; ++i) {
+        const int bits = pass_bits(i);
+        const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
+        if (shm > 48 * 1024 &&
+            (err = cudaFuncSetAttribute(hist_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
+            break;
+        hist_select_kernel<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, i == 0,
+                                                                       kq, hist, msum, tickets);
+        err = cudaGetLastError();
+    }
+    if (err) return err;
+    tail_final_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_layers, n_p, st, msum, tcnt, tsum,
+                                                                tickets + n_layers, mean, pml, tvar);
+    return cudaGetLastError();
+}
+
 int blocks_per_layer(int64_t n, int n_layers) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // about 16 values per thread (4 steps of kUnroll)
     int64_t want = (n + (int64_t)kThreads * 16 - 1) / ((int64_t)kThreads * 16);
     int64_t cap = std::max<int64_t>(1, (4LL * sms + n_layers - 1) / n_layers);
     return (int)std::max<int64_t>(1, std::min(want, cap));
@@ -351,10 +452,11 @@ cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const do
                         double* mean, double* pml, double* tvar, cudaStream_t s) {
     const int nblk = blocks_per_layer(n, n_layers);
     const int n_prob = n_layers * n_p;
-    // scratch: k values, state, histograms, partial sums
+    // scratch: state, histograms and tickets (zeroed together), partial sums
     const size_t o_st = 0;
     const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
-    const size_t o_ms = align256(o_h + sizeof(unsigned int) * kMaxBins * (size_t)n_prob);
+    const size_t hist_bytes = sizeof(unsigned int) * (kMaxBins * (size_t)n_prob + n_layers + 1);
+    const size_t o_ms = align256(o_h + hist_bytes);
     const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
     const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
     const size_t total = align256(o_ts + sizeof(double) * (size_t)n_prob * nblk);
@@ -363,35 +465,12 @@ cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const do
     if (err != cudaSuccess) return err;
     KParams kq = {};
     for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs[q], n);
-    auto* st = (SelState*)(w + o_st);
     auto* hist = (unsigned int*)(w + o_h);
-    auto* msum = (double*)(w + o_ms);
-    auto* tcnt = (unsigned long long*)(w + o_tc);
-    auto* tsum = (double*)(w + o_ts);
-    do {
-        if ((err = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kMaxBins * (size_t)n_prob, s))) break;
-        init_state_kernel<<<(n_prob + 255) / 256, 256, 0, s>>>(st, n_prob, n_p, kq);
-        if ((err = cudaGetLastError())) break;
-        for (int i = 0; i < kPasses && !err; ++i) {
-            const int bits = pass_bits(i);
-            const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
-            if (shm > 48 * 1024) {
-                err = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-                if (err) break;
-            }
-            hist_kernel<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, hist,
-                                                                   i == 0 ? msum : nullptr);
-            if ((err = cudaGetLastError())) break;
-            select_kernel<<<n_prob, kThreads, 0, s>>>(st, hist, pass_shift(i), bits);
-            err = cudaGetLastError();
-        }
-        if (err) break;
-        tail_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_p, st, tcnt, tsum);
-        if ((err = cudaGetLastError())) break;
-        finalize_kernel<<<(n_prob + 3) / 4, 128, 0, s>>>(st, n_layers, n_p, nblk, n, msum, tcnt, tsum, mean, pml,
-                                                         tvar);
-        err = cudaGetLastError();
-    } while (0);
+    err = cudaMemsetAsync(hist, 0, hist_bytes, s);
+    if (!err)
+        err = launch_metric_kernels(ylt, n, n_layers, n_p, kq, nblk, (SelState*)(w + o_st), hist,
+                                    hist + kMaxBins * (size_t)n_prob, (double*)(w + o_ms),
+                                    (unsigned long long*)(w + o_tc), (double*)(w + o_ts), mean, pml, tvar, s);
     const cudaError_t e2 = cudaFreeAsync(w, s);
     return err ? err : e2;
 }
@@ -484,7 +563,8 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     const int n_prob = n_layers * n_p;
     const size_t o_st = 0;
     const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
-    const size_t o_ms = align256(o_h + sizeof(unsigned int) * kMaxBins * (size_t)n_prob);
+    const size_t hist_bytes = sizeof(unsigned int) * (kMaxBins * (size_t)n_prob + n_layers + 1);
+    const size_t o_ms = align256(o_h + hist_bytes);
     const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
     const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
     const size_t total = align256(o_ts + sizeof(double) * (size_t)n_prob * nblk);
@@ -497,36 +577,15 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     }
     KParams kq = {};
     for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs_host[q], n_trials);
-    auto* st = (SelState*)(w + o_st);
     auto* hist = (unsigned int*)(w + o_h);
-    auto* msum = (double*)(w + o_ms);
-    auto* tcnt = (unsigned long long*)(w + o_tc);
-    auto* tsum = (double*)(w + o_ts);
-    do {
-        // the scratch keeps the previous call's contents: the histograms must start at zero
-        if ((err = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kMaxBins * (size_t)n_prob, stream))) break;
-        init_state_kernel<<<(n_prob + 255) / 256, 256, 0, stream>>>(st, n_prob, n_p, kq);
-        if ((err = cudaGetLastError())) break;
-        for (int i = 0; i < kPasses && !err; ++i) {
-            const int bits = pass_bits(i);
-            const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
-            if (shm > 48 * 1024) {
-                err = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-                if (err) break;
-            }
-            hist_kernel<<<dim3(nblk, n_layers), kThreads, shm, stream>>>(ylt_dev, n_trials, n_p, st, pass_shift(i),
-                                                                        bits, hist, i == 0 ? msum : nullptr);
-            if ((err = cudaGetLastError())) break;
-            select_kernel<<<n_prob, kThreads, 0, stream>>>(st, hist, pass_shift(i), bits);
-            err = cudaGetLastError();
-        }
-        if (err) break;
-        tail_kernel<<<dim3(nblk, n_layers), kThreads, 0, stream>>>(ylt_dev, n_trials, n_p, st, tcnt, tsum);
-        if ((err = cudaGetLastError())) break;
-        finalize_kernel<<<(n_prob + 3) / 4, 128, 0, stream>>>(st, n_layers, n_p, nblk, n_trials, msum, tcnt, tsum,
-                                                                  mean_dev, pml_dev, tvar_dev);
-        err = cudaGetLastError();
-    } while (0);
+    // the scratch keeps the previous call's contents: the histograms and the
+    // tickets must start at zero
+    err = cudaMemsetAsync(hist, 0, hist_bytes, stream);
+    if (!err)
+        err = launch_metric_kernels(ylt_dev, n_trials, n_layers, n_p, kq, nblk, (SelState*)(w + o_st), hist,
+                                    hist + kMaxBins * (size_t)n_prob, (double*)(w + o_ms),
+                                    (unsigned long long*)(w + o_tc), (double*)(w + o_ts), mean_dev, pml_dev,
+                                    tvar_dev, stream);
     if (err != cudaSuccess) {
         set_last_error(err);
         return ART_ECUDA;
