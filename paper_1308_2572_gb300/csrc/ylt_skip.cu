@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGrou
                 } else {
                     w = wi < (uint32_t)smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);
                 }
-                nz[k] = (w >> (uid[k] & 31)) & 1u;
+                nz[k] = __funnelshift_r(w, 0u, uid[k]) & 1u;  // bit uid mod 32 of the word
             }
             if constexpr (COMPACT) {
 #pragma unroll
@@ -352,7 +352,11 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGrou
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < E; ++k) add_occ<LT>(o[k], hi, lo);
+                // empty slots hold +0, which two-sum adds exactly: no test
+#pragma unroll
+                for (int k = 0; k < E; ++k)
+#pragma unroll
+                    for (int j = 0; j < LT; ++j) two_sum_acc(hi[j], lo[j], o[k][j]);
             }
             if (early_exit && group_capped<LT>(g, hi, lo)) {
                 // the rest of the trial cannot change its loss: skip it (and
