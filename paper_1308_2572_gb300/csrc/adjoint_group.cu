@@ -30,7 +30,8 @@
 //     the set of layers covering column k and W[S] = sum_{j in S} g_j a_j is
 //     a 2^LT-entry table of the trial's weights (FP32, per warp, built per
 //     trial); at the end of the trial the partials are summed across the
-//     warp and lane k adds the total to its compensated FP32 pair.
+//     warp (recursive halving: 31 shuffles for every column at once) and
+//     lane k adds column k's total to its compensated FP32 pair.
 // A trial with no layer on the middle branch costs only its branch codes.
 // The lane values are reduced warp -> CTA -> grid in a fixed order (no
 // atomics: deterministic); FP64 arithmetic runs only in that final
@@ -237,19 +238,18 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
         if (code == 2) two_sum_add(al_h, al_l, gt);
         const bool mid_l = code == 1 && gt != 0.0f;
         if (!__ballot_sync(FULL, mid_l)) continue;  // no layer of the group has a middle-branch weight
-        // the trial's weight table W[S] = sum_{j in S} g_j a_j
+        // the trial's weight table W[S] = sum_{j in S} g_j a_j, by doubling:
+        // W[S + 2^b] = W[S] + g_b a_b for S < 2^b (the terms in increasing j,
+        // as a direct sum adds them)
         {
-            float ga[LT];
-#pragma unroll
-            for (int j = 0; j < LT; ++j) ga[j] = __shfl_sync(FULL, mid_l ? gt : 0.0f, j);
-            for (int s = lane; s < NW; s += 32) {
-                float w = 0.0f;
-#pragma unroll
-                for (int j = 0; j < LT; ++j)
-                    if ((s >> j) & 1) w += ga[j];
-                s_w[s] = w;
-            }
+            if (lane == 0) s_w[0] = 0.0f;
             __syncwarp();
+#pragma unroll
+            for (int b = 0; b < LT; ++b) {
+                const float gb = __shfl_sync(FULL, mid_l ? gt : 0.0f, b);
+                for (int s = lane; s < (1 << b); s += 32) s_w[s + (1 << b)] = s_w[s] + gb;
+                __syncwarp();
+            }
         }
         uint64_t cnt_mid = 0, cnt_cap = 0;
         float part[NP];
@@ -341,13 +341,25 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
         if (lane < qn) eval_event<NP, LT>(g, masks, (uint32_t)q[lane], (uint32_t)y.catalogue - 1u, s_spread, s_w, s_col, cnt_mid, cnt_cap, part);
         __syncwarp();
         flush_counts();
-        // the trial's column partials, summed across the warp, go to lane k's pair
+        // the trial's column partials summed across the warp by recursive
+        // halving (31 shuffles for all columns): at distance o a lane keeps
+        // the half of its columns selected by bit o of its index and adds
+        // the partner's copy of that half; lane k ends with column k
+        {
+            float v[32];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            float v = part[k];
+            for (int k = 0; k < 32; ++k) v[k] = k < NP ? part[k] : 0.0f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-            if (lane == k) two_sum_add(col_h, col_l, v);
+            for (int o = 16; o > 0; o >>= 1) {
+                const bool upper = (lane & o) != 0;
+#pragma unroll
+                for (int i = 0; i < o; ++i) {
+                    const float keep = upper ? v[i + o] : v[i];
+                    const float send = upper ? v[i] : v[i + o];
+                    v[i] = keep + __shfl_xor_sync(FULL, send, o);
+                }
+            }
+            if (lane < NP) two_sum_add(col_h, col_l, v[0]);
         }
         __syncwarp();  // the weight table is rebuilt by the next trial
     }
