@@ -77,14 +77,16 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
 }
 
 // Backward: counts of values above and equal to each PML, then the weights.
+template <int NQ>
 __global__ void __launch_bounds__(kThreads) count_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                          const double* __restrict__ pml,
                                                          unsigned long long* __restrict__ part_gt,
                                                          unsigned long long* __restrict__ part_eq) {
     __shared__ unsigned long long sh_red_u[32];
     const int j = blockIdx.y;
-    unsigned long long thr[kMaxProbs], gt[kMaxProbs], eq[kMaxProbs];
-    for (int q = 0; q < kMaxProbs; ++q) {
+    unsigned long long thr[NQ], gt[NQ], eq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
         thr[q] = q < n_p ? key_of(pml[j * n_p + q]) : 0;
         gt[q] = 0;
         eq[q] = 0;
@@ -93,13 +95,13 @@ __global__ void __launch_bounds__(kThreads) count_kernel(const double* __restric
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long key = key_of(row[i]);
 #pragma unroll
-        for (int q = 0; q < kMaxProbs; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             gt[q] += (q < n_p && key > thr[q]) ? 1 : 0;
             eq[q] += (q < n_p && key == thr[q]) ? 1 : 0;
         }
     }
 #pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         if (q >= n_p) break;
         const unsigned long long a = block_sum_u64(gt[q], sh_red_u);
         const unsigned long long b = block_sum_u64(eq[q], sh_red_u);
@@ -127,6 +129,7 @@ __global__ void weights_kernel(int n_layers, int n_p, int nblk, const KParams kq
     w_eq[i] = ce ? ((k - (double)cg) / (k * (double)ce)) : 0.0;
 }
 
+template <int NQ>
 __global__ void __launch_bounds__(kThreads) grad_ylt_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                             const double* __restrict__ pml,
                                                             const double* __restrict__ gmean,
@@ -136,9 +139,10 @@ __global__ void __launch_bounds__(kThreads) grad_ylt_kernel(const double* __rest
                                                             double* __restrict__ gylt) {
     const int j = blockIdx.y;
     const double base = gmean ? gmean[j] / (double)n : 0.0;
-    unsigned long long thr[kMaxProbs];
-    double cg[kMaxProbs], ce[kMaxProbs];
-    for (int q = 0; q < kMaxProbs; ++q) {
+    unsigned long long thr[NQ];
+    double cg[NQ], ce[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
         const bool on = q < n_p && gtvar;
         thr[q] = on ? key_of(pml[j * n_p + q]) : 0;
         cg[q] = on ? gtvar[j * n_p + q] * w_gt[j * n_p + q] : 0.0;
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) grad_ylt_kernel(const double* __rest
         const unsigned long long key = key_of(row[i]);
         double g = base;
 #pragma unroll
-        for (int q = 0; q < kMaxProbs; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             if (q < n_p) {
                 if (key > thr[q]) g += cg[q];
                 else if (key == thr[q]) g += ce[q];
@@ -227,6 +231,7 @@ __device__ void select_block(SelState* __restrict__ st, unsigned int* __restrict
 // after a fence: no block waits for another) picks the digits of the
 // layer's problems and resets the counter. The first pass matches every key
 // (it starts the state from k) and writes the blocks' partial sums (mean).
+template <int NQ>
 __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                                SelState* __restrict__ st, int shift, int bits,
                                                                bool first, const KParams kq,
@@ -239,9 +244,9 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
     const int nb = 1 << bits;
     const int j = blockIdx.y;
     for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
-    unsigned long long pre[kMaxProbs], msk[kMaxProbs];
+    unsigned long long pre[NQ], msk[NQ];
 #pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         pre[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].prefix) : 1ULL;  // unused slots never match
         msk[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].mask) : 0ULL;
     }
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
             const unsigned long long key = key_of(v[u]);
             const unsigned dig = (unsigned)(key >> shift) & dmask;
 #pragma unroll
-            for (int q = 0; q < kMaxProbs; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 if (q < n_p) {
                     // lanes with the same digit add once (losses cluster:
                     // many trials share a value, such as a capped layer's AggL)
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
 // the last block of the grid (ticket counter) sums the partials of every
 // problem in a fixed order (one warp per problem) and writes mean, PML and
 // TVaR.
+template <int NQ>
 __global__ void __launch_bounds__(kThreads) tail_final_kernel(const double* __restrict__ ylt, int64_t n, int n_layers,
                                                               int n_p, const SelState* __restrict__ st,
                                                               const double* __restrict__ mean_part,
@@ -316,29 +322,32 @@ __global__ void __launch_bounds__(kThreads) tail_final_kernel(const double* __re
     __shared__ bool sh_last;
     const int j = blockIdx.y;
     const int nblk = gridDim.x;
-    unsigned long long thr[kMaxProbs];
+    unsigned long long thr[NQ];
 #pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
+    for (int q = 0; q < NQ; ++q) thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
     const double* row = ylt + (size_t)j * (size_t)n;
-    double s[kMaxProbs];
-    unsigned long long c[kMaxProbs];
-    for (int q = 0; q < kMaxProbs; ++q) {
+    double s[NQ];
+    unsigned long long c[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
         s[q] = 0.0;
         c[q] = 0;
     }
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
          i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
         double v[kUnroll];
+        bool valid[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-            v[u] = i < n ? row[i] : -1.0;  // below every key: never counted
+            valid[u] = i < n;
+            v[u] = valid[u] ? row[i] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const unsigned long long key = v[u] < 0.0 ? 0ULL : key_of(v[u]);
+            const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;  // 0: never above a threshold
 #pragma unroll
-            for (int q = 0; q < kMaxProbs; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < n_p && key > thr[q]) {
                     s[q] += v[u];
                     c[q] += 1;
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) tail_final_kernel(const double* __re
         }
     }
 #pragma unroll
-    for (int q = 0; q < kMaxProbs; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         if (q >= n_p) break;
         const double rs = block_sum(s[q], sh_red);
         const unsigned long long rc = block_sum_u64(c[q], sh_red_u);
@@ -409,20 +418,24 @@ cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers
                                   int nblk, SelState* st, unsigned int* hist, unsigned int* tickets, double* msum,
                                   unsigned long long* tcnt, double* tsum, double* mean, double* pml, double* tvar,
                                   cudaStream_t s) {
+    // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
+    auto hist_k = n_p <= 1 ? hist_select_kernel<1> : n_p <= 2 ? hist_select_kernel<2>
+                : n_p <= 4 ? hist_select_kernel<4> : hist_select_kernel<8>;
+    auto tail_k = n_p <= 1 ? tail_final_kernel<1> : n_p <= 2 ? tail_final_kernel<2>
+                : n_p <= 4 ? tail_final_kernel<4> : tail_final_kernel<8>;
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < kPasses && !err; ++i) {
         const int bits = pass_bits(i);
         const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
-        if (shm > 48 * 1024 &&
-            (err = cudaFuncSetAttribute(hist_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
+        if (shm > 48 * 1024 && (err = cudaFuncSetAttribute(hist_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
             break;
-        hist_select_kernel<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, i == 0,
-                                                                       kq, hist, msum, tickets);
+        hist_k<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, i == 0, kq, hist, msum,
+                                                           tickets);
         err = cudaGetLastError();
     }
     if (err) return err;
-    tail_final_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_layers, n_p, st, msum, tcnt, tsum,
-                                                                tickets + n_layers, mean, pml, tvar);
+    tail_k<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_layers, n_p, st, msum, tcnt, tsum, tickets + n_layers,
+                                                     mean, pml, tvar);
     return cudaGetLastError();
 }
 
@@ -495,14 +508,18 @@ cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers,
     auto* wg = (double*)(w + o_wg);
     auto* we = (double*)(w + o_we);
     do {
+        // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
+        auto count_k = n_p <= 1 ? count_kernel<1> : n_p <= 2 ? count_kernel<2>
+                     : n_p <= 4 ? count_kernel<4> : count_kernel<8>;
+        auto grad_k = n_p <= 1 ? grad_ylt_kernel<1> : n_p <= 2 ? grad_ylt_kernel<2>
+                    : n_p <= 4 ? grad_ylt_kernel<4> : grad_ylt_kernel<8>;
         if (gtvar) {
-            count_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_p, pml, pg, pe);
+            count_k<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_p, pml, pg, pe);
             if ((err = cudaGetLastError())) break;
             weights_kernel<<<(n_prob + 127) / 128, 128, 0, s>>>(n_layers, n_p, nblk, kq, pg, pe, wg, we);
             if ((err = cudaGetLastError())) break;
         }
-        grad_ylt_kernel<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, gtvar ? n_p : 0, pml, gmean, gtvar, wg, we,
-                                                                 gylt);
+        grad_k<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, gtvar ? n_p : 0, pml, gmean, gtvar, wg, we, gylt);
         err = cudaGetLastError();
     } while (0);
     const cudaError_t e2 = cudaFreeAsync(w, s);
