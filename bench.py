@@ -246,8 +246,11 @@ def algorithmic_bytes(w, variant: str):
         # pass an add per slot of every queued event
         nnz = float((port.elt_losses != 0).sum())
         flops = 2.0 * nnz + nnz * float(port.elts_per_layer().sum()) / port.n_elt + sum(n_events * d * lp for d in dens)
-        return {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
-                "l2": n_groups * ids + build + reads, "fp64_flops": flops}
+        out = {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
+               "l2": n_groups * ids + build + reads}
+        if variant == "fp64":
+            out["fp64_flops"] = flops
+        return out
     if variant == "sparse":
         nnz_per_event = float((port.elt_losses != 0).sum(axis=0).mean())
         csr = 4 * (C + 1) + 8 * float((port.elt_losses != 0).sum())
