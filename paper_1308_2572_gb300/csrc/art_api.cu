@@ -542,12 +542,15 @@ art_status validate_yet(int64_t n_trials, const int32_t* ids, const int64_t* off
     return ART_OK;
 }
 
+// build_tables false: the skip and all-FP64 variants reuse the occurrence
+// tables a previous call on the stream wrote (the host-run path builds them
+// once for all its chunks).
 cudaError_t run_forward(art_portfolio* p, int variant, const YetArgs& y, double* ylt, uint8_t* branch,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool build_tables = true) {
     if (variant == ART_VARIANT_PLAIN) return launch_plain(p, y, ylt, branch, s);
-    if (variant == ART_VARIANT_SKIP) return launch_skip(p, y, ylt, branch, s);
+    if (variant == ART_VARIANT_SKIP) return launch_skip(p, y, ylt, branch, s, build_tables);
     if (variant == ART_VARIANT_SPARSE) return launch_sparse(p, y, ylt, branch, s);
-    if (variant == ART_VARIANT_FP64 && !p->ogroups64.empty()) return launch_skip64(p, y, ylt, branch, s);
+    if (variant == ART_VARIANT_FP64 && !p->ogroups64.empty()) return launch_skip64(p, y, ylt, branch, s, build_tables);
     return launch_batched(p, y, ylt, branch, variant == ART_VARIANT_FP64, s);
 }
 
@@ -883,6 +886,13 @@ art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* e
     // the copy stream must not run ahead of work already queued on `stream`
     if ((e = cudaEventRecord(p->ev_done[0], stream))) return fail(e);
     if ((e = cudaEventRecord(p->ev_done[1], stream))) return fail(e);
+    // the occurrence tables of the skip and all-FP64 variants depend on the
+    // terms only: written once here, read by every chunk
+    const bool tables = variant == ART_VARIANT_SKIP || (variant == ART_VARIANT_FP64 && !p->ogroups64.empty());
+    if (tables) {
+        const YetArgs none{nullptr, nullptr, 0, 0, p->catalogue};
+        if ((e = run_forward(p, variant, none, nullptr, nullptr, stream, true))) return fail(e);
+    }
     int64_t c = 0;
     for (int64_t t0 = 0; t0 < n_trials && !e; t0 += chunk, ++c) {
         const int slot = (int)(c & 1);
@@ -903,7 +913,7 @@ art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* e
         YetArgs y{p->stage_ids[slot] - i0, trial_off_host ? p->stage_off[slot] : nullptr, nt,
                   trial_off_host ? 0 : events_per_trial, p->catalogue};
         if (!trial_off_host) y.ids = p->stage_ids[slot];
-        if ((e = run_forward(p, variant, y, p->stage_ylt[slot], nullptr, stream))) break;
+        if ((e = run_forward(p, variant, y, p->stage_ylt[slot], nullptr, stream, !tables))) break;
         if ((e = cudaMemcpy2DAsync(ylt_host + t0, sizeof(double) * n_trials, p->stage_ylt[slot], sizeof(double) * nt,
                                    sizeof(double) * nt, p->n_layers, cudaMemcpyDeviceToHost, stream)))
             break;

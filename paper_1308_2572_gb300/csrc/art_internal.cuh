@@ -280,8 +280,12 @@ cudaError_t launch_payouts(art_portfolio* p, int32_t j, const YetArgs& y, double
                            double* ylt, cudaStream_t s);
 cudaError_t launch_sparse(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
 cudaError_t build_sparse(art_portfolio* p, const float* src, cudaStream_t s);
-cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
-cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s);
+// build: write the occurrence tables first (false: reuse the ones the last
+// call on this stream wrote with the same terms)
+cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s,
+                        bool build = true);
+cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s,
+                          bool build = true);
 cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np, uint32_t* bitmap, cudaStream_t s);
 // Write every occurrence group's X and bitmap (one launch) from the layer tables.
 cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s);

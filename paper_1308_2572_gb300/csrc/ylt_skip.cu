@@ -542,10 +542,11 @@ cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s) {
+cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s,
+                        bool build) {
     const bool early = (p->flags & ART_FLAG_EARLY_EXIT) != 0;
     // steps 2-3 once per catalogue event, with the terms as they are now
-    cudaError_t err = build_occurrence(p, s);
+    cudaError_t err = build ? build_occurrence(p, s) : cudaSuccess;
     if (err != cudaSuccess || y.n_trials == 0) return err;
     for (const OccGroupArgs& g : p->ogroups) {
         switch (p->og_lp) {

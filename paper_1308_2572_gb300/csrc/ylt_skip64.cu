@@ -363,7 +363,8 @@ cudaError_t launch_group64(const OccGroupArgs& g, const YetArgs& y, int num_sms,
 
 }  // namespace
 
-cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s) {
+cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t* branch, cudaStream_t s,
+                          bool build) {
     const bool early = (p->flags & ART_FLAG_EARLY_EXIT) != 0;
     const int32_t words = (int32_t)(((int64_t)p->catalogue + 31) / 32);
     const dim3 grid((unsigned)(((int64_t)words * 32 + 255) / 256), (unsigned)p->ogroups64.size());
@@ -371,17 +372,22 @@ cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8
     // per-layer tables
     const bool csr = p->sp_ptr && p->d_slotmask64 && p->d_elt_terms64 && p->d_occ;
     const SparseEntry* en = reinterpret_cast<const SparseEntry*>(p->sp_entries);
-    if (csr) switch (p->og_lp64) {
-        case 1: build_occ64_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        case 2: build_occ64_csr_kernel<2><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        case 4: build_occ64_csr_kernel<4><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        default: return cudaErrorInvalidValue;
-    }
-    else switch (p->og_lp64) {
-        case 1: build_occ64_kernel<1><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        case 2: build_occ64_kernel<2><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        case 4: build_occ64_kernel<4><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
-        default: return cudaErrorInvalidValue;
+    if (build) {
+        if (csr) {
+            switch (p->og_lp64) {
+                case 1: build_occ64_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+                case 2: build_occ64_csr_kernel<2><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+                case 4: build_occ64_csr_kernel<4><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+                default: return cudaErrorInvalidValue;
+            }
+        } else {
+            switch (p->og_lp64) {
+                case 1: build_occ64_kernel<1><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+                case 2: build_occ64_kernel<2><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+                case 4: build_occ64_kernel<4><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
+                default: return cudaErrorInvalidValue;
+            }
+        }
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || y.n_trials == 0) return err;

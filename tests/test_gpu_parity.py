@@ -216,18 +216,28 @@ def test_determinism_and_graph_replay():
 
 
 def test_host_buffers_match_device_path():
-    for w in (workloads.random_case(202, n_trials=5000, max_len=80), workloads.make("c0u")):
-        p = art.portfolio_from_workload(w)
-        try:
-            dev, _ = run_ylt(p, w, art.ART_VARIANT_BATCHED)
-            L, T = w.portfolio.n_layers, w.yet.n_trials
-            ids = torch.from_numpy(w.yet.event_ids).pin_memory()
-            off = None if w.yet.trial_off is None else torch.from_numpy(w.yet.trial_off)
-            out = torch.zeros((L, T), dtype=torch.float64).pin_memory()
-            art.art_run_ylt_host(p, T, ids, off, w.yet.events_per_trial, out)
-            assert torch.equal(out, dev.cpu())
-        finally:
-            p.close()
+    """art_run_ylt_host (chunks of the YET copied from host memory, the YLT
+    copied back) gives the device path's bits for every variant; the last
+    workload spans two chunks."""
+    cases = (workloads.random_case(202, n_trials=5000, max_len=80), workloads.make("c0u"),
+             workloads.random_case(205, catalogue=20011, n_elt=12, n_layers=11, n_trials=50000, dense_k=400,
+                                   nnz_frac=0.05))
+    variants = [(art.ART_VARIANT_BATCHED, ALL_LAYOUTS), (art.ART_VARIANT_SKIP, ALL_LAYOUTS),
+                (art.ART_VARIANT_SPARSE, ALL_LAYOUTS), (art.ART_VARIANT_PLAIN, ALL_LAYOUTS),
+                (art.ART_VARIANT_FP64, OCC64_LAYOUTS | art.ART_LAYOUT_SPARSE)]
+    for w in cases:
+        for v, layouts in variants:
+            p = art.portfolio_from_workload(w, layouts=layouts)
+            try:
+                dev, _ = run_ylt(p, w, v)
+                L, T = w.portfolio.n_layers, w.yet.n_trials
+                ids = torch.from_numpy(w.yet.event_ids).pin_memory()
+                off = None if w.yet.trial_off is None else torch.from_numpy(w.yet.trial_off)
+                out = torch.zeros((L, T), dtype=torch.float64).pin_memory()
+                art.art_run_ylt_host(p, T, ids, off, w.yet.events_per_trial, out)
+                assert torch.equal(out, dev.cpu()), (w.name, v)
+            finally:
+                p.close()
 
 
 def test_out_of_range_ids_flag_without_trapping():
