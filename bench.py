@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probes", action="store_true", help="skip the libart bandwidth probes")
+    ap.add_argument("--graph", action="store_true",
+                    help="ART_FLAG_GRAPH: the forward's launches replay from a captured CUDA graph")
     ap.add_argument("--l2-persist", action="store_true",
                     help="persisting L2 access-policy window over the hot table (ART_FLAG_L2_PERSIST)")
     ap.add_argument("--trials", type=int, default=0,
@@ -374,8 +376,8 @@ def main():
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
     if args.config == "c3":
         layouts |= art.ART_LAYOUT_GROUP  # the adjoint reads the group tables
-    p = art.portfolio_from_workload(w, device=dev, layouts=layouts,
-                                    flags=art.ART_FLAG_L2_PERSIST if args.l2_persist else 0)
+    base_flags = (art.ART_FLAG_L2_PERSIST if args.l2_persist else 0) | (art.ART_FLAG_GRAPH if args.graph else 0)
+    p = art.portfolio_from_workload(w, device=dev, layouts=layouts, flags=base_flags)
     ids = torch.from_numpy(yet.event_ids).to(dev)
     off = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).to(dev)
     ylt = torch.empty((L, T), dtype=torch.float64, device=dev)
@@ -533,7 +535,7 @@ def main():
     # optional early exit (capped trials stop being read), reported separately
     early = None
     if variant == "skip":
-        art.art_set_flags(p, art.ART_FLAG_EARLY_EXIT)
+        art.art_set_flags(p, art.ART_FLAG_EARLY_EXIT | base_flags)
         art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -543,7 +545,7 @@ def main():
         torch.cuda.synchronize(dev)
         early = {"forward_ms": e0.elapsed_time(e1) / 5,
                  "note": "ART_FLAG_EARLY_EXIT: trials stop being read once capped; not part of value"}
-        art.art_set_flags(p, 0)
+        art.art_set_flags(p, base_flags)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -569,7 +571,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
-                       "variant": variant, "autotune": tune, "l2_persist": bool(args.l2_persist), "layers": L, "trials": T, "events": yet.n_events,
+                       "variant": variant, "autotune": tune, "l2_persist": bool(args.l2_persist), "graph": bool(args.graph), "layers": L, "trials": T, "events": yet.n_events,
                        "lookups_per_step": lookups,
                        "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
                        "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"},
