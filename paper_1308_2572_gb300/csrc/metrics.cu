@@ -51,6 +51,22 @@ __device__ __forceinline__ unsigned long long key_of(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
 
+// A problem whose mask covers every key bit is decided: its prefix is the key.
+constexpr unsigned long long kAllKeyBits = 0x7fffffffffffffffULL;
+
+// Block-wide maximum of a 64-bit value (valid in thread 0).
+__device__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = max(r, sh[i]);
+    return r;
+}
+
 // Block-wide sum of a double in a fixed order (warp tree, then warps in order).
 __device__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -236,19 +252,33 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
                                                                SelState* __restrict__ st, int shift, int bits,
                                                                bool first, const KParams kq,
                                                                unsigned int* __restrict__ ghist,
+                                                               unsigned long long* __restrict__ minmax,
                                                                double* __restrict__ part_sum,
                                                                unsigned int* __restrict__ tickets) {
     extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
     __shared__ double sh_red[32];
+    __shared__ unsigned long long sh_red_u[32];
     __shared__ bool sh_last;
     const int nb = 1 << bits;
     const int j = blockIdx.y;
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
     unsigned long long pre[NQ], msk[NQ];
+    bool done[NQ];
+    bool all_done = true;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         pre[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].prefix) : 1ULL;  // unused slots never match
         msk[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].mask) : 0ULL;
+        done[q] = q >= n_p || msk[q] == kAllKeyBits;  // decided by an earlier pass
+        all_done = all_done && done[q];
+    }
+    if (all_done) return;  // the same for every block of the layer: no ticket is taken
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
+    // largest candidate key and largest complement (the smallest candidate)
+    unsigned long long kmax[NQ], kinv[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        kmax[q] = 0;
+        kinv[q] = 0;
     }
     __syncthreads();
     const double* row = ylt + (size_t)j * (size_t)n;
@@ -276,9 +306,13 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
                 if (q < n_p) {
                     // lanes with the same digit add once (losses cluster:
                     // many trials share a value, such as a capped layer's AggL)
-                    const bool hit = valid[u] && (key & msk[q]) == pre[q];
+                    const bool hit = valid[u] && !done[q] && (key & msk[q]) == pre[q];
                     const unsigned peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
                     if (hit && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh_hist[q * nb + dig], __popc(peers));
+                    if (hit) {
+                        kmax[q] = max(kmax[q], key);
+                        kinv[q] = max(kinv[q], ~key);
+                    }
                 }
             }
         }
@@ -286,6 +320,16 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
     if (first) {
         const double r = block_sum(sum, sh_red);
         if (threadIdx.x == 0) part_sum[(size_t)j * gridDim.x + blockIdx.x] = r;
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (q >= n_p || done[q]) continue;
+        const unsigned long long a = block_max_u64(kmax[q], sh_red_u);
+        const unsigned long long b = block_max_u64(kinv[q], sh_red_u);
+        if (threadIdx.x == 0) {
+            atomicMax(&minmax[2 * ((size_t)j * n_p + q)], a);
+            atomicMax(&minmax[2 * ((size_t)j * n_p + q) + 1], b);
+        }
     }
     __syncthreads();
     unsigned int* gh = ghist + ((size_t)j * n_p) * kMaxBins;
@@ -299,8 +343,30 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
-    for (int q = 0; q < n_p; ++q)
-        select_block(&st[j * n_p + q], gh + (size_t)q * kMaxBins, shift, bits, first, kq.k[q]);
+    for (int q = 0; q < n_p; ++q) {
+        if (done[q]) continue;
+        SelState* sq = &st[j * n_p + q];
+        unsigned long long* mm = &minmax[2 * ((size_t)j * n_p + q)];
+        const unsigned long long hi = __ldcg(mm), lo = ~__ldcg(mm + 1);
+        if (hi == lo) {
+            // every candidate holds the same key (a capped layer's AggL, say):
+            // the k-th largest is decided without the remaining digits
+            if (threadIdx.x == 0) {
+                sq->prefix = hi;
+                sq->mask = kAllKeyBits;
+                sq->krem = 1;
+                if (first) sq->k = kq.k[q];
+            }
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) gh[(size_t)q * kMaxBins + i] = 0;
+        } else {
+            select_block(sq, gh + (size_t)q * kMaxBins, shift, bits, first, kq.k[q]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mm[0] = 0;
+            mm[1] = 0;
+        }
+    }
     if (threadIdx.x == 0) tickets[j] = 0;
 }
 
@@ -415,9 +481,9 @@ __global__ void __launch_bounds__(kThreads) tail_final_kernel(const double* __re
 // then the fused tail and final reduction (seven launches). hist and the
 // tickets (contiguous, n_layers + 1 counters after the bins) must be zero.
 cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers, int32_t n_p, const KParams& kq,
-                                  int nblk, SelState* st, unsigned int* hist, unsigned int* tickets, double* msum,
-                                  unsigned long long* tcnt, double* tsum, double* mean, double* pml, double* tvar,
-                                  cudaStream_t s) {
+                                  int nblk, SelState* st, unsigned int* hist, unsigned long long* minmax,
+                                  unsigned int* tickets, double* msum, unsigned long long* tcnt, double* tsum,
+                                  double* mean, double* pml, double* tvar, cudaStream_t s) {
     // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
     auto hist_k = n_p <= 1 ? hist_select_kernel<1> : n_p <= 2 ? hist_select_kernel<2>
                 : n_p <= 4 ? hist_select_kernel<4> : hist_select_kernel<8>;
@@ -429,8 +495,8 @@ cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers
         const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
         if (shm > 48 * 1024 && (err = cudaFuncSetAttribute(hist_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
             break;
-        hist_k<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, i == 0, kq, hist, msum,
-                                                           tickets);
+        hist_k<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, i == 0, kq, hist,
+                                                           minmax, msum, tickets);
         err = cudaGetLastError();
     }
     if (err) return err;
@@ -468,7 +534,10 @@ cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const do
     // scratch: state, histograms and tickets (zeroed together), partial sums
     const size_t o_st = 0;
     const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
-    const size_t hist_bytes = sizeof(unsigned int) * (kMaxBins * (size_t)n_prob + n_layers + 1);
+    // bins, then per problem the candidates' largest key and complement, then
+    // the tickets: zeroed together
+    const size_t hist_bytes = sizeof(unsigned int) * kMaxBins * (size_t)n_prob +
+                              sizeof(unsigned long long) * 2 * (size_t)n_prob + sizeof(unsigned int) * (n_layers + 1);
     const size_t o_ms = align256(o_h + hist_bytes);
     const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
     const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
@@ -482,7 +551,10 @@ cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const do
     err = cudaMemsetAsync(hist, 0, hist_bytes, s);
     if (!err)
         err = launch_metric_kernels(ylt, n, n_layers, n_p, kq, nblk, (SelState*)(w + o_st), hist,
-                                    hist + kMaxBins * (size_t)n_prob, (double*)(w + o_ms),
+                                    (unsigned long long*)(hist + kMaxBins * (size_t)n_prob),
+                                    (unsigned int*)((unsigned long long*)(hist + kMaxBins * (size_t)n_prob) +
+                                                    2 * (size_t)n_prob),
+                                    (double*)(w + o_ms),
                                     (unsigned long long*)(w + o_tc), (double*)(w + o_ts), mean, pml, tvar, s);
     const cudaError_t e2 = cudaFreeAsync(w, s);
     return err ? err : e2;
@@ -580,7 +652,10 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     const int n_prob = n_layers * n_p;
     const size_t o_st = 0;
     const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
-    const size_t hist_bytes = sizeof(unsigned int) * (kMaxBins * (size_t)n_prob + n_layers + 1);
+    // bins, then per problem the candidates' largest key and complement, then
+    // the tickets: zeroed together
+    const size_t hist_bytes = sizeof(unsigned int) * kMaxBins * (size_t)n_prob +
+                              sizeof(unsigned long long) * 2 * (size_t)n_prob + sizeof(unsigned int) * (n_layers + 1);
     const size_t o_ms = align256(o_h + hist_bytes);
     const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
     const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
@@ -600,7 +675,10 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     err = cudaMemsetAsync(hist, 0, hist_bytes, stream);
     if (!err)
         err = launch_metric_kernels(ylt_dev, n_trials, n_layers, n_p, kq, nblk, (SelState*)(w + o_st), hist,
-                                    hist + kMaxBins * (size_t)n_prob, (double*)(w + o_ms),
+                                    (unsigned long long*)(hist + kMaxBins * (size_t)n_prob),
+                                    (unsigned int*)((unsigned long long*)(hist + kMaxBins * (size_t)n_prob) +
+                                                    2 * (size_t)n_prob),
+                                    (double*)(w + o_ms),
                                     (unsigned long long*)(w + o_tc), (double*)(w + o_ts), mean_dev, pml_dev,
                                     tvar_dev, stream);
     if (err != cudaSuccess) {
