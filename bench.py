@@ -337,7 +337,7 @@ def main():
     ap.add_argument("--config", default="c1")
     ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64", "skip", "sparse"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -517,7 +517,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        each = []
         for _ in range(args.e2e_steps):
+            t1 = time.perf_counter()
             art.art_run_ylt_host(p, T, ids_h, off_h, K, ylt_h, stream)
             ylt_d.copy_(ylt_h, non_blocking=True)
             art.art_metrics(ylt_d, T, L, probs, mean, pml, tvar, stream)
@@ -525,11 +527,25 @@ def main():
             out_h[L:L + L * n_p].copy_(pml.reshape(-1), non_blocking=True)
             out_h[L + L * n_p:].copy_(tvar.reshape(-1), non_blocking=True)
             torch.cuda.synchronize(dev)
+            each.append((time.perf_counter() - t1) * 1e3)
         e2e_s = rank_max((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
+        # the host-to-device link on its own, same pinned buffer, one copy
+        nb = min(ids_h.numel(), 1 << 28)
+        dst = torch.empty(nb, dtype=ids_h.dtype, device=dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dst.copy_(ids_h[:nb], non_blocking=True)
+        c0.record()
+        dst.copy_(ids_h[:nb], non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize(dev)
+        link_gbs = nb * ids_h.element_size() / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        del dst
         h2d = yet.event_ids.nbytes + (0 if yet.trial_off is None else yet.trial_off.nbytes) + 8 * L * T
         d2h = 8 * L * T + 8 * L * (1 + 2 * n_p)
         e2e = {"value": whole_job_rate(lookups, world, e2e_s), "unit": "trial-events*ELTs/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_each_step_rank0": [round(t, 3) for t in each],
+               "h2d_copy_gbs_rank0": link_gbs,
                "path": "art_run_ylt_host (pinned host YET, chunked H2D overlapped with compute) + art_metrics"}
 
     # optional early exit (capped trials stop being read), reported separately

@@ -115,6 +115,37 @@ def test_metrics_edges_and_determinism():
         np.testing.assert_allclose(a[0], om, rtol=1e-12)
 
 
+@pytest.mark.parametrize("probs", [[0.5], [0.5, 0.9, 0.99, 0.999],
+                                   [0.3, 0.45, 0.5, 0.55, 0.9, 0.99, 0.996, 0.999]])
+def test_metrics_ties_decided_after_some_digits(probs):
+    """Layers whose k-th largest loss sits in a block of equal losses among
+    distinct losses sharing its leading bits: the candidates collapse to one
+    key only after several radix digits, and the selection stops there. Next
+    to a constant layer, a lognormal one and one capped above every quantile
+    (with uncapped losses of the same binary exponent); PML exact, TVaR and
+    mean within 1e-12 of the oracle's full sort, for 1, 4 and 8 probabilities."""
+    rng = np.random.default_rng(11)
+    n = 50021
+    y = np.empty((5, n))
+    y[0] = 2.0e7
+    y[1] = rng.lognormal(10.0, 2.0, n)
+    base = 1234.5
+    y[2] = base * (1.0 + rng.uniform(-1e-9, 1e-9, n))      # same leading ~30 bits, distinct
+    y[2, rng.choice(n, 6000, replace=False)] = base         # the ties straddle the median
+    y[3] = np.where(rng.uniform(size=n) < 0.9995, 5.0e6, rng.uniform(4.2e6, 5.0e6, n))
+    y[4] = np.where(rng.uniform(size=n) < 0.5, 0.0, 1.0)    # half zeros, half one value
+    yd = torch.from_numpy(y).cuda().contiguous()
+    a = gpu_metrics(yd, probs)
+    b = gpu_metrics(yd, probs)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    om, op, ot = oracle.metrics(y, probs)
+    np.testing.assert_array_equal(a[1], op)
+    np.testing.assert_allclose(a[2], ot, rtol=1e-12)
+    np.testing.assert_allclose(a[0], om, rtol=1e-12)
+    assert np.all(a[1][2][np.asarray(probs) == 0.5] == base)
+
+
 def test_catalogue_beyond_twice_the_shared_bitmap():
     """A catalogue of 4,000,037 events: the skip forward's and the group
     adjoint's bitmaps no longer fold into shared memory, so the upper events'
