@@ -337,7 +337,7 @@ def main():
     ap.add_argument("--config", default="c1")
     ap.add_argument("--variant", default="auto", choices=["auto", "plain", "batched", "fp64", "skip", "sparse"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -272,6 +272,20 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
         all_done = all_done && done[q];
     }
     if (all_done) return;  // the same for every block of the layer: no ticket is taken
+    // problems with the same prefix and mask see the same candidates (every
+    // problem in the first pass; later, probabilities whose k-th largest
+    // keys share their leading digits): the first of them, the source,
+    // histograms for all
+    __shared__ int sh_src[kMaxProbs];
+    int src[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        src[q] = q;
+#pragma unroll
+        for (int r = NQ - 1; r >= 0; --r)
+            if (r < q && !done[r] && !done[q] && pre[r] == pre[q] && msk[r] == msk[q]) src[q] = r;
+        if (threadIdx.x == 0 && q < n_p) sh_src[q] = src[q];
+    }
     for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
     // largest candidate key and largest complement (the smallest candidate)
     unsigned long long kmax[NQ], kinv[NQ];
@@ -303,15 +317,19 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
             const unsigned dig = (unsigned)(key >> shift) & dmask;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                if (q < n_p) {
-                    // lanes with the same digit add once (losses cluster:
-                    // many trials share a value, such as a capped layer's AggL)
-                    const bool hit = valid[u] && !done[q] && (key & msk[q]) == pre[q];
-                    const unsigned peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
-                    if (hit && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh_hist[q * nb + dig], __popc(peers));
-                    if (hit) {
-                        kmax[q] = max(kmax[q], key);
-                        kinv[q] = max(kinv[q], ~key);
+                if (q < n_p && !done[q] && src[q] == q) {  // the same for the whole block
+                    const bool hit = valid[u] && (key & msk[q]) == pre[q];
+                    // after the first pass few warps hold a candidate at all
+                    if (first || __any_sync(0xffffffffu, hit)) {
+                        // lanes with the same digit add once (losses cluster:
+                        // many trials share a value, such as a capped layer's AggL)
+                        const unsigned peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
+                        if (hit && lane == (unsigned)(__ffs(peers) - 1))
+                            atomicAdd(&sh_hist[q * nb + dig], __popc(peers));
+                        if (hit) {
+                            kmax[q] = max(kmax[q], key);
+                            kinv[q] = max(kinv[q], ~key);
+                        }
                     }
                 }
             }
@@ -320,6 +338,16 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
     if (first) {
         const double r = block_sum(sum, sh_red);
         if (threadIdx.x == 0) part_sum[(size_t)j * gridDim.x + blockIdx.x] = r;
+    }
+    // a problem that shares its source's candidates shares its extremes
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+        for (int r = 0; r < NQ; ++r)
+            if (r < q && src[q] == r) {
+                kmax[q] = kmax[r];
+                kinv[q] = kinv[r];
+            }
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -334,8 +362,9 @@ __global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __r
     __syncthreads();
     unsigned int* gh = ghist + ((size_t)j * n_p) * kMaxBins;
     for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
-        const unsigned c = sh_hist[i];
-        if (c) atomicAdd(&gh[(size_t)(i / nb) * kMaxBins + (i % nb)], c);
+        const int q = i >> bits, b = i & (int)dmask;
+        const unsigned c = sh_hist[sh_src[q] * nb + b];  // zero for a decided problem
+        if (c) atomicAdd(&gh[(size_t)q * kMaxBins + b], c);
     }
     __threadfence();
     __syncthreads();

@@ -101,6 +101,7 @@ def test_metrics_edges_and_determinism():
     cases = [torch.zeros((2, 1), dtype=torch.float64),                         # one trial
              torch.full((3, 4097), 7.5, dtype=torch.float64),                  # all tied
              torch.rand((1, 123457), generator=g, dtype=torch.float64) * 1e9,  # ragged size
+             torch.rand((3, 123458), generator=g, dtype=torch.float64) * 1e9,  # even length, ragged
              torch.tensor([[0.0, -0.0, 1.0, 5e-324, 1e300, 2.0]], dtype=torch.float64)]  # signed zero, subnormal
     for y in cases:
         yd = y.cuda().contiguous()
@@ -144,6 +145,27 @@ def test_metrics_ties_decided_after_some_digits(probs):
     np.testing.assert_allclose(a[2], ot, rtol=1e-12)
     np.testing.assert_allclose(a[0], om, rtol=1e-12)
     assert np.all(a[1][2][np.asarray(probs) == 0.5] == base)
+
+
+def test_metrics_on_a_table_not_on_a_16_byte_boundary():
+    """A table that starts 8 bytes past a 16-byte boundary (even row length):
+    the metrics agree with the same table on an aligned copy and with the
+    oracle."""
+    torch.manual_seed(4)
+    L, n = 3, 40002
+    y = torch.distributions.LogNormal(10.0, 2.0).sample((L, n)).double()
+    buf = torch.zeros(L * n + 2, dtype=torch.float64, device="cuda")
+    off = buf[1:1 + L * n].view(L, n)
+    off.copy_(y.cuda())
+    assert off.data_ptr() % 16 == 8
+    probs = [0.9, 0.99, 0.999]
+    a = gpu_metrics(off, probs)
+    b = gpu_metrics(y.cuda().contiguous(), probs)
+    om, op, ot = oracle.metrics(y.numpy(), probs)
+    for r in (a, b):
+        np.testing.assert_array_equal(r[1], op)
+        np.testing.assert_allclose(r[2], ot, rtol=1e-12)
+        np.testing.assert_allclose(r[0], om, rtol=1e-12)
 
 
 def test_catalogue_beyond_twice_the_shared_bitmap():
