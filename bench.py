@@ -472,7 +472,7 @@ def main():
     ab = algorithmic_bytes(w, variant)
     secs = fwd_mean / 1e3
     achieved = ab["s8d"] / secs / 1e9
-    # measured limits the driver's figures do not cover (libart probes)
+    # measured limits the copy-bandwidth and GEMM peaks do not cover (libart probes)
     probes = {}
     if rank == 0 and not args.no_probes:
         probes = {"l2_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 64 << 20),

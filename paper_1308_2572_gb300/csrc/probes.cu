@@ -1,6 +1,6 @@
 // probes.cu -- measurements of the limits the ARA kernels run against (the
-// paper has no counterpart; they give the roofline denominators the driver's
-// copy-bandwidth and GEMM figures do not cover).
+// paper has no counterpart; they give the roofline denominators that a
+// device's copy-bandwidth and GEMM peaks do not cover).
 //
 //   ART_PROBE_STREAM     streaming read of a buffer (GB/s of buffer bytes)
 //   ART_PROBE_GATHER32   random 32-byte sector reads over a buffer (GB/s of
