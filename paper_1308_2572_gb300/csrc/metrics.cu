@@ -535,12 +535,19 @@ cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers
 }
 
 int blocks_per_layer(int64_t n, int n_layers) {
-    int dev = 0, sms = 148;
+    int dev = 0, sms = 148, l2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     // about 16 values per thread (4 steps of kUnroll)
     int64_t want = (n + (int64_t)kThreads * 16 - 1) / ((int64_t)kThreads * 16);
-    int64_t cap = std::max<int64_t>(1, (4LL * sms + n_layers - 1) / n_layers);
+    // a YLT larger than L2 streams from HBM in every pass, and more blocks
+    // keep more of its loads in flight (8 per SM); one that L2 holds is
+    // re-read from L2, where each block's fixed cost (clearing, flushing
+    // and ticketing its histograms) weighs more (4 per SM)
+    const bool streamed = (double)n * (double)n_layers * sizeof(double) > (double)l2;
+    const int64_t per_sm = streamed ? 8 : 4;
+    int64_t cap = std::max<int64_t>(1, (per_sm * sms + n_layers - 1) / n_layers);
     return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
