@@ -6,16 +6,19 @@
 // largest trial loss and TVaR_p the mean of the k largest.
 //
 // Exact selection without a sort: trial losses are >= 0, so the FP64 bit
-// pattern (sign cleared, which also folds -0 onto +0) orders like the value.
-// A most-significant-digit radix select over 63 bits in six passes (digits of
+// pattern (sign cleared, which also folds -0 onto +0) orders like the value. A
+// most-significant-digit radix select over 63 bits in six passes (digits of
 // 11, 11, 11, 11, 11 and 8 bits) narrows, for every (layer, probability)
 // problem at once, the prefix of the k-th largest key. Each pass is one
 // launch: its blocks histogram the keys that match the prefix found so far
 // (shared-memory histograms with warp-aggregated atomics: lanes holding the
 // same digit add once; flushed to global with atomics), and the last block of
 // each layer to finish (a ticket counter after a fence; no block waits for
-// another) picks the digit where the count from the top crosses the
-// remaining rank. A last launch sums the values strictly above the k-th
+// another) picks the digit where the count from the top crosses the remaining
+// rank. Problems of a layer that share a prefix (all of them in the first
+// pass) share one histogram, and a problem whose candidates all hold one key
+// (their smallest and largest agree) is decided at once, its later passes
+// returning early. A last launch sums the values strictly above the k-th
 // largest, and its last block reduces the partials: TVaR adds the tied
 // remainder, (sum_gt + (k - count_gt) * PML) / k. Seven launches in all. Sums
 // are FP64 and deterministic (per-thread, per-block, then per-problem in a
