@@ -32,6 +32,14 @@ MUTANTS = {
     "grad_occ_sign": ("row[0] = -a * n_occ_mid;", "row[0] = a * n_occ_mid;"),
     "grad_mult_ignores_branch": ("if (xl_branch(elt_mult[e] * y, elt_ded[e], elt_lim[e]) == 1) dm[e] += y;", "dm[e] += y;"),
     "running_first_payout": ("double pd = cum[d] - (d ? cum[d - 1] : 0.0);", "double pd = cum[d] - (d ? cum[d - 1] : cum[d]);"),
+    "tvar_wrong_divisor": ("tvar[(int64_t)j * n_p + q] = top / (double)k;",
+                           "tvar[(int64_t)j * n_p + q] = top / (double)(k > 1 ? k - 1 : k);"),
+    "tvar_drops_kth": ("for (int64_t i = 0; i < k; ++i) top += buf[i];", "for (int64_t i = 0; i + 1 < k; ++i) top += buf[i];"),
+    "mean_wrong_divisor": ("mean[j] = s / (double)n_trials;", "mean[j] = s / (double)(n_trials > 1 ? n_trials - 1 : 1);"),
+    "grad_occ_lim_counts_mid": ("row[1] = a * n_occ_cap;", "row[1] = a * n_occ_mid;"),
+    "grad_agg_lim_on_mid_branch": ("row[3] = cc;", "row[3] = a;"),
+    "grad_mult_ignores_agg_branch": ("for (int32_t e = 0; e < n_elt; ++e) dm[e] *= a;", ""),
+    "aggregate_retention_dropped": ("ylt[w] = xl(s, p->agg_ret[j], p->agg_lim[j]);", "ylt[w] = xl(s, 0.0, p->agg_lim[j]);"),
 }
 
 
