@@ -40,6 +40,9 @@ MUTANTS = {
     "grad_agg_lim_on_mid_branch": ("row[3] = cc;", "row[3] = a;"),
     "grad_mult_ignores_agg_branch": ("for (int32_t e = 0; e < n_elt; ++e) dm[e] *= a;", ""),
     "aggregate_retention_dropped": ("ylt[w] = xl(s, p->agg_ret[j], p->agg_lim[j]);", "ylt[w] = xl(s, 0.0, p->agg_lim[j]);"),
+    "running_occurrence_limit_dropped": ("lo[d] = xl(lo[d], occ_ret[j], occ_lim[j]);",
+                                         "lo[d] = xl(lo[d], occ_ret[j], INFINITY);"),
+    "running_cumulative_restarts": ("cum[d] = lo[d] + (d ? cum[d - 1] : 0.0);", "cum[d] = lo[d];"),
 }
 
 
