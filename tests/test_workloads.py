@@ -85,3 +85,27 @@ def test_random_cases_are_seeded():
     c = workloads.random_case(6)
     assert np.array_equal(a.yet.event_ids, b.yet.event_ids)
     assert not np.array_equal(a.portfolio.elt_losses, c.portfolio.elt_losses)
+
+
+def _branches(name, n_trials=None):
+    import oracle  # test infrastructure: the FP64 reference
+    w = workloads.make(name, n_trials=n_trials)
+    y = oracle.ylt(w.oracle_problem())[0]
+    lim = w.portfolio.agg_lim[:, None]
+    zero, cap = (y == 0).mean(axis=1), (y == lim).mean(axis=1)
+    return zero, 1.0 - zero - cap, cap, ((y > 0) & (y < lim)).any(axis=0).mean()
+
+
+def test_parity_workloads_reach_every_aggregate_branch():
+    """The unsaturated and multi-layer workloads put trials on all three
+    pieces of the aggregate terms (zero, middle, capped), so parity and
+    gradient tests exercise each; the literal one-layer terms cap every
+    trial."""
+    zero, mid, cap, any_mid = _branches("c3", 2000)
+    assert any_mid > 0.9                      # nearly every trial is on some layer's middle piece
+    assert np.all(mid > 0.05)
+    assert cap[0] > 0.05 and zero[-1] > 0.5   # low layers cap often, high layers rarely attach
+    zero, mid, cap, _ = _branches("c1u", 2000)
+    assert zero[0] > 0.1 and mid[0] > 0.5 and cap[0] > 0.005
+    zero, mid, cap, _ = _branches("c1", 500)
+    assert cap[0] == 1.0
