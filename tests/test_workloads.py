@@ -109,3 +109,13 @@ def test_parity_workloads_reach_every_aggregate_branch():
     assert zero[0] > 0.1 and mid[0] > 0.5 and cap[0] > 0.005
     zero, mid, cap, _ = _branches("c1", 500)
     assert cap[0] == 1.0
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_pool_workloads_spread_over_the_aggregate_branches(name):
+    """The log-uniform layer terms of the pool workloads leave about a
+    quarter of (layer, trial) results at zero, a quarter capped and half in
+    between, with most layers at least 10% in between."""
+    zero, mid, cap, _ = _branches(name, 300)
+    assert 0.15 < zero.mean() < 0.4 and 0.15 < cap.mean() < 0.4 and mid.mean() > 0.35
+    assert (mid >= 0.1).mean() > 0.45
