@@ -256,7 +256,8 @@ ART_API art_status art_run_payouts(art_portfolio* p, int32_t layer, int64_t n_tr
  * integer), PML_p = the k-th largest Y_{j,.} and TVaR_p = the mean of the k
  * largest. Exact selection (radix select on the FP64 bit patterns), FP64 sums.
  *
- *  ylt_dev     [n_layers][n_trials] FP64, values >= 0 (the YLT).
+ *  ylt_dev     [n_layers][n_trials] FP64, values >= 0 (the YLT);
+ *              1 <= n_trials <= 2^31 - 1, 1 <= n_layers <= 65535.
  *  probs_host  [n_p] probabilities in (0, 1); 1 <= n_p <= 8.
  *  mean_dev    [n_layers] FP64 output (may be NULL).
  *  pml_dev     [n_layers][n_p] FP64 output (may be NULL).
@@ -306,9 +307,13 @@ ART_API art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trials, 
  * TVaR_{j,q}) with respect to the YLT: grad_ylt[j][t] = gm_j / T
  * + sum_q gt_{j,q} w_{j,q}(t), where w = 1/k for Y > PML, (k - #greater) /
  * (k #equal) for Y == PML (ties share the boundary weight), 0 below.
+ *  ylt_dev, n_trials, n_layers: as art_metrics; probs_host and n_p (0 <= n_p
+ *                    <= 8) may be NULL and 0 when grad_tvar_dev is NULL.
  *  pml_dev           [n_layers][n_p] from art_metrics on the same YLT.
  *  grad_mean_dev     [n_layers] or NULL; grad_tvar_dev [n_layers][n_p] or NULL.
  *  grad_ylt_dev      [n_layers][n_trials] FP64 output.
+ * Errors: ART_EINVAL (sizes, a NULL YLT or output, TVaR gradients without
+ * PML or probabilities), ART_ENOMEM, ART_ECUDA.
  */
 ART_API art_status art_metrics_backward(const double* ylt_dev, int64_t n_trials, int32_t n_layers,
                                 const double* probs_host, int32_t n_p, const double* pml_dev,
