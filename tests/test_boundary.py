@@ -90,6 +90,14 @@ def test_other_entry_points_reject_bad_arguments_on_the_host(art):
     bad = np.array([1.0])
     assert L.art_metrics(fake, 10, 1, bad.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
     assert L.art_metrics(fake, 10, 1, probs.ctypes.data, 9, None, None, None, None) == art.ART_EINVAL
+    # the documented size limits: trials below 2^31, layers up to 65535
+    assert L.art_metrics(fake, 1 << 31, 1, probs.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
+    assert L.art_metrics(fake, 10, 65536, probs.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
+    assert L.art_metrics(fake, 10, 0, probs.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
+    assert L.art_metrics_noalloc(fake, 10, 65536, probs.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
+    # TVaR gradients need the PML and the probabilities
+    assert L.art_metrics_backward(fake, 10, 1, None, 0, None, None, fake, fake, None) == art.ART_EINVAL
+    assert L.art_metrics_backward(fake, 10, 1, probs.ctypes.data, 1, None, None, fake, fake, None) == art.ART_EINVAL
     assert L.art_metrics_backward(fake, 10, 1, None, 0, None, None, fake, None, None) == art.ART_EINVAL
     assert L.art_run_ylt_backward(None, 10, fake, None, 5, fake, fake, fake, fake, None) == art.ART_EINVAL
     assert L.art_get_device_status(None, None) == art.ART_EINVAL
