@@ -194,7 +194,10 @@ ART_API art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t tr
  * aggregate terms telescope to XL(S; AggR, AggL) because AggR >= 0, so event
  * order (and the timestamps) does not change Y.
  *
- *  n_trials           T >= 0 (0 is a no-op).
+ *  n_trials           0 <= T <= 2^40 (0 is a no-op); a dense YET also needs
+ *                     T K <= 2^62, and every trial must hold fewer than 2^31
+ *                     events (the kernels index positions within a trial in
+ *                     32 bits).
  *  event_ids_dev      int32 event ids. Dense: [T][K]. CSR: trial t is
  *                     event_ids_dev[off[t] .. off[t+1]); must not be NULL for
  *                     CSR input, even when every trial is empty.
