@@ -145,7 +145,7 @@ typedef struct {
  *  elt_lim_host       per-ELT terms but not their form; this is the reading).
  *                     m_e, D_e finite >= 0; Lim_e > 0 or +INFINITY.
  *                     elt_mult_host may be NULL (all 1).
- *  n_layers           1..65536.
+ *  n_layers           1..65536 (art_metrics takes at most 65535 per call).
  *  layer_elt_off_host [n_layers + 1], starts at 0, non-decreasing; layer j
  *                     covers layer_elt_ids_host[off[j] .. off[j+1]), 1..32
  *                     distinct ELT ids per layer.
@@ -287,9 +287,10 @@ ART_API art_status art_metrics(const double* ylt_dev, int64_t n_trials, int32_t 
  * (8 MiB) in size; every GPU that loads the library holds those 8 MiB until
  * the process exits. The scratch needed is about
  *   n_layers * n_p * (8 KiB + 32 B + 16 B * b) + n_layers * 8 B * b
- * with b = min(ceil(n_trials / 4096), ceil(4 * SMs / n_layers)) blocks per
- * layer; a call that needs more returns ART_EINVAL and enqueues nothing
- * (in practice, n_layers * n_p above about 1000).
+ * with b = min(ceil(n_trials / 4096), ceil(c * SMs / n_layers)) blocks per
+ * layer, c = 8 when the YLT is larger than the device's L2 and 4 otherwise;
+ * a call that needs more returns ART_EINVAL and enqueues nothing (in
+ * practice, n_layers * n_p above about 1000).
  *
  * The first call on each device looks up that device's address of the
  * scratch array (cudaGetSymbolAddress, with the device current); make that
