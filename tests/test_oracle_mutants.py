@@ -63,3 +63,39 @@ def test_pins_catch_planted_mistake(name):
         assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
     finally:
         shutil.rmtree(d, ignore_errors=True)
+
+
+# The exact transcription (oracle/literal.py) is a pin itself: planted
+# mistakes in it must fail the worked example or the brute-force comparison
+# with the C oracle.
+LIT = os.path.join(ROOT, "oracle", "literal.py")
+LIT_MUTANTS = {
+    "no_elt_accumulation": ("lo = [lo[d] + l[d] for d in range(k)]", "lo = [l[d] for d in range(k)]"),
+    "occurrence_limit_dropped": ("lo = [_xl(v, Fraction(occ_r), occ_l) for v in lo]",
+                                 "lo = [_xl(v, Fraction(occ_r), None) for v in lo]"),
+    "first_payout": ("(capped[d - 1] if d else Fraction(0))", "(capped[d - 1] if d else capped[0])"),
+    "multiplier_dropped": ("_xl(Fraction(m) * xd,", "_xl(xd,"),
+    "cumulative_restarts": ("run += v", "run = v"),
+    "deductible_sign": ("w = v - ret", "w = v + ret"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LIT_MUTANTS))
+def test_pins_catch_planted_mistake_in_the_transcription(name, monkeypatch):
+    import types
+
+    import test_oracle_pins as pins
+    old, new = LIT_MUTANTS[name]
+    src = open(LIT).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mod = types.ModuleType("literal_mutant")
+    exec(compile(src.replace(old, new, 1), "literal_mutant", "exec"), mod.__dict__)
+    monkeypatch.setattr(pins, "algorithm1_trial", mod.algorithm1_trial)
+    caught = []
+    for pin in (pins.test_worked_example_literal_transcription, pins.test_brute_force_against_exact_transcription):
+        try:
+            pin()
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught the transcription mutant {name}"
+
