@@ -164,23 +164,35 @@ ART_API art_status art_create_portfolio(int32_t catalogue_size, int32_t n_elt, c
                                 cudaStream_t stream, art_portfolio** out);
 
 /* Replace the terms without rebuilding tables (pricing loops, finite
- * differences). Any pointer may be NULL to keep those terms. Same validation
- * and rounding as art_create_portfolio. Takes effect for calls enqueued
- * afterwards on any stream; the caller orders it against calls in flight. */
+ * differences). The terms are those of Section II: per ELT the financial
+ * terms (multiplier, deductible, limit), per layer the occurrence and
+ * aggregate retentions and limits. Any pointer may be NULL to keep those
+ * terms. Same validation and rounding as art_create_portfolio. Takes effect
+ * for calls enqueued afterwards on any stream; the caller orders it against
+ * calls in flight. Errors: ART_EINVAL (NULL portfolio or invalid terms;
+ * nothing changes), ART_ECUDA (the device copy could not be refreshed;
+ * destroy the portfolio). */
 ART_API art_status art_update_terms(art_portfolio* p, const float* elt_mult_host, const float* elt_ded_host,
                             const float* elt_lim_host, const art_layer_terms* terms_host);
 
-/* Read back the terms as the kernels apply them (after FP32 rounding).
- * Any pointer may be NULL. */
+/* Read back the Section II terms as the kernels apply them (after FP32
+ * rounding): elt_* [n_elt], terms_host [n_layers], caller-owned host
+ * arrays. Any pointer may be NULL. Errors: ART_EINVAL (NULL portfolio). */
 ART_API art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* elt_ded_host,
                          float* elt_lim_host, art_layer_terms* terms_host);
 
-/* Replace the portfolio's ART_FLAG_* flags (ART_FLAG_L2_PERSIST takes effect
- * only if it was set at creation, which reserves the persisting L2 area). */
+/* Replace the portfolio's ART_FLAG_* flags (execution options with no
+ * counterpart in the paper; ART_FLAG_L2_PERSIST takes effect only if it was
+ * set at creation, which reserves the persisting L2 area). Drops a captured
+ * graph. Errors: ART_EINVAL (NULL portfolio or an unknown flag bit). */
 ART_API art_status art_set_flags(art_portfolio* p, int32_t flags);
 
-/* Select the kernel variant (ART_VARIANT_*) and batched tile shape; 0 keeps
- * the current value of a tile parameter. */
+/* Select the kernel variant (ART_VARIANT_*; every variant computes
+ * Algorithm 1 of Section II) and the batched tile shape; 0 keeps the
+ * current value of a tile parameter. Drops a captured graph. Errors:
+ * ART_EINVAL (NULL portfolio, unknown variant, negative tile, CTA size not a
+ * multiple of 32 or above 1024), ART_EUNSUPPORTED (the variant's layout was
+ * not built). */
 ART_API art_status art_set_variant(art_portfolio* p, int32_t variant, int32_t trial_tile, int32_t cta_threads);
 
 /*
@@ -223,6 +235,11 @@ ART_API art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t
  * owns the staging buffers (grown on demand, freed with the portfolio).
  * Blocks until the result is in ylt_host. Dense YETs only (trial_off NULL)
  * or CSR with host offsets. Pinned host memory gives full copy bandwidth.
+ * The chunks stand for the paper's chunked reads of the YET (Section III);
+ * the result is that of art_run_ylt (Algorithm 1, Section II). Host offsets
+ * are checked on the host (off[0] = 0, non-decreasing) before any copy.
+ * Errors: ART_EINVAL, ART_EUNSUPPORTED, ART_ECUDA (including a failed
+ * staging allocation).
  */
 ART_API art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
                             const int64_t* trial_off_host, int32_t events_per_trial,
@@ -308,7 +325,8 @@ ART_API art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trials, 
 
 /*
  * art_metrics_backward -- gradient of sum_j (gm_j mean_j + sum_q gt_{j,q}
- * TVaR_{j,q}) with respect to the YLT: grad_ylt[j][t] = gm_j / T
+ * TVaR_{j,q}) with respect to the YLT (the paper has no gradients; the
+ * metrics are those of Section I, read as in art_metrics): grad_ylt[j][t] = gm_j / T
  * + sum_q gt_{j,q} w_{j,q}(t), where w = 1/k for Y > PML, (k - #greater) /
  * (k #equal) for Y == PML (ties share the boundary weight), 0 below.
  *  ylt_dev, n_trials, n_layers: as art_metrics; probs_host and n_p (0 <= n_p
@@ -385,7 +403,10 @@ typedef struct {
  * variable ART_AUTOTUNE_CACHE names a file, a shape recorded there for the
  * same device, portfolio shape and YET shape (trials bucketed by powers of
  * two) is applied without timing, and a newly timed shape is appended.
- * Synchronises the stream. Not for use during stream capture.
+ * Synchronises the stream. Not for use during stream capture. The paper
+ * picks its threads per block by measurement too (Section IV); this widens
+ * that to the variants and tile shapes here. Errors: ART_EINVAL,
+ * ART_EUNSUPPORTED (no variant's layout was built), ART_ECUDA.
  */
 ART_API art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_dev,
                                 const int64_t* trial_off_dev, int32_t events_per_trial, double* ylt_dev,
@@ -393,20 +414,28 @@ ART_API art_status art_autotune(art_portfolio* p, int64_t n_trials, const int32_
 
 /* Synchronise the stream, then read and clear the portfolio's device error
  * flags: ART_OK, ART_EID_RANGE (an id outside [0, C) was seen; it counted as
- * zero loss) or ART_EINVAL (decreasing CSR offsets were seen). */
+ * zero loss: event ids index the direct-access tables of Section III) or
+ * ART_EINVAL (decreasing CSR offsets were seen). Errors of the call itself:
+ * ART_EINVAL (NULL portfolio), ART_ECUDA. */
 ART_API art_status art_get_device_status(art_portfolio* p, cudaStream_t stream);
 
-/* Bytes of device memory the portfolio holds, per layout (NULL to skip). */
+/* Bytes of device memory the portfolio holds, per layout (the direct-access
+ * tables of Section III and their derived forms; NULL to skip). Errors:
+ * ART_EINVAL (NULL portfolio). */
 ART_API art_status art_get_footprint(const art_portfolio* p, int64_t* layer_bytes, int64_t* pool_bytes,
                                      int64_t* pool64_bytes, int64_t* group_bytes, int64_t* sparse_bytes);
 
-/* Free the portfolio (synchronises the device first). NULL is a no-op. */
+/* Free the portfolio and every buffer it owns (synchronises the device
+ * first). NULL is a no-op. No counterpart in the paper; never fails. */
 ART_API void art_destroy_portfolio(art_portfolio* p);
 
-/* Static, human-readable name of a status. */
+/* Static, human-readable name of a status (an unknown code gets a generic
+ * name). No counterpart in the paper; never fails. */
 ART_API const char* art_status_string(art_status s);
 
-/* Text of the last CUDA error this thread saw inside the library. */
+/* Text of the last CUDA error this thread saw inside the library (empty
+ * before any; the pointer stays valid until this thread's next library call
+ * that records an error). No counterpart in the paper; never fails. */
 ART_API const char* art_last_cuda_error(void);
 
 /* Probe kinds for art_probe. */
@@ -430,7 +459,8 @@ enum {
  */
 ART_API art_status art_probe(int32_t kind, int64_t bytes, int32_t reps, double* result);
 
-/* Library version, major * 10000 + minor * 100 + patch. */
+/* Library version, major * 10000 + minor * 100 + patch. No counterpart in
+ * the paper; never fails. */
 ART_API int32_t art_version(void);
 
 #ifdef __cplusplus

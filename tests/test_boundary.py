@@ -32,6 +32,19 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+def test_every_entry_point_is_documented():
+    """Each declaration in include/art.h follows a comment that cites the
+    paper's passage (or says the paper has no counterpart) and states the
+    errors it returns (or that it never fails)."""
+    src = open(os.path.join(ROOT, "include", "art.h")).read()
+    for m in re.finditer(r"ART_API\s+[\w\s\*]+?\b(art_\w+)\s*\(", src):
+        before = src[:m.start()]
+        end = before.rfind("*/")
+        block = before[before.rfind("/*", 0, end):end]
+        assert re.search(r"Section|Algorithm|paper", block), m.group(1)
+        assert re.search(r"Errors|ART_E|never fails|no-op", block), m.group(1)
+
+
 def test_library_exports_every_declared_symbol(art):
     L = art.lib()
     names = declared_entry_points()
