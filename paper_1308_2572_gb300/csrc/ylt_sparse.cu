@@ -409,6 +409,10 @@ cudaError_t build_sparse(art_portfolio* p, const float* src, cudaStream_t s) {
     const unsigned grid = (unsigned)((C + 255) / 256);
     sparse_count_kernel<<<grid, 256, 0, s>>>(src, C, p->n_elt, cnt);
     sparse_scan_kernel<<<1, 1024, 0, s>>>(cnt, C, p->sp_ptr);
+    if ((e = cudaGetLastError())) {
+        cudaFree(cnt);
+        return e;
+    }
     uint32_t total = 0;
     e = cudaMemcpyAsync(&total, p->sp_ptr + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
