@@ -7,6 +7,13 @@ branch of every (layer, trial)), art_metrics. Backward: art_metrics_backward
 (dLoss/dYLT), then art_run_ylt_backward (the adjoint kernel, which re-reads
 only trials on the middle aggregate branch). Terms are host-side FP64 tensors;
 FP32 rounding of OccR, OccL and the ELT terms happens in the library.
+
+The portfolio holds one set of terms, and the adjoint differentiates at the
+terms the portfolio holds when it runs. Each forward therefore records the
+terms it applied (as rounded by the library), and its backward re-applies
+them when the portfolio has moved on -- another forward in between, a
+finite-difference evaluation, a second scenario -- runs the adjoint, waits
+for it and puts the portfolio's terms back as it found them.
 """
 from __future__ import annotations
 
@@ -14,6 +21,10 @@ import numpy as np
 import torch
 
 from . import art
+
+
+def _same_terms(a, b) -> bool:
+    return all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
 class ARAFunction(torch.autograd.Function):
@@ -35,6 +46,8 @@ class ARAFunction(torch.autograd.Function):
         tvar = torch.empty((L, n_p), dtype=torch.float64, device=dev)
         art.art_metrics(ylt, n_trials, L, probs, mean, pml, tvar)
         ctx.portfolio, ctx.yet, ctx.probs = portfolio, yet, np.asarray(probs, dtype=np.float64)
+        # the terms as the kernels applied them (after FP32 rounding)
+        ctx.terms_applied = art.art_get_terms(portfolio)
         ctx.save_for_backward(ylt, branch, pml)
         return mean.cpu(), tvar.cpu()
 
@@ -51,7 +64,22 @@ class ARAFunction(torch.autograd.Function):
         art.art_metrics_backward(ylt, n_trials, L, ctx.probs, pml, gm, gt, grad_ylt)
         grad_terms = torch.empty((L, 4), dtype=torch.float64, device=dev)
         grad_mult = torch.empty(p.n_elt, dtype=torch.float64, device=dev)
-        art.art_run_ylt_backward(p, n_trials, ids, off, k, branch, grad_ylt, grad_terms, grad_mult)
+        current = art.art_get_terms(p)
+        moved = not _same_terms(current, ctx.terms_applied)
+        if moved:
+            # work already queued may still read the portfolio's terms
+            torch.cuda.current_stream(dev).synchronize()
+            m, d, l, t = ctx.terms_applied
+            art.art_update_terms(p, elt_mult=m, elt_ded=d, elt_lim=l, terms=t)
+        try:
+            art.art_run_ylt_backward(p, n_trials, ids, off, k, branch, grad_ylt, grad_terms, grad_mult)
+        finally:
+            if moved:
+                # the adjoint reads the terms while it runs: wait for it before
+                # giving the portfolio its terms back
+                torch.cuda.current_stream(dev).synchronize()
+                m, d, l, t = current
+                art.art_update_terms(p, elt_mult=m, elt_ded=d, elt_lim=l, terms=t)
         gtc = grad_terms.cpu()
         return (None, None, None, gtc[:, 0], gtc[:, 1], gtc[:, 2], gtc[:, 3], grad_mult.cpu())
 

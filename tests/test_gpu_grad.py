@@ -171,6 +171,38 @@ def test_autograd_function(c3):
     np.testing.assert_allclose(mult.grad.numpy(), gm, rtol=1e-12, atol=0)
 
 
+def test_autograd_backward_uses_its_own_forward_terms(c3):
+    """forward(A), forward(B), backward of A: the gradient is A's (against the
+    oracle's analytic gradient at A's terms), and the portfolio keeps B's terms."""
+    w, p, yet = c3
+    L, E = w.portfolio.n_layers, w.portfolio.n_elt
+    art.art_set_variant(p, art.ART_VARIANT_PLAIN)
+    m0, _, _, t0 = art.art_get_terms(p)
+    try:
+        pa = [torch.tensor(t0[:, c], dtype=torch.float64, requires_grad=True) for c in range(4)]
+        ma = torch.tensor(m0.astype(np.float64), requires_grad=True)
+        mean_a, tvar_a = layer_metrics(p, yet, [PROB], *pa, ma)
+        # scenario B: other retentions and multipliers, forward only
+        tb = t0.copy()
+        tb[:, 0] *= 1.5
+        tb[:, 2] *= 0.8
+        mb = (m0 * np.float32(1.1)).astype(np.float64)
+        pb = [torch.tensor(tb[:, c], dtype=torch.float64, requires_grad=True) for c in range(4)]
+        layer_metrics(p, yet, [PROB], *pb, torch.tensor(mb, requires_grad=True))
+        after_b = art.art_get_terms(p)
+        (mean_a.sum() + tvar_a.sum()).backward()
+        # the portfolio is left with B's terms
+        assert all(np.array_equal(x, y) for x, y in zip(art.art_get_terms(p), after_b))
+        k = oracle.tail_count(PROB, N_TRIALS)
+        y_ref, _, _ = oracle.ylt(w.oracle_problem())
+        ot, om, _, _ = oracle.grad(w.oracle_problem(), _oracle_weights(y_ref, k))
+        got = np.stack([pa[c].grad.numpy() for c in range(4)], axis=1)
+        np.testing.assert_allclose(got, ot, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(ma.grad.numpy(), om, rtol=1e-6, atol=1e-3)
+    finally:
+        art.art_update_terms(p, elt_mult=m0, terms=t0)
+
+
 def _adjoint(p, yet, br, g, L, n_elt):
     ids, off, K, T = yet
     gt = torch.empty((L, 4), dtype=torch.float64, device="cuda")
