@@ -9,10 +9,13 @@ lognormal(12, 2) losses each (synthetic, seeded).
 
 Metric: trial-events x ELTs per second (sum_t K_t * sum_j |E_j| per step /
 step time), plus ms per 1M-trial YLT and the roofline fraction of the
-forward kernel.
+forward kernel. After the headline line's timed region, the batching (c2),
+differentiation (c3) and precision (c4) workloads are timed too and reported
+in its `workloads` record (--workloads none skips them).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1]
-                  [--variant auto|plain|batched|fp64] [--impl ours|reference]
+                  [--variant auto|plain|batched|fp64|skip|sparse]
+                  [--impl ours|reference] [--workloads c2,c3,c4|none]
 """
 from __future__ import annotations
 
@@ -20,7 +23,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -44,6 +46,8 @@ CONFIG_TEXT = {
     "c3": "c1's YET and 16 ELTs, 8 layers of 8 ELTs; step = forward + EL/TVaR_0.99 + their gradients w.r.t. "
           "OccR, OccL, AggR, AggL and the 16 ELT multipliers (adjoint)",
 }
+VARIANT_KERNEL = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_skip64", "skip": "ylt_skip",
+                  "sparse": "ylt_sparse"}
 
 
 def log(*a):
@@ -93,7 +97,6 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.out = None
 
     def start(self):
         try:
@@ -131,7 +134,8 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"ylt_plain": "ylt_plain.cu", "ylt_skip": "ylt_skip.cu", "ylt_batched": "ylt_batched.cu",
-                  "ylt_skip64": "ylt_skip64.cu", "ylt_sparse": "ylt_sparse.cu"}
+                  "ylt_skip64": "ylt_skip64.cu", "ylt_sparse": "ylt_sparse.cu", "metrics": "metrics.cu",
+                  "adjoint_group": "adjoint_group.cu"}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -143,20 +147,20 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (profiles/<kernel>_<workload>.md lines
-    'dram_bytes_per_launch: N' and 'source_hash: H')."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+def recorded_traffic(kernel: str, workload: str, profiles_dir: str = None):
+    """DRAM bytes per launch from the committed ncu record
+    profiles/<kernel>_<workload>.json ({"source_hash", "dram_bytes_per_launch",
+    ...}), if it was taken on the current kernel sources; else None."""
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), f"{kernel}_{workload}.json")
     try:
-        txt = open(path).read()
-    except OSError:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
-    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != kernel_source_hash(kernel):
+    if rec.get("source_hash") != kernel_source_hash(kernel):
         return None
-    return float(m.group(1))
+    v = rec.get("dram_bytes_per_launch")
+    return float(v) if v is not None else None
 
 
 def layer_groups(port, with_layers: bool = False):
@@ -205,19 +209,35 @@ def occurrence_density(port, layers) -> float:
     return float(hit.sum()) / port.catalogue_size
 
 
-def algorithmic_bytes(w, variant: str):
-    """Bytes one forward launch set moves, three ways.
+def _pad(n: int) -> int:
+    return 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
+
+
+def _sec(nbytes) -> int:
+    return 32 * -(-int(nbytes) // 32)
+
+
+def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6):
+    """What one forward launch set moves and reads, for the roofline.
 
     s8d: the per-unit figure -- 4 B per event id (plus 8 B per CSR offset)
       and the 32-byte sectors every table read touches (32 * ceil(row / 32)
       per row read; 32 B of offsets plus 8 B per entry for the CSR), plus the
-      YLT written; for the skip variant, the rows read are those of the
-      per-call occurrence-loss table, plus its build pass (group table read
-      once, table and bitmap written). The tables here (128 MB to 8 GB) do
-      not fit the 126 MB L2 next to the id stream, so these count against HBM.
-    compulsory: ids, offsets and YLT once, plus every distinct row a pass can
-      touch read once (the least DRAM traffic the pass can have).
-    l2: the id stream plus the sectors the table reads touch (L2 traffic).
+      YLT written; for the skip and all-FP64 variants, the rows read are
+      those of the per-call occurrence-loss tables X, plus their build pass
+      (per-layer tables read once, X and the bitmaps written).
+    compulsory: the least DRAM traffic of the pass -- ids, offsets and YLT
+      once, plus every distinct table row a pass can touch read once (for the
+      skip and all-FP64 variants: the build pass; X is then gathered from L2).
+    l2: the L2 sector traffic -- the id stream, the sectors the table reads
+      touch and the build pass.
+    table_bytes: the largest table the per-event reads gather from (X for the
+      skip and all-FP64 variants: (C + 1) rows of LP entries); l2_resident
+      says whether it fits the L2 (l2_bytes), in which case its gathers are
+      L2 traffic, not DRAM traffic.
+    lookups_performed: table entries the kernels read per launch set (the
+      skip and all-FP64 variants: one per (catalogue event, layer ELT) in the
+      build plus one X row per gathered event; the others: per occurrence).
     """
     port, yet = w.portfolio, w.yet
     n_events = yet.n_events
@@ -225,52 +245,102 @@ def algorithmic_bytes(w, variant: str):
     ylt = 8 * yet.n_trials * port.n_layers
     C = port.catalogue_size
     touched_frac = 1.0 - np.exp(-n_events / C)
-    sec = lambda nbytes: 32 * -(-nbytes // 32)
-    pad = lambda n: 4 if n <= 4 else (8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32)))
+    elts_total = float(port.elts_per_layer().sum())
     if variant in ("skip", "fp64"):
-        # one streamed pass over the per-layer tables that writes each
-        # occurrence group's table X [C][LP] and its bitmap, then per group
-        # and event an id and, where X is non-zero, one sector of X
-        # (the all-FP64 variant: the same with 8-byte entries of X)
+        # one streamed pass over the per-layer tables writes each occurrence
+        # group's table X [C + 1][LP] and its bitmap, then per group and
+        # event an id and, where X is non-zero, one sector of X (the all-FP64
+        # variant: 8-byte entries of X in groups of 4 layers)
         L = port.n_layers
-        per = 4 if variant == "fp64" else 8  # layers per occurrence group (FP64 tables: 4)
+        per = 4 if variant == "fp64" else 8
         lp = 1 if L <= 1 else (2 if L <= 2 else (4 if (L <= 4 or per == 4) else 8))
         xb = 8 if variant == "fp64" else 4
         groups = occurrence_groups(port, per)
         dens = [occurrence_density(port, lays) for lays in groups]
-        reads = sum(n_events * d * sec(xb * lp) for d in dens)
-        build = float(sum(4 * pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (C * xb * lp + C / 8)
+        gathered = sum(n_events * d for d in dens)
+        reads = sum(n_events * d * _sec(xb * lp) for d in dens)
+        build = float(sum(4 * _pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (
+            (C + 1) * xb * lp + C / 8)
         n_groups = len(groups)
+        table = float((C + 1) * xb * lp)
         # FP64 operations of the all-FP64 variant: its CSR build costs an FMA
         # per non-zero loss and an add per (loss, layer holding it); the trial
         # pass an add per slot of every queued event
         nnz = float((port.elt_losses != 0).sum())
-        flops = 2.0 * nnz + nnz * float(port.elts_per_layer().sum()) / port.n_elt + sum(n_events * d * lp for d in dens)
+        flops = 2.0 * nnz + nnz * elts_total / port.n_elt + sum(n_events * d * lp for d in dens)
         out = {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
-               "l2": n_groups * ids + build + reads}
+               "l2": n_groups * ids + build + reads, "table_bytes": table, "l2_resident": table <= l2_bytes,
+               "lookups_performed": C * elts_total + gathered}
         if variant == "fp64":
             out["fp64_flops"] = flops
         return out
     if variant == "sparse":
-        nnz_per_event = float((port.elt_losses != 0).sum(axis=0).mean())
-        csr = 4 * (C + 1) + 8 * float((port.elt_losses != 0).sum())
+        nnz = float((port.elt_losses != 0).sum())
+        nnz_per_event = nnz / C
+        csr = 4 * (C + 1) + 8 * nnz
         reads = n_events * (32 + 8 * nnz_per_event)
-        return {"s8d": ids + ylt + reads, "compulsory": ids + ylt + csr * touched_frac, "l2": ids + reads}
+        return {"s8d": ids + ylt + reads, "compulsory": ids + ylt + csr * touched_frac, "l2": ids + reads,
+                "table_bytes": csr, "l2_resident": csr <= l2_bytes, "lookups_performed": n_events * nnz_per_event}
     if variant == "plain":
-        rows = [4 * pad(int(n)) for n in port.elts_per_layer()]
-        reads = float(sum(sec(r) for r in rows)) * n_events
+        rows = [4 * _pad(int(n)) for n in port.elts_per_layer()]
+        reads = float(sum(_sec(r) for r in rows)) * n_events
         table = float(sum(rows)) * C
         n_launch = port.n_layers
+        looked = n_events * elts_total
+        biggest = float(max(rows)) * C
     else:
         epl = 1
         while 32 * epl < port.n_elt:
             epl *= 2
         rowb = 32 * epl * (8 if variant == "fp64" else 4)
-        reads = float(sec(rowb)) * n_events
-        table = float(rowb) * C
+        reads = float(_sec(rowb)) * n_events
+        table = biggest = float(rowb) * C
         n_launch = 1
+        looked = n_events * 32.0 * epl
     return {"s8d": n_launch * ids + ylt + reads, "compulsory": n_launch * ids + ylt + table * touched_frac,
-            "l2": n_launch * ids + reads}
+            "l2": n_launch * ids + reads, "table_bytes": biggest, "l2_resident": biggest <= l2_bytes,
+            "lookups_performed": looked}
+
+
+def roofline(ab: dict, secs: float, hbm_gbs: float, l2_gbs=None, fp64_gflops=None) -> dict:
+    """The bound a forward launch set runs against, from its accounting (see
+    algorithmic_bytes) and its measured time.
+
+    A gathered table that fits L2 (the skip variant's occurrence tables):
+    t* = max(compulsory DRAM bytes / HBM peak, L2 sector bytes / probed L2
+    gather rate); the larger term names the bound ("hbm" or "l2") and gives
+    achieved and peak, so frac = achieved / peak = t* / t. Without the L2
+    probe that case falls back to the DRAM term. A table larger than L2:
+    every sector read counts as DRAM traffic ("hbm", the per-unit bytes). The
+    all-FP64 variant, given the probed FP64 add rate: "alu". Beside the bound
+    the line keeps the HBM fraction by the compulsory DRAM bytes alone.
+    """
+    gb = lambda b: b / secs / 1e9
+    out = {"hbm_frac_by_dram_bytes": gb(ab["compulsory"]) / hbm_gbs,
+           "algorithmic_bytes_per_launch": ab["s8d"], "compulsory_bytes_per_launch": ab["compulsory"],
+           "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": gb(ab["l2"]),
+           "gathered_table_bytes": ab["table_bytes"], "gathered_table_fits_l2": bool(ab["l2_resident"])}
+    if "fp64_flops" in ab and fp64_gflops:
+        a = ab["fp64_flops"] / secs / 1e9
+        out.update(bound="alu", achieved=a, peak=fp64_gflops, unit="GFLOP/s", frac=a / fp64_gflops,
+                   peak_source="probed FP64 add rate (art_probe)", hbm_achieved_gbs=gb(ab["s8d"]))
+        return out
+    if ab["l2_resident"]:
+        t_dram = ab["compulsory"] / (hbm_gbs * 1e9)
+        t_l2 = ab["l2"] / (l2_gbs * 1e9) if l2_gbs else 0.0
+        out["t_star_ms"] = max(t_dram, t_l2) * 1e3
+        if t_l2 > t_dram:
+            out.update(bound="l2", achieved=gb(ab["l2"]), peak=l2_gbs, unit="GB/s",
+                       peak_source="probed random 32-byte L2 gather rate (art_probe)")
+        else:
+            out.update(bound="hbm", achieved=gb(ab["compulsory"]), peak=hbm_gbs, unit="GB/s",
+                       peak_source="hbm_gbs (copy bandwidth)")
+    else:
+        out.update(bound="hbm", achieved=gb(ab["s8d"]), peak=hbm_gbs, unit="GB/s",
+                   peak_source="hbm_gbs (copy bandwidth)")
+        out["t_star_ms"] = ab["s8d"] / (hbm_gbs * 1e9) * 1e3
+    out["frac"] = out["achieved"] / out["peak"]
+    return out
 
 
 def run_reference(args):
@@ -311,7 +381,6 @@ def run_reference(args):
 def cpu_baseline(args, w_full):
     """Oracle timed on the host cores on a bounded sample (about 10-20 s)."""
     import oracle
-    from paper_1308_2572_gb300 import workloads
     T = w_full.yet.n_trials
     probe = min(T, 500)
     trials = np.arange(probe, dtype=np.int64)
@@ -329,6 +398,169 @@ def cpu_baseline(args, w_full):
             "kind": "oracle", "sample": f"YLT of the first {n} of {T} trials, all layers ({dt:.1f} s)"}
 
 
+def time_forward(art, torch, p, T, ids, off, K, ylt, stream, reps: int, warm: int = 1) -> float:
+    """Mean forward ms over `reps` launches after `warm` untimed ones."""
+    for _ in range(warm):
+        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def link_probe(torch, src, dev, nbytes: int, reps: int = 8) -> dict:
+    """The host-to-device link on its own: `reps` back-to-back copies of the
+    host-run path's chunk size from the same pinned buffer, each timed with
+    events; median and the whole run's rate."""
+    n = min(src.numel(), nbytes // src.element_size())
+    dst = torch.empty(n, dtype=src.dtype, device=dev)
+    dst.copy_(src[:n], non_blocking=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record()
+    for i in range(reps):
+        dst.copy_(src[:n], non_blocking=True)
+        ev[i + 1].record()
+    torch.cuda.synchronize(dev)
+    each = [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]
+    b = n * src.element_size()
+    out = {"copy_bytes": b, "copies": reps, "median_gbs": b / (statistics.median(each) * 1e-3) / 1e9,
+           "run_gbs": reps * b / (ev[0].elapsed_time(ev[reps]) * 1e-3) / 1e9}
+    del dst
+    return out
+
+
+VMAP_NAMES = ("plain", "batched", "fp64", "skip", "sparse")
+
+
+def extra_workload(name: str, dev, probes: dict, hbm: float, l2_size: float) -> dict:
+    """One of the batching (c2), differentiation (c3) or precision (c4)
+    workloads at full size, after the headline's timed region: forward time
+    of each variant, the autotuned choice and its roofline; for c3 the whole
+    step with the adjoint; for c4 the all-FP64 variant and the mixed
+    variant's error against it."""
+    import torch
+    from paper_1308_2572_gb300 import art, workloads
+    vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64,
+            "skip": art.ART_VARIANT_SKIP, "sparse": art.ART_VARIANT_SPARSE}
+    t_gen = time.perf_counter()
+    w = workloads.make(name)
+    port, yet = w.portfolio, w.yet
+    L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
+    layouts = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_SPARSE
+    if name == "c3":
+        layouts |= art.ART_LAYOUT_GROUP
+    if name == "c4":
+        layouts |= art.ART_LAYOUT_OCC64
+    p = art.portfolio_from_workload(w, device=dev, layouts=layouts)
+    ids = torch.from_numpy(yet.event_ids).to(dev)
+    off = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).to(dev)
+    ylt = torch.empty((L, T), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rec = {"description": CONFIG_TEXT.get(name, ""), "layers": L, "trials": T, "events": yet.n_events,
+           "lookups_per_step": w.lookups(), "setup_s": round(time.perf_counter() - t_gen, 1)}
+    try:
+        fwd = {}
+        for v in ("skip", "sparse", "batched", "plain"):
+            art.art_set_variant(p, vmap[v])
+            slow = v == "plain"
+            fwd[v] = time_forward(art, torch, p, T, ids, off, K, ylt, stream, reps=1 if slow else 3)
+        rec["forward_ms_by_variant_default_shapes"] = fwd
+        tune = art.art_autotune(p, T, ids, off, K, ylt, sample_trials=min(T, 65536), stream=stream)
+        inv = {v: k for k, v in vmap.items()}
+        chosen = inv.get(tune["variant"], "skip")
+        ms = time_forward(art, torch, p, T, ids, off, K, ylt, stream, reps=5)
+        rec.update(variant=chosen, autotune=tune, forward_ms=ms, ms_per_1M_trial_ylt=ms * 1e6 / T,
+                   trial_events_elts_per_s=w.lookups() / (ms * 1e-3),
+                   vs_plain_one_layer_per_launch=fwd["plain"] / ms)
+        ab = algorithmic_bytes(w, chosen, l2_size)
+        roof = roofline(ab, ms * 1e-3, hbm, probes.get("l2_gather32_gbs"),
+                        probes.get("fp64_add_gflops") if chosen == "fp64" else None)
+        roof.update(kernel=VARIANT_KERNEL[chosen], traffic=recorded_traffic(VARIANT_KERNEL[chosen], name))
+        rec["roofline"] = roof
+        rec["lookups_performed_per_step"] = ab["lookups_performed"]
+        probs = list(w.probs)
+        n_p = len(probs)
+        mean = torch.empty(L, dtype=torch.float64, device=dev)
+        pml = torch.empty((L, n_p), dtype=torch.float64, device=dev)
+        tvar = torch.empty((L, n_p), dtype=torch.float64, device=dev)
+        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        for _ in range(5):
+            art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+        e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        rec["metrics_ms"] = e[0].elapsed_time(e[1]) / 5
+        if name == "c3":
+            art.art_set_variant(p, vmap[chosen])
+            branch = torch.empty((L, T), dtype=torch.uint8, device=dev)
+            gylt = torch.empty_like(ylt)
+            ones_l = torch.ones(L, dtype=torch.float64, device=dev)
+            ones_lp = torch.ones((L, n_p), dtype=torch.float64, device=dev)
+            gterms = torch.empty((L, 4), dtype=torch.float64, device=dev)
+            gmult = torch.empty(port.n_elt, dtype=torch.float64, device=dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            parts = {"forward": [], "metrics": [], "metrics_backward": [], "adjoint": []}
+            for i in range(8):
+                ev[0].record(stream)
+                art.art_run_ylt(p, T, ids, off, K, ylt, branch, stream)
+                ev[1].record(stream)
+                art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+                ev[2].record(stream)
+                art.art_metrics_backward(ylt, T, L, probs, pml, ones_l, ones_lp, gylt, stream)
+                ev[3].record(stream)
+                art.art_run_ylt_backward(p, T, ids, off, K, branch, gylt, gterms, gmult, stream)
+                ev[4].record(stream)
+                torch.cuda.synchronize(dev)
+                if i >= 3:
+                    for k, n in enumerate(parts):
+                        parts[n].append(ev[k].elapsed_time(ev[k + 1]))
+            rec["step_with_gradients_ms"] = float(np.mean([sum(x) for x in zip(*parts.values())]))
+            rec["step_parts_ms"] = {k: float(np.mean(v)) for k, v in parts.items()}
+            rec["gradients"] = "d(EL_j + TVaR_0.99,j)/d(OccR, OccL, AggR, AggL) per layer and d/d(m_e) per ELT"
+        if name == "c4":
+            # the all-FP64 variant and the mixed one's error against it (the
+            # all-FP64 variant equals the FP64 oracle: tests/test_gpu_precision.py)
+            art.art_set_variant(p, art.ART_VARIANT_FP64)
+            y64 = torch.empty_like(ylt)
+            rec["fp64_forward_ms"] = time_forward(art, torch, p, T, ids, off, K, y64, stream, reps=2)
+            art.art_set_variant(p, vmap[chosen])
+            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
+            # the gross loss G per (layer, trial): the all-FP64 forward with
+            # identity terms (no deductible, limit, retention or cap)
+            m0, d0, l0, t0 = art.art_get_terms(p)
+            ident = np.tile(np.array([0.0, np.inf, 0.0, np.inf]), (L, 1))
+            gross = torch.empty_like(ylt)
+            try:
+                art.art_update_terms(p, elt_ded=np.zeros_like(d0), elt_lim=np.full_like(l0, np.inf), terms=ident)
+                art.art_set_variant(p, art.ART_VARIANT_FP64)
+                art.art_run_ylt(p, T, ids, off, K, gross, None, stream)
+                torch.cuda.synchronize(dev)
+            finally:
+                art.art_update_terms(p, elt_mult=m0, elt_ded=d0, elt_lim=l0, terms=t0)
+            rel = (ylt - y64).abs() / torch.where(gross > 0, gross, torch.ones_like(gross))
+            m64, p64, t64 = (torch.empty_like(mean), torch.empty_like(pml), torch.empty_like(tvar))
+            art.art_metrics(y64, T, L, probs, m64, p64, t64, stream)
+            art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+            torch.cuda.synchronize(dev)
+            relerr = lambda a, b: float(((a - b).abs() / b.abs().clamp_min(1e-300)).max())
+            rec["precision_vs_all_fp64"] = {
+                "trials": T, "max_abs_dy_over_gross": float(rel.max()),
+                "pml_rel_err_by_prob": {str(pr): relerr(pml[:, q], p64[:, q]) for q, pr in enumerate(probs)},
+                "tvar_rel_err_by_prob": {str(pr): relerr(tvar[:, q], t64[:, q]) for q, pr in enumerate(probs)},
+                "mean_rel_err": relerr(mean, m64),
+                "note": f"mixed ({chosen}) against the all-FP64 GPU variant on every (layer, trial)"}
+            del y64, gross, rel
+    finally:
+        p.close()
+        del ylt, ids, off
+        torch.cuda.empty_cache()
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,6 +574,8 @@ def main():
     ap.add_argument("--ref-trials", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probes", action="store_true", help="skip the libart bandwidth probes")
+    ap.add_argument("--workloads", default="c2,c3,c4",
+                    help="further workloads timed after the headline (comma list, or none)")
     ap.add_argument("--graph", action="store_true",
                     help="ART_FLAG_GRAPH: the forward's launches replay from a captured CUDA graph")
     ap.add_argument("--l2-persist", action="store_true",
@@ -363,6 +597,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    l2_size = float(torch.cuda.get_device_properties(dev).L2_cache_size)
 
     t_gen = time.perf_counter()
     w = workloads.make(args.config, n_trials=args.trials or None)
@@ -412,15 +647,7 @@ def main():
     fwd_ms = {}
     for v in cands:
         art.art_set_variant(p, vmap[v])
-        for _ in range(2):
-            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(3):
-            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        fwd_ms[v] = e0.elapsed_time(e1) / 3
+        fwd_ms[v] = time_forward(art, torch, p, T, ids, off, K, ylt, stream, reps=3, warm=2)
     variant = min(fwd_ms, key=fwd_ms.get)
     tune = None
     if args.variant == "auto":
@@ -467,11 +694,6 @@ def main():
     value = whole_job_rate(lookups * args.steps, world, total_ms / 1e3)
     fwd_mean = float(np.mean(fwd))
 
-    # roofline of the dominant kernel (the forward)
-    peak, peak_kind = measured_peaks()
-    ab = algorithmic_bytes(w, variant)
-    secs = fwd_mean / 1e3
-    achieved = ab["s8d"] / secs / 1e9
     # measured limits the copy-bandwidth and GEMM peaks do not cover (libart probes)
     probes = {}
     if rank == 0 and not args.no_probes:
@@ -480,39 +702,35 @@ def main():
                   "dram_gather32_gbs": art.art_probe(art.ART_PROBE_GATHER32, 8 << 30, 3),
                   "stream_read_gbs": art.art_probe(art.ART_PROBE_STREAM, 8 << 30, 3),
                   "fp64_add_gflops": art.art_probe(art.ART_PROBE_FP64ADD, 0, 3)}
-    kernel_name = {"plain": "ylt_plain", "batched": "ylt_batched", "fp64": "ylt_skip64", "skip": "ylt_skip",
-                   "sparse": "ylt_sparse"}[variant]
-    traffic = recorded_traffic(kernel_name, args.config)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "kernel": kernel_name,
-            "algorithmic_bytes_per_launch": ab["s8d"],
-            "compulsory_bytes_per_launch": ab["compulsory"], "compulsory_gbs": ab["compulsory"] / secs / 1e9,
-            "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": ab["l2"] / secs / 1e9}
+    # roofline of the dominant kernel (the forward)
+    peak, peak_kind = measured_peaks()
+    ab = algorithmic_bytes(w, variant, l2_size)
+    roof = roofline(ab, fwd_mean / 1e3, peak, probes.get("l2_gather32_gbs"),
+                    probes.get("fp64_add_gflops") if variant == "fp64" else None)
+    kernel_name = VARIANT_KERNEL[variant]
+    roof.update(kernel=kernel_name, traffic=recorded_traffic(kernel_name, args.config),
+                hbm_peak_source=f"{peak_kind} hbm_gbs {peak} GB/s (copy bandwidth)")
     if probes:
-        roof["l2_gather_peak_gbs"] = probes["l2_gather32_gbs"]
-        roof["l2_frac"] = roof["l2_sector_gbs"] / probes["l2_gather32_gbs"]
         roof["probes"] = probes
-    if "fp64_flops" in ab:
-        # the all-FP64 variant is bound by the FP64 pipe: against the probed
-        # FP64 add rate when the probes ran
-        fp64 = ab["fp64_flops"] / secs / 1e9
-        roof["fp64_gflops"] = fp64
-        if probes:
-            roof.update({"bound": "alu", "achieved": fp64, "peak": probes["fp64_add_gflops"], "unit": "GFLOP/s",
-                         "frac": fp64 / probes["fp64_add_gflops"],
-                         "peak_source": "probed FP64 add rate (art_probe), not in MEASURED_PEAKS.json",
-                         "hbm_achieved_gbs": achieved})
 
-    # end to end: host buffers through the C ABI (ids H2D in chunks, YLT D2H),
-    # then the metrics on a device copy of the YLT and their D2H
+    # end to end through the C ABI with host buffers: the pinned YET goes to
+    # the device in chunks, the forward and the metrics run there, the YLT
+    # and the metrics come back
     e2e = None
     if args.e2e_steps > 0:
         ids_h = torch.from_numpy(yet.event_ids).pin_memory()
+        assert ids_h.is_pinned()
         off_h = None if yet.trial_off is None else torch.from_numpy(yet.trial_off).pin_memory()
         ylt_h = torch.empty((L, T), dtype=torch.float64).pin_memory()
-        ylt_d = torch.empty((L, T), dtype=torch.float64, device=dev)
-        out_h = torch.empty((L * (1 + 2 * n_p),), dtype=torch.float64).pin_memory()
-        art.art_run_ylt_host(p, T, ids_h, off_h, K, ylt_h, stream)  # warm staging buffers
+        mean_h = torch.empty(L, dtype=torch.float64).pin_memory()
+        pml_h = torch.empty((L, n_p), dtype=torch.float64).pin_memory()
+        tvar_h = torch.empty((L, n_p), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            art.art_run_ylt_host_metrics(p, T, ids_h, off_h, K, probs, ylt=ylt_h, mean=mean_h, pml=pml_h,
+                                         tvar=tvar_h, stream=stream)
+
+        e2e_step()  # grows the staging and device YLT buffers
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
@@ -520,46 +738,26 @@ def main():
         each = []
         for _ in range(args.e2e_steps):
             t1 = time.perf_counter()
-            art.art_run_ylt_host(p, T, ids_h, off_h, K, ylt_h, stream)
-            ylt_d.copy_(ylt_h, non_blocking=True)
-            art.art_metrics(ylt_d, T, L, probs, mean, pml, tvar, stream)
-            out_h[:L].copy_(mean, non_blocking=True)
-            out_h[L:L + L * n_p].copy_(pml.reshape(-1), non_blocking=True)
-            out_h[L + L * n_p:].copy_(tvar.reshape(-1), non_blocking=True)
-            torch.cuda.synchronize(dev)
+            e2e_step()  # blocks until the results are in host memory
             each.append((time.perf_counter() - t1) * 1e3)
         e2e_s = rank_max((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
-        # the host-to-device link on its own, same pinned buffer, one copy
-        nb = min(ids_h.numel(), 1 << 28)
-        dst = torch.empty(nb, dtype=ids_h.dtype, device=dev)
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        dst.copy_(ids_h[:nb], non_blocking=True)
-        c0.record()
-        dst.copy_(ids_h[:nb], non_blocking=True)
-        c1.record()
-        torch.cuda.synchronize(dev)
-        link_gbs = nb * ids_h.element_size() / (c0.elapsed_time(c1) * 1e-3) / 1e9
-        del dst
-        h2d = yet.event_ids.nbytes + (0 if yet.trial_off is None else yet.trial_off.nbytes) + 8 * L * T
+        # the bytes the step moves: the YET (and offsets) in, the YLT and the metrics out
+        h2d = yet.event_ids.nbytes + (0 if yet.trial_off is None else yet.trial_off.nbytes)
         d2h = 8 * L * T + 8 * L * (1 + 2 * n_p)
-        e2e = {"value": whole_job_rate(lookups, world, e2e_s), "unit": "trial-events*ELTs/s", "ms_per_step": e2e_s * 1e3,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+        link = link_probe(torch, ids_h, dev, 64 << 20)
+        e2e = {"value": whole_job_rate(lookups, world, e2e_s), "unit": "trial-events*ELTs/s",
+               "ms_per_step": e2e_s * 1e3, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_each_step_rank0": [round(t, 3) for t in each],
-               "h2d_copy_gbs_rank0": link_gbs,
-               "path": "art_run_ylt_host (pinned host YET, chunked H2D overlapped with compute) + art_metrics"}
+               "step_h2d_gbs": h2d / e2e_s / 1e9, "h2d_link_rank0": link,
+               "path": "art_run_ylt_host_metrics (pinned host YET in 64 MiB chunks, H2D overlapped with the "
+                       "forward; YLT kept on the device for art_metrics; YLT and metrics copied back)"}
+        del ids_h, ylt_h
 
     # optional early exit (capped trials stop being read), reported separately
     early = None
     if variant == "skip":
         art.art_set_flags(p, art.ART_FLAG_EARLY_EXIT | base_flags)
-        art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(5):
-            art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        early = {"forward_ms": e0.elapsed_time(e1) / 5,
+        early = {"forward_ms": time_forward(art, torch, p, T, ids, off, K, ylt, stream, reps=5),
                  "note": "ART_FLAG_EARLY_EXIT: trials stop being read once capped; not part of value"}
         art.art_set_flags(p, base_flags)
 
@@ -580,24 +778,42 @@ def main():
         # event masks, a pass and its reduction (group tables), else per layer
         # a pass and its reduction plus one scatter
         launches += 3 + (3 * n_groups if layouts & art.ART_LAYOUT_GROUP else 2 * L + 1)
+    config = {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
+              "variant": variant, "autotune": tune, "l2_persist": bool(args.l2_persist), "graph": bool(args.graph),
+              "layers": L, "trials": T, "events": yet.n_events,
+              "lookups_per_step": lookups, "lookups_performed_per_step": ab["lookups_performed"],
+              "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
+              "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"}
+    p.close()
+    del ylt, ids, off
+    torch.cuda.empty_cache()
+
+    extras = {}
+    names = [] if args.workloads in ("", "none") else [n for n in args.workloads.split(",") if n != args.config]
+    if rank == 0 and not args.trials:
+        for name in names:
+            t0 = time.perf_counter()
+            try:
+                extras[name] = extra_workload(name, dev, probes, peak, l2_size)
+            except Exception as ex:  # reported, not fatal: the headline stands on its own
+                extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            extras[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+            log(f"[bench] {name}: {json.dumps(extras[name])[:400]}")
+    if dist:
+        dist.barrier()
+
     if rank == 0:
         line = {
             "metric": "trial-events x ELTs per second", "value": value, "unit": "trial-events*ELTs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
-            "config": {"workload": args.config, "description": CONFIG_TEXT.get(args.config, ""),
-                       "variant": variant, "autotune": tune, "l2_persist": bool(args.l2_persist), "graph": bool(args.graph), "layers": L, "trials": T, "events": yet.n_events,
-                       "lookups_per_step": lookups,
-                       "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
-                       "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"},
+            "data": "synthetic", "config": config,
             "ms_per_1M_trial_ylt": fwd_mean * 1e6 / T,
             "forward_ms": fwd_mean, "forward_ms_by_variant": fwd_ms,
             "roofline": roof, "clocks": clk, "e2e": e2e, "early_exit": early, "gpu_launches": launches * args.steps,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "workloads": extras or None,
         }
         print(json.dumps(line), flush=True)
-    p.close()
     if dist:
         dist.destroy_process_group()
     return 0

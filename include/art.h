@@ -246,6 +246,31 @@ ART_API art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const in
                             double* ylt_host, cudaStream_t stream);
 
 /*
+ * art_run_ylt_host_metrics -- the simulation stage and the financial
+ * functions from host buffers in one call (Section II, Algorithm 1 on a YET
+ * read in chunks as in Section III; Section I, PML and TVaR of the YLT): the
+ * YET goes to the device in chunks as in art_run_ylt_host, the whole YLT is
+ * kept on the device, art_metrics runs on it there, and only the results
+ * come back. The YLT never makes a device-host-device round trip.
+ *  ylt_host      NULL, or [n_layers][T] FP64 host output (the YLT as well).
+ *  probs_host    [n_p] probabilities in (0, 1), 1 <= n_p <= 8.
+ *  mean_host     [n_layers], pml_host and tvar_host [n_layers][n_p]: FP64
+ *                host outputs, each may be NULL.
+ * Limits: those of art_run_ylt_host and of art_metrics (1 <= T <= 2^31 - 1,
+ * n_layers <= 65535). The portfolio owns a device array for the whole YLT
+ * ([n_layers][T] FP64, grown on demand, freed with the portfolio) besides
+ * the staging buffers; the metrics' scratch comes from the stream-ordered
+ * allocator. Blocks until the results are in host memory. Results equal
+ * art_run_ylt followed by art_metrics. Errors: ART_EINVAL, ART_EUNSUPPORTED,
+ * ART_ECUDA (including a failed allocation).
+ */
+ART_API art_status art_run_ylt_host_metrics(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
+                                            const int64_t* trial_off_host, int32_t events_per_trial,
+                                            double* ylt_host, const double* probs_host, int32_t n_p,
+                                            double* mean_host, double* pml_host, double* tvar_host,
+                                            cudaStream_t stream);
+
+/*
  * art_run_payouts -- Algorithm 1's running form for one layer (Section II:
  * the cumulative sum of the occurrence-net losses, the aggregate terms on
  * every cumulative value, the per-event difference, and the trial loss as

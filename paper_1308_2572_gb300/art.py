@@ -27,7 +27,7 @@ EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set
            "art_run_ylt_host", "art_metrics", "art_metrics_backward", "art_run_ylt_backward",
            "art_get_device_status", "art_get_footprint", "art_destroy_portfolio", "art_status_string",
            "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe", "art_autotune",
-           "art_run_payouts", "art_set_flags")
+           "art_run_payouts", "art_set_flags", "art_run_ylt_host_metrics")
 
 
 class LayerTerms(ctypes.Structure):
@@ -77,6 +77,7 @@ def lib():
         "art_set_flags": ([P, i32], st),
         "art_run_ylt": ([P, i64, P, P, i32, P, P, P], st),
         "art_run_ylt_host": ([P, i64, P, P, i32, P, P], st),
+        "art_run_ylt_host_metrics": ([P, i64, P, P, i32, P, P, i32, P, P, P, P], st),
         "art_metrics": ([P, i64, i32, P, i32, P, P, P, P], st),
         "art_metrics_backward": ([P, i64, i32, P, i32, P, P, P, P, P], st),
         "art_metrics_noalloc": ([P, i64, i32, P, i32, P, P, P, P], st),
@@ -231,6 +232,18 @@ def art_run_ylt_host(p, n_trials: int, event_ids, trial_off, events_per_trial: i
     rc = lib().art_run_ylt_host(_h(p), int(n_trials), _hptr(event_ids), _hptr(trial_off), int(events_per_trial),
                                 _hptr(ylt), _stream(stream))
     _check(rc, "art_run_ylt_host")
+
+
+def art_run_ylt_host_metrics(p, n_trials: int, event_ids, trial_off, events_per_trial: int, probs,
+                             ylt=None, mean=None, pml=None, tvar=None, stream=None) -> None:
+    """Host buffers in (the YET) and out (the YLT if given, mean [L], PML and
+    TVaR [L][n_p]; numpy or CPU tensors, pinned for full speed): the YLT stays
+    on the device for the metrics."""
+    pr = np.ascontiguousarray(probs, dtype=np.float64)
+    rc = lib().art_run_ylt_host_metrics(_h(p), int(n_trials), _hptr(event_ids), _hptr(trial_off),
+                                        int(events_per_trial), _hptr(ylt), _hptr(pr), pr.size, _hptr(mean),
+                                        _hptr(pml), _hptr(tvar), _stream(stream))
+    _check(rc, "art_run_ylt_host_metrics")
 
 
 def art_run_payouts(p, layer: int, n_trials: int, event_ids, trial_off, events_per_trial: int, payouts=None,

@@ -507,6 +507,8 @@ void free_portfolio(art_portfolio* p) {
         if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
         if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
     }
+    cudaFree(p->host_ylt);
+    cudaFree(p->host_out);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     delete p;
@@ -827,14 +829,17 @@ art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t* event_
     return e ? fail(e) : ART_OK;
 }
 
-art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
-                            const int64_t* trial_off_host, int32_t events_per_trial, double* ylt_host,
-                            cudaStream_t stream) {
-    if (!p) return ART_EINVAL;
-    art_status st = validate_yet(n_trials, event_ids_host, trial_off_host, events_per_trial);
-    if (st) return st;
-    if (n_trials == 0) return ART_OK;
-    if (!ylt_host) return ART_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// The host-buffer forward: the YET goes to the device in chunks of trials on
+// `stream` (copies on the portfolio's copy stream, double-buffered), each
+// chunk's YLT rows go to ylt_host (if not NULL) and into columns t0.. of the
+// device array ylt_dev ([n_layers][n_trials], if not NULL). Blocks until the
+// last copy is done. Arguments validated by the caller.
+art_status host_run(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host, const int64_t* trial_off_host,
+                    int32_t events_per_trial, double* ylt_host, double* ylt_dev, cudaStream_t stream) {
     if (trial_off_host) {
         if (trial_off_host[0] != 0) return ART_EINVAL;
         for (int64_t t = 0; t < n_trials; ++t)
@@ -914,13 +919,83 @@ art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* e
                   trial_off_host ? 0 : events_per_trial, p->catalogue};
         if (!trial_off_host) y.ids = p->stage_ids[slot];
         if ((e = run_forward(p, variant, y, p->stage_ylt[slot], nullptr, stream, !tables))) break;
-        if ((e = cudaMemcpy2DAsync(ylt_host + t0, sizeof(double) * n_trials, p->stage_ylt[slot], sizeof(double) * nt,
-                                   sizeof(double) * nt, p->n_layers, cudaMemcpyDeviceToHost, stream)))
+        if (ylt_dev && (e = cudaMemcpy2DAsync(ylt_dev + t0, sizeof(double) * n_trials, p->stage_ylt[slot],
+                                              sizeof(double) * nt, sizeof(double) * nt, p->n_layers,
+                                              cudaMemcpyDeviceToDevice, stream)))
+            break;
+        if (ylt_host && (e = cudaMemcpy2DAsync(ylt_host + t0, sizeof(double) * n_trials, p->stage_ylt[slot],
+                                               sizeof(double) * nt, sizeof(double) * nt, p->n_layers,
+                                               cudaMemcpyDeviceToHost, stream)))
             break;
         e = cudaEventRecord(p->ev_done[slot], stream);
     }
     const cudaError_t e2 = cudaStreamSynchronize(stream);
     if (e || e2) return fail(e ? e : e2);
+    return ART_OK;
+}
+
+bool valid_probs(const double* probs, int32_t n_p) {
+    if (!probs || n_p < 1 || n_p > kMaxProbs) return false;
+    for (int q = 0; q < n_p; ++q)
+        if (!(probs[q] > 0.0 && probs[q] < 1.0)) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
+                            const int64_t* trial_off_host, int32_t events_per_trial, double* ylt_host,
+                            cudaStream_t stream) {
+    if (!p) return ART_EINVAL;
+    art_status st = validate_yet(n_trials, event_ids_host, trial_off_host, events_per_trial);
+    if (st) return st;
+    if (n_trials == 0) return ART_OK;
+    if (!ylt_host) return ART_EINVAL;
+    return host_run(p, n_trials, event_ids_host, trial_off_host, events_per_trial, ylt_host, nullptr, stream);
+}
+
+art_status art_run_ylt_host_metrics(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host,
+                                    const int64_t* trial_off_host, int32_t events_per_trial, double* ylt_host,
+                                    const double* probs_host, int32_t n_p, double* mean_host, double* pml_host,
+                                    double* tvar_host, cudaStream_t stream) {
+    if (!p) return ART_EINVAL;
+    art_status st = validate_yet(n_trials, event_ids_host, trial_off_host, events_per_trial);
+    if (st) return st;
+    if (n_trials < 1 || n_trials > 0x7fffffffLL || p->n_layers > 65535 || !valid_probs(probs_host, n_p))
+        return ART_EINVAL;
+    const int64_t L = p->n_layers;
+    const int64_t need_ylt = L * n_trials, need_out = L * (1 + 2 * (int64_t)n_p);
+    cudaError_t e = cudaSuccess;
+    if (need_ylt > p->host_ylt_cap || need_out > p->host_out_cap) {
+        cudaStreamSynchronize(stream);
+        cudaFree(p->host_ylt);
+        cudaFree(p->host_out);
+        p->host_ylt = p->host_out = nullptr;
+        p->host_ylt_cap = p->host_out_cap = 0;
+        if ((e = cudaMalloc(&p->host_ylt, sizeof(double) * need_ylt))) return fail(e);
+        if ((e = cudaMalloc(&p->host_out, sizeof(double) * need_out))) return fail(e);
+        p->host_ylt_cap = need_ylt;
+        p->host_out_cap = need_out;
+    }
+    // chunks of the YET through the forward; the YLT stays on the device too
+    st = host_run(p, n_trials, event_ids_host, trial_off_host, events_per_trial, ylt_host, p->host_ylt, stream);
+    if (st) return st;
+    double* d_mean = p->host_out;
+    double* d_pml = d_mean + L;
+    double* d_tvar = d_pml + L * n_p;
+    if ((e = metrics_run(p->host_ylt, n_trials, (int32_t)L, probs_host, n_p, d_mean, d_pml, d_tvar, stream)))
+        return fail(e);
+    if (mean_host && (e = cudaMemcpyAsync(mean_host, d_mean, sizeof(double) * L, cudaMemcpyDeviceToHost, stream)))
+        return fail(e);
+    if (pml_host &&
+        (e = cudaMemcpyAsync(pml_host, d_pml, sizeof(double) * L * n_p, cudaMemcpyDeviceToHost, stream)))
+        return fail(e);
+    if (tvar_host &&
+        (e = cudaMemcpyAsync(tvar_host, d_tvar, sizeof(double) * L * n_p, cudaMemcpyDeviceToHost, stream)))
+        return fail(e);
+    if ((e = cudaStreamSynchronize(stream))) return fail(e);
     return ART_OK;
 }
 

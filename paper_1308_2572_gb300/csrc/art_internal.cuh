@@ -265,6 +265,10 @@ struct art_portfolio {
     int64_t stage_ids_cap = 0, stage_trials_cap = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+    // host-run path with metrics: the whole YLT and the metric outputs on the device
+    double* host_ylt = nullptr;
+    double* host_out = nullptr;
+    int64_t host_ylt_cap = 0, host_out_cap = 0;
 
     // cached graph of one batched launch
     cudaGraphExec_t graph_exec = nullptr;

@@ -1,10 +1,12 @@
 """bench.py's roofline bookkeeping (no GPU): the grouping it assumes matches
 the library's rules, and each variant is accounted against the right
 bound."""
+import json
 import os
 import sys
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -53,7 +55,60 @@ def test_each_variant_is_accounted_against_its_bound():
     w = workloads.make("c0", n_trials=200)
     for v in ("plain", "skip", "batched", "sparse"):
         ab = bench.algorithmic_bytes(w, v)
-        assert set(ab) == {"s8d", "compulsory", "l2"}, v
+        assert {"s8d", "compulsory", "l2", "table_bytes", "l2_resident", "lookups_performed"} <= set(ab), v
         assert ab["s8d"] >= ab["compulsory"] > 0
     ab = bench.algorithmic_bytes(w, "fp64")
     assert ab["fp64_flops"] > 0  # the all-FP64 variant is bound by the FP64 pipe
+
+
+def test_skip_variant_counts_the_lookups_it_performs():
+    """The memoised forward reads each catalogue event's row once per layer
+    ELT in its build and one row of X per event with an occurrence loss."""
+    w = workloads.make("c0u", n_trials=300)
+    port = w.portfolio
+    ab = bench.algorithmic_bytes(w, "skip")
+    dens = bench.occurrence_density(port, [0])
+    want = port.catalogue_size * int(port.elts_per_layer().sum()) + w.yet.n_events * dens
+    assert ab["lookups_performed"] == want
+    assert ab["lookups_performed"] < w.lookups()  # fewer than one per (occurrence, ELT)
+    assert ab["table_bytes"] == 4 * (port.catalogue_size + 1) and ab["l2_resident"]
+    plain = bench.algorithmic_bytes(w, "plain")
+    assert plain["lookups_performed"] == w.lookups()
+
+
+def test_roofline_of_an_l2_resident_table():
+    """The one-layer paper-scale step as measured: 4.14 GB compulsory DRAM
+    bytes, 7.01 GB of L2 sectors, 1.331 ms; HBM 6769.4 GB/s, probed L2 gather
+    6956 GB/s. t* = max(0.612, 1.008) ms: L2-bound at 0.757, and 0.46 of HBM
+    by the DRAM bytes alone."""
+    ab = {"s8d": 7.02e9, "compulsory": 4.14e9, "l2": 7.01e9, "table_bytes": 8e6, "l2_resident": True}
+    r = bench.roofline(ab, 1.331e-3, 6769.4, 6956.0)
+    assert r["bound"] == "l2" and r["unit"] == "GB/s" and r["peak"] == 6956.0
+    assert r["t_star_ms"] == pytest.approx(max(4.14e9 / 6769.4e9, 7.01e9 / 6956e9) * 1e3)
+    assert r["frac"] == pytest.approx(r["t_star_ms"] / 1.331, rel=1e-12)
+    assert r["frac"] == pytest.approx(0.757, abs=1e-3)
+    assert r["hbm_frac_by_dram_bytes"] == pytest.approx(0.4595, abs=1e-3)
+    assert r["achieved"] / r["peak"] == r["frac"]
+    # a faster DRAM-side case flips the bound to HBM (compulsory bytes)
+    r2 = bench.roofline(dict(ab, l2=1e9), 1.0e-3, 6769.4, 6956.0)
+    assert r2["bound"] == "hbm" and r2["frac"] == pytest.approx(4.14e9 / 1e-3 / 6769.4e9)
+    # no L2 probe: the DRAM term alone
+    assert bench.roofline(ab, 1.331e-3, 6769.4, None)["bound"] == "hbm"
+
+
+def test_roofline_of_a_table_larger_than_l2_and_of_fp64():
+    ab = {"s8d": 68e9, "compulsory": 4.2e9, "l2": 68e9, "table_bytes": 128e6, "l2_resident": False}
+    r = bench.roofline(ab, 11.2e-3, 6769.4, 6956.0)
+    assert r["bound"] == "hbm" and r["frac"] == pytest.approx(68e9 / 11.2e-3 / 6769.4e9)
+    r = bench.roofline(dict(ab, fp64_flops=1e11), 0.69, 6769.4, 6956.0, fp64_gflops=528.0)
+    assert r["bound"] == "alu" and r["unit"] == "GFLOP/s" and r["frac"] == pytest.approx(1e11 / 0.69 / 528e9)
+
+
+def test_traffic_comes_from_a_json_record_of_the_current_sources(tmp_path):
+    rec = {"kernel": "ylt_skip", "workload": "c1", "source_hash": bench.kernel_source_hash("ylt_skip"),
+           "dram_bytes_per_launch": 4.06e9}
+    (tmp_path / "ylt_skip_c1.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("ylt_skip", "c1", str(tmp_path)) == 4.06e9
+    (tmp_path / "ylt_skip_c1.json").write_text(json.dumps(dict(rec, source_hash="0" * 16)))
+    assert bench.recorded_traffic("ylt_skip", "c1", str(tmp_path)) is None  # stale sources
+    assert bench.recorded_traffic("ylt_plain", "c1", str(tmp_path)) is None  # no record

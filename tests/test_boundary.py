@@ -98,6 +98,8 @@ def test_other_entry_points_reject_bad_arguments_on_the_host(art):
     fake = ctypes.c_void_p(16)
     assert L.art_run_ylt(None, 10, fake, None, 5, fake, None, None) == art.ART_EINVAL
     assert L.art_run_ylt_host(None, 10, fake, None, 5, fake, None) == art.ART_EINVAL
+    assert L.art_run_ylt_host_metrics(None, 10, fake, None, 5, None, probs.ctypes.data, 1, None, None, None,
+                                      None) == art.ART_EINVAL
     assert L.art_metrics(None, 10, 1, probs.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
     assert L.art_metrics(fake, 0, 1, probs.ctypes.data, 1, None, None, None, None) == art.ART_EINVAL
     bad = np.array([1.0])

@@ -240,6 +240,40 @@ def test_host_buffers_match_device_path():
                 p.close()
 
 
+def test_host_buffers_with_metrics_match_device_path():
+    """art_run_ylt_host_metrics (YET from host memory, YLT kept on the device
+    for the metrics) gives the bits of art_run_ylt followed by art_metrics,
+    for a dense YET spanning two chunks and a ragged CSR one, with and
+    without the YLT copied back."""
+    cases = (workloads.random_case(206, catalogue=20011, n_elt=12, n_layers=11, n_trials=50000, dense_k=400,
+                                   nnz_frac=0.05),
+             workloads.random_case(207, n_trials=7000, max_len=90))
+    probs = [0.9, 0.99, 0.999]
+    for w in cases:
+        p = art.portfolio_from_workload(w, layouts=ALL_LAYOUTS)
+        try:
+            dev, _ = run_ylt(p, w, art.ART_VARIANT_SKIP)
+            mean, pml, tvar = gpu_metrics(dev, probs)
+            L, T = w.portfolio.n_layers, w.yet.n_trials
+            ids = torch.from_numpy(w.yet.event_ids).pin_memory()
+            off = None if w.yet.trial_off is None else torch.from_numpy(w.yet.trial_off)
+            for want_ylt in (True, False):
+                out = torch.zeros((L, T), dtype=torch.float64).pin_memory() if want_ylt else None
+                m = np.zeros(L)
+                pm = np.zeros((L, len(probs)))
+                tv = np.zeros((L, len(probs)))
+                art.art_run_ylt_host_metrics(p, T, ids, off, w.yet.events_per_trial, probs, ylt=out, mean=m,
+                                             pml=pm, tvar=tv)
+                if want_ylt:
+                    assert torch.equal(out, dev.cpu()), w.name
+                assert np.array_equal(m, mean) and np.array_equal(pm, pml) and np.array_equal(tv, tvar), w.name
+            om, op, ot = oracle.metrics(dev.cpu().numpy(), probs)
+            np.testing.assert_array_equal(pm, op)
+            np.testing.assert_allclose(tv, ot, rtol=1e-12)
+        finally:
+            p.close()
+
+
 def test_out_of_range_ids_flag_without_trapping():
     w = workloads.random_case(203, n_trials=50, min_len=5, max_len=20)
     ids = w.yet.event_ids.copy()
