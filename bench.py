@@ -343,6 +343,65 @@ def roofline(ab: dict, secs: float, hbm_gbs: float, l2_gbs=None, fp64_gflops=Non
     return out
 
 
+def first_layers(w, n: int):
+    """The workload with only its first n layers (smaller profiling cases of
+    the multi-layer kernels: the same occurrence-group shapes, fewer groups)."""
+    import dataclasses
+    port = w.portfolio
+    n = min(n, port.n_layers)
+    off = port.layer_elt_off[:n + 1].copy()
+    sub = dataclasses.replace(port, layer_elt_off=off, layer_elt_ids=port.layer_elt_ids[:off[-1]].copy(),
+                              occ_ret=port.occ_ret[:n].copy(), occ_lim=port.occ_lim[:n].copy(),
+                              agg_ret=port.agg_ret[:n].copy(), agg_lim=port.agg_lim[:n].copy())
+    return dataclasses.replace(w, portfolio=sub)
+
+
+def synthetic_ylt(torch, L: int, T: int, dev, seed: int = 1308):
+    """A seeded YLT [L][T] shaped like the pool workloads' (lognormal
+    aggregate losses, a quarter of the trials without loss, a layer-dependent
+    share of 0-30% of the trials at the layer's aggregate cap), for timing
+    the metrics kernels alone."""
+    g = torch.Generator(device=dev).manual_seed(seed)
+    y = torch.empty((L, T), dtype=torch.float64, device=dev)
+    y.log_normal_(16.0, 1.5, generator=g)
+    share = torch.linspace(0.0, 0.3, L, dtype=torch.float64, device=dev)
+    head = torch.sort(y[:, :min(T, 50000)], dim=1).values
+    idx = ((1.0 - share) * (head.shape[1] - 1)).long()
+    cap = head[torch.arange(L, device=dev), idx]
+    torch.minimum(y, cap[:, None], out=y)
+    y[:, ::4] = 0.0
+    return y
+
+
+def run_metrics_only(args):
+    """art_metrics alone on a synthetic YLT of --layers x --trials (default
+    128 x 1,000,000) at --probs: ms per call, and GB/s per full read."""
+    import torch
+    from paper_1308_2572_gb300 import art
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L, T = args.layers or 128, args.trials or 1_000_000
+    probs = [float(x) for x in args.probs.split(",")]
+    y = synthetic_ylt(torch, L, T, dev)
+    n_p = len(probs)
+    mean = torch.empty(L, dtype=torch.float64, device=dev)
+    pml = torch.empty((L, n_p), dtype=torch.float64, device=dev)
+    tvar = torch.empty((L, n_p), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        art.art_metrics(y, T, L, probs, mean, pml, tvar)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        art.art_metrics(y, T, L, probs, mean, pml, tvar)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metrics_only": True, "layers": L, "trials": T, "probs": probs, "ms_per_call": ms,
+                      "ylt_gbs_per_full_read": L * T * 8 / (ms * 1e-3) / 1e9}), flush=True)
+    return 0
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, on the host cores, on a
     bounded sample of the workload per step."""
@@ -582,13 +641,20 @@ def main():
                     help="persisting L2 access-policy window over the hot table (ART_FLAG_L2_PERSIST)")
     ap.add_argument("--trials", type=int, default=0,
                     help="keep only the first N trials (small cases for profiling; 0 = the full workload)")
+    ap.add_argument("--layers", type=int, default=0,
+                    help="keep only the first N layers (small cases for profiling; 0 = all)")
+    ap.add_argument("--metrics-only", action="store_true",
+                    help="time art_metrics alone on a synthetic YLT of --layers x --trials (128 x 1,000,000)")
+    ap.add_argument("--probs", default="0.99,0.996,0.999", help="probabilities of --metrics-only")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.metrics_only:
+        return run_metrics_only(args)
 
     import torch
-    from paper_1308_2572_gb300 import art, workloads
+    from paper_1308_2572_gb300 import art, shard, workloads
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -599,8 +665,16 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     l2_size = float(torch.cuda.get_device_properties(dev).L2_cache_size)
 
+    # the differentiation workload (c3) steps forward and backward; the
+    # others, on more than one GPU, shard one YLT: each rank draws its own
+    # YET of the workload's recipe (the same portfolio), and the metrics of
+    # the whole YLT come from the ranks' top-k lists, all-gathered and merged
+    with_grad = args.config == "c3"
+    sharded = world > 1 and not with_grad
     t_gen = time.perf_counter()
-    w = workloads.make(args.config, n_trials=args.trials or None)
+    w = workloads.make(args.config, n_trials=args.trials or None, shard=rank if sharded else 0)
+    if args.layers:
+        w = first_layers(w, args.layers)
     log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
@@ -625,9 +699,8 @@ def main():
     vmap = {"plain": art.ART_VARIANT_PLAIN, "batched": art.ART_VARIANT_BATCHED, "fp64": art.ART_VARIANT_FP64,
             "skip": art.ART_VARIANT_SKIP, "sparse": art.ART_VARIANT_SPARSE}
 
-    # the differentiation workload (c3) steps forward and backward: branch
-    # codes in the forward, then dLoss/dYLT for sum(EL + TVaR) and the adjoint
-    with_grad = args.config == "c3"
+    # c3: branch codes in the forward, then dLoss/dYLT for sum(EL + TVaR)
+    # and the adjoint
     branch = torch.empty((L, T), dtype=torch.uint8, device=dev) if with_grad else None
     gylt = torch.empty_like(ylt) if with_grad else None
     ones_l = torch.ones(L, dtype=torch.float64, device=dev)
@@ -635,9 +708,15 @@ def main():
     gterms = torch.empty((L, 4), dtype=torch.float64, device=dev)
     gmult = torch.empty(port.n_elt, dtype=torch.float64, device=dev)
 
+    def metrics():
+        if sharded:
+            shard.sharded_metrics(ylt, world * T, probs, stream=stream)
+        else:
+            art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+
     def step():
         art.art_run_ylt(p, T, ids, off, K, ylt, branch, stream)
-        art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+        metrics()
         if with_grad:
             art.art_metrics_backward(ylt, T, L, probs, pml, ones_l, ones_lp, gylt, stream)
             art.art_run_ylt_backward(p, T, ids, off, K, branch, gylt, gterms, gmult, stream)
@@ -677,7 +756,7 @@ def main():
         ev[i][0].record(stream)
         art.art_run_ylt(p, T, ids, off, K, ylt, branch, stream)
         ev[i][1].record(stream)
-        art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
+        metrics()
         if with_grad:
             art.art_metrics_backward(ylt, T, L, probs, pml, ones_l, ones_lp, gylt, stream)
             art.art_run_ylt_backward(p, T, ids, off, K, branch, gylt, gterms, gmult, stream)
@@ -727,8 +806,16 @@ def main():
         tvar_h = torch.empty((L, n_p), dtype=torch.float64).pin_memory()
 
         def e2e_step():
-            art.art_run_ylt_host_metrics(p, T, ids_h, off_h, K, probs, ylt=ylt_h, mean=mean_h, pml=pml_h,
-                                         tvar=tvar_h, stream=stream)
+            if sharded:
+                # the shard's YLT comes back to the host and goes to the
+                # device again for the top-k lists: the host-buffer call
+                # returns the YLT, and the merge needs every rank's lists
+                art.art_run_ylt_host(p, T, ids_h, off_h, K, ylt_h, stream)
+                ylt.copy_(ylt_h, non_blocking=True)
+                shard.sharded_metrics(ylt, world * T, probs, stream=stream)
+            else:
+                art.art_run_ylt_host_metrics(p, T, ids_h, off_h, K, probs, ylt=ylt_h, mean=mean_h, pml=pml_h,
+                                             tvar=tvar_h, stream=stream)
 
         e2e_step()  # grows the staging and device YLT buffers
         if dist:
@@ -744,13 +831,18 @@ def main():
         # the bytes the step moves: the YET (and offsets) in, the YLT and the metrics out
         h2d = yet.event_ids.nbytes + (0 if yet.trial_off is None else yet.trial_off.nbytes)
         d2h = 8 * L * T + 8 * L * (1 + 2 * n_p)
+        if sharded:
+            h2d += 8 * L * T  # the shard's YLT back to the device
+            d2h = 8 * L * T + 8 * L * (shard.list_length(world * T, probs) * world + world)
         link = link_probe(torch, ids_h, dev, 64 << 20)
         e2e = {"value": whole_job_rate(lookups, world, e2e_s), "unit": "trial-events*ELTs/s",
                "ms_per_step": e2e_s * 1e3, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_each_step_rank0": [round(t, 3) for t in each],
                "step_h2d_gbs": h2d / e2e_s / 1e9, "h2d_link_rank0": link,
-               "path": "art_run_ylt_host_metrics (pinned host YET in 64 MiB chunks, H2D overlapped with the "
-                       "forward; YLT kept on the device for art_metrics; YLT and metrics copied back)"}
+               "path": ("art_run_ylt_host per rank, the shard's YLT to the device, art_topk, all-gather, host "
+                        "merge (art_merge_topk)") if sharded else
+                       ("art_run_ylt_host_metrics (pinned host YET in 64 MiB chunks, H2D overlapped with the "
+                        "forward; YLT kept on the device for art_metrics; YLT and metrics copied back)")}
         del ids_h, ylt_h
 
     # optional early exit (capped trials stop being read), reported separately
@@ -783,14 +875,18 @@ def main():
               "layers": L, "trials": T, "events": yet.n_events,
               "lookups_per_step": lookups, "lookups_performed_per_step": ab["lookups_performed"],
               "l2": "inputs larger than L2 (the 4 GB YET is re-streamed every step)",
-              "parallelism": f"{world} independent ranks (weak scaling, no collective in the data path)"}
+              "parallelism": (f"{world} ranks sharding one YLT of {world} x {T} trials: each rank its own YET "
+                              "shard; per-layer top-k lists and sums all-gathered (NCCL) and merged exactly for "
+                              "the metrics (weak scaling)") if sharded else
+                             (f"{world} independent ranks (weak scaling, no collective in the data path)"
+                              if world > 1 else "one GPU")}
     p.close()
     del ylt, ids, off
     torch.cuda.empty_cache()
 
     extras = {}
     names = [] if args.workloads in ("", "none") else [n for n in args.workloads.split(",") if n != args.config]
-    if rank == 0 and not args.trials:
+    if rank == 0 and not args.trials and not args.layers:
         for name in names:
             t0 = time.perf_counter()
             try:

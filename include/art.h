@@ -349,6 +349,48 @@ ART_API art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trials, 
                                        double* tvar_dev, cudaStream_t stream);
 
 /*
+ * art_topk -- one shard's share of the metrics of a YLT split by trials
+ * (Section III: trials are independent; Section IV-C: the multi-GPU runs
+ * split the trials of the YET between the GPUs). PML_p and TVaR_p of a layer
+ * depend only on its ceil((1 - p) N) largest trial losses, and those of the
+ * whole YLT lie among the union of every shard's largest: per layer, this
+ * writes the shard's k largest losses and its loss sum, and art_merge_topk
+ * gives the whole YLT's metrics from the shards' outputs.
+ *  ylt_dev   [n_layers][n_trials] FP64, this shard's trials (values >= 0);
+ *            1 <= n_trials <= 2^31 - 1, 1 <= n_layers <= 65535.
+ *  k         list length, 1 <= k <= 2^31 - 1.
+ *  top_dev   [n_layers][k] FP64 output: the losses above the shard's
+ *            min(k, n_trials)-th largest in trial order, then that loss as
+ *            often as needed to fill min(k, n_trials) entries, then zeros.
+ *  sum_dev   [n_layers] FP64 output (may be NULL): each layer's loss sum.
+ * Deterministic (the same list for the same YLT). Scratch from the
+ * stream-ordered allocator. Errors: ART_EINVAL, ART_ECUDA.
+ */
+ART_API art_status art_topk(const double* ylt_dev, int64_t n_trials, int32_t n_layers, int64_t k, double* top_dev,
+                            double* sum_dev, cudaStream_t stream);
+
+/*
+ * art_merge_topk -- the merge step of sharded metrics (Section I: PML and
+ * TVaR of the YLT; Section IV-C: trials split between GPUs), on the host.
+ * From the lists and sums of n_shards shards (art_topk outputs gathered in
+ * shard order), the mean, PML and TVaR of the whole YLT of n_trials_total
+ * trials as art_metrics defines them: PML the k_q-th largest of the union of
+ * the lists, k_q = ceil((1 - p_q) n_trials_total), TVaR the mean of the k_q
+ * largest, the mean the shards' sums over n_trials_total.
+ *  top_host   [n_shards][n_layers][k] FP64; sum_host [n_shards][n_layers] FP64.
+ *  probs_host [n_p] in (0, 1), 1 <= n_p <= 8, every k_q <= k.
+ *  mean_host  [n_layers], pml_host and tvar_host [n_layers][n_p]: host
+ *             outputs, each may be NULL.
+ * PML equals art_metrics on the whole YLT bit for bit; TVaR and the mean
+ * differ only in the order of their FP64 additions (sums in shard and list
+ * order: deterministic). Runs on host threads; needs no GPU.
+ * Errors: ART_EINVAL (NULL inputs, sizes, probabilities, a k_q above k).
+ */
+ART_API art_status art_merge_topk(const double* top_host, const double* sum_host, int32_t n_shards, int32_t n_layers,
+                                  int64_t k, int64_t n_trials_total, const double* probs_host, int32_t n_p,
+                                  double* mean_host, double* pml_host, double* tvar_host);
+
+/*
  * art_metrics_backward -- gradient of sum_j (gm_j mean_j + sum_q gt_{j,q}
  * TVaR_{j,q}) with respect to the YLT (the paper has no gradients; the
  * metrics are those of Section I, read as in art_metrics): grad_ylt[j][t] = gm_j / T

@@ -27,7 +27,7 @@ EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set
            "art_run_ylt_host", "art_metrics", "art_metrics_backward", "art_run_ylt_backward",
            "art_get_device_status", "art_get_footprint", "art_destroy_portfolio", "art_status_string",
            "art_last_cuda_error", "art_version", "art_metrics_noalloc", "art_probe", "art_autotune",
-           "art_run_payouts", "art_set_flags", "art_run_ylt_host_metrics")
+           "art_run_payouts", "art_set_flags", "art_run_ylt_host_metrics", "art_topk", "art_merge_topk")
 
 
 class LayerTerms(ctypes.Structure):
@@ -81,6 +81,8 @@ def lib():
         "art_metrics": ([P, i64, i32, P, i32, P, P, P, P], st),
         "art_metrics_backward": ([P, i64, i32, P, i32, P, P, P, P, P], st),
         "art_metrics_noalloc": ([P, i64, i32, P, i32, P, P, P, P], st),
+        "art_topk": ([P, i64, i32, i64, P, P, P], st),
+        "art_merge_topk": ([P, P, i32, i32, i64, i64, P, i32, P, P, P], st),
         "art_run_ylt_backward": ([P, i64, P, P, i32, P, P, P, P, P], st),
         "art_get_device_status": ([P, P], st),
         "art_get_footprint": ([P, P, P, P, P, P], st),
@@ -277,6 +279,23 @@ def art_metrics_noalloc(ylt, n_trials: int, n_layers: int, probs: Sequence[float
         raise ArtError(rc, "art_metrics_noalloc (invalid arguments, or the layers x probabilities need more than "
                            "the 8 MiB static scratch)")
     _check(rc, "art_metrics_noalloc")
+
+
+def art_topk(ylt, n_trials: int, n_layers: int, k: int, top, sums=None, stream=None) -> None:
+    """One shard's per-layer top-k list (CUDA float64 [L][k]) and loss sums
+    (CUDA float64 [L] or None) for a sharded metrics merge."""
+    rc = lib().art_topk(_dptr(ylt), int(n_trials), int(n_layers), int(k), _dptr(top), _dptr(sums), _stream(stream))
+    _check(rc, "art_topk")
+
+
+def art_merge_topk(top, sums, n_shards: int, n_layers: int, k: int, n_trials_total: int, probs, mean=None,
+                   pml=None, tvar=None) -> None:
+    """Host merge of the shards' lists ([S][L][k]) and sums ([S][L]) into the
+    whole YLT's mean [L], PML and TVaR [L][n_p] (host arrays or CPU tensors)."""
+    pr = np.ascontiguousarray(probs, dtype=np.float64)
+    rc = lib().art_merge_topk(_hptr(top), _hptr(sums), int(n_shards), int(n_layers), int(k), int(n_trials_total),
+                              _hptr(pr), pr.size, _hptr(mean), _hptr(pml), _hptr(tvar))
+    _check(rc, "art_merge_topk")
 
 
 def art_metrics_backward(ylt, n_trials: int, n_layers: int, probs, pml, grad_mean, grad_tvar, grad_ylt,

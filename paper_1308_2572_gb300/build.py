@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libart.so")
-SOURCES = ["art_api.cu", "ylt_plain.cu", "ylt_batched.cu", "ylt_skip.cu", "ylt_skip64.cu", "ylt_sparse.cu", "metrics.cu", "adjoint.cu", "adjoint_group.cu", "probes.cu", "payouts.cu"]
+SOURCES = ["art_api.cu", "ylt_plain.cu", "ylt_batched.cu", "ylt_skip.cu", "ylt_skip64.cu", "ylt_sparse.cu", "metrics.cu", "adjoint.cu", "adjoint_group.cu", "probes.cu", "payouts.cu", "shard.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]

@@ -301,6 +301,10 @@ cudaError_t launch_adjoint_groups(art_portfolio* p, const YetArgs& y, const uint
                                   double* grad_terms, double* grad_mult, cudaStream_t s);
 cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
                         double* mean, double* pml, double* tvar, cudaStream_t s);
+// The same with the ranks k given (clamped to [1, n]) instead of
+// probabilities; sum_out (may be NULL) receives each layer's FP64 loss sum.
+cudaError_t metrics_run_k(const double* ylt, int64_t n, int32_t n_layers, const int64_t* k, int32_t n_p,
+                          double* mean, double* pml, double* tvar, double* sum_out, cudaStream_t s);
 cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs,
                                  int32_t n_p, const double* pml, const double* gmean, const double* gtvar,
                                  double* gylt, cudaStream_t s);

@@ -6,23 +6,33 @@
 // largest trial loss and TVaR_p the mean of the k largest.
 //
 // Exact selection without a sort: trial losses are >= 0, so the FP64 bit
-// pattern (sign cleared, which also folds -0 onto +0) orders like the value. A
-// most-significant-digit radix select over 63 bits in six passes (digits of
-// 11, 11, 11, 11, 11 and 8 bits) narrows, for every (layer, probability)
-// problem at once, the prefix of the k-th largest key. Each pass is one
-// launch: its blocks histogram the keys that match the prefix found so far
-// (shared-memory histograms with warp-aggregated atomics: lanes holding the
-// same digit add once; flushed to global with atomics), and the last block of
-// each layer to finish (a ticket counter after a fence; no block waits for
-// another) picks the digit where the count from the top crosses the remaining
-// rank. Problems of a layer that share a prefix (all of them in the first
-// pass) share one histogram, and a problem whose candidates all hold one key
-// (their smallest and largest agree) is decided at once, its later passes
-// returning early. A last launch sums the values strictly above the k-th
-// largest, and its last block reduces the partials: TVaR adds the tied
-// remainder, (sum_gt + (k - count_gt) * PML) / k. Seven launches in all. Sums
-// are FP64 and deterministic (per-thread, per-block, then per-problem in a
-// fixed order).
+// pattern (sign cleared, which also folds -0 onto +0) orders like the value.
+// A most-significant-digit radix select over the 63 key bits narrows, for
+// every (layer, probability) problem at once, the prefix of the k-th largest
+// key: a first digit of 13 bits (the binary exponent and two leading mantissa
+// bits), then digits of 11, 11, 11, 11 and 6 bits. Each pass is one launch:
+// its blocks histogram the keys that match the prefix found so far
+// (shared-memory histograms with warp-aggregated atomics, flushed to global
+// with atomics), and the last block of each layer to finish (a ticket counter
+// after a fence; no block waits for another) picks the digit where the count
+// from the top crosses the remaining rank. A problem whose candidates all
+// hold one key is decided at once.
+//
+// Only the first two passes read the whole YLT. The first also sums each
+// layer for the mean and records its smallest and largest key; its last block
+// lays out, per layer, a candidate list as long as the first-digit buckets
+// its problems selected (while the lists fit the scratch). The second pass
+// copies into that list every key of those buckets other than 0 and the
+// layer's largest key -- the two values that repeat most (trials without a
+// loss, trials at the aggregate cap), which are only counted -- and sums, in
+// a fixed order, the values above each problem's bucket. The remaining
+// passes and the tail read the candidate list alone, adding the counted keys
+// to the histograms where they match. The tail sums the candidates above the
+// k-th largest key of the problem's bucket as integers: they share one binary
+// exponent, so their mantissas add exactly and in any order. TVaR is
+// (sum_gt + (k - count_gt) PML) / k. A layer whose candidates do not fit
+// keeps reading its whole row in every pass, and its tail sums in a fixed
+// order. Every sum is deterministic.
 #include <algorithm>
 #include <cmath>
 
@@ -33,29 +43,45 @@ namespace art {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;  // values per thread whose loads are in flight together
-constexpr int kMaxBins = 2048;
+constexpr int kUnroll = 8;        // values per thread whose loads are in flight together
 constexpr int kPasses = 6;
-__host__ __device__ constexpr int pass_shift(int i) { return i < 5 ? 52 - 11 * i : 0; }
-__host__ __device__ constexpr int pass_bits(int i) { return i < 5 ? 11 : 8; }
+constexpr int kBins1 = 8192;      // first digit: key bits 62..50
+constexpr int kMaxBins = 2048;    // later digits: 11 bits (the last one 6)
+constexpr int kShift1 = 50;
+__host__ __device__ constexpr int pass_shift(int i) { return i == 0 ? kShift1 : (i < 5 ? kShift1 - 11 * i : 0); }
+__host__ __device__ constexpr int pass_bits(int i) { return i == 0 ? 13 : (i < 5 ? 11 : 6); }
+constexpr unsigned long long kAllKeyBits = 0x7fffffffffffffffULL;  // a decided problem's mask
+constexpr unsigned long long kMant = (1ULL << 52) - 1;
 
 struct KParams {
     long long k[kMaxProbs];
 };
 
+// Selection state of one (layer, probability) problem.
 struct SelState {
-    unsigned long long prefix;
-    unsigned long long mask;
-    long long krem;
+    unsigned long long prefix;  // key bits found so far (the k-th largest key once decided)
+    unsigned long long mask;    // which bits prefix holds
+    long long krem;             // rank of the k-th largest among the keys matching prefix
     long long k;
+    long long above1;           // keys above the first-digit bucket
+    unsigned long long b1;      // the first-digit bucket (key >> 50)
+    int first_decided;          // decided in the first pass (a constant layer)
+    int pad_;
+};
+
+// Per-layer state; every field but need, cand_off and compact starts at zero.
+struct LayerState {
+    unsigned long long kmax, kinv;         // largest key, complement of the smallest (first pass)
+    unsigned long long cnt_zero, cnt_max;  // keys equal to 0 / to kmax (second pass, compacted layers)
+    unsigned long long need;               // candidate slots the selected buckets hold (first pass)
+    unsigned long long cand_off;           // the layer's candidate list in the scratch
+    unsigned int cand_n;                   // candidates written (second pass)
+    int compact;                           // later passes read the candidate list
 };
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
-
-// A problem whose mask covers every key bit is decided: its prefix is the key.
-constexpr unsigned long long kAllKeyBits = 0x7fffffffffffffffULL;
 
 // Block-wide maximum of a 64-bit value (valid in thread 0).
 __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
@@ -93,6 +119,625 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
     return r;
+}
+
+// Histogram add for the lanes with `hit`, warp-aggregated: when every such
+// lane has the same digit (losses cluster: a capped layer, zero trials) one
+// lane adds them all; otherwise lanes with equal digits add once each.
+// Called by the whole warp.
+__device__ __forceinline__ void hist_add(unsigned int* h, unsigned dig, bool hit, unsigned lane) {
+    const unsigned act = __ballot_sync(0xffffffffu, hit);
+    if (!act) return;
+    const int first = __ffs(act) - 1;
+    const unsigned d0 = __shfl_sync(0xffffffffu, dig, first);
+    if (__all_sync(0xffffffffu, !hit || dig == d0)) {
+        if (lane == (unsigned)first) atomicAdd(h + d0, __popc(act));
+        return;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
+    if (hit && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(h + dig, __popc(peers));
+}
+
+// Block-wide digit pick: the bin of bins[0, nb) (shared memory) where the
+// count of keys from the top reaches krem, and the count in the bins above
+// it. Valid in every thread on return.
+__device__ void pick_digit(const unsigned int* bins, int nb, long long krem, int* bin_out,
+                           unsigned long long* above_out) {
+    __shared__ unsigned long long sh_scan[kThreads];
+    __shared__ int sh_bin;
+    __shared__ unsigned long long sh_above;
+    const int per = (nb + kThreads - 1) / kThreads;
+    // thread i covers descending ranks [i*per, (i+1)*per): bins nb-1-i*per downwards
+    unsigned long long local = 0;
+    for (int r = 0; r < per; ++r) {
+        const int idx = threadIdx.x * per + r;
+        if (idx < nb) local += bins[nb - 1 - idx];
+    }
+    sh_scan[threadIdx.x] = local;
+    if (threadIdx.x == 0) {
+        sh_bin = -1;
+        sh_above = 0;
+    }
+    __syncthreads();
+    for (int o = 1; o < kThreads; o <<= 1) {
+        const unsigned long long add = threadIdx.x >= (unsigned)o ? sh_scan[threadIdx.x - o] : 0ULL;
+        __syncthreads();
+        sh_scan[threadIdx.x] += add;
+        __syncthreads();
+    }
+    const unsigned long long incl = sh_scan[threadIdx.x];
+    const unsigned long long excl = incl - local;
+    if ((long long)excl < krem && krem <= (long long)incl) {
+        unsigned long long run = excl;
+        for (int r = 0; r < per; ++r) {
+            const int idx = threadIdx.x * per + r;
+            if (idx >= nb) break;
+            const unsigned c = bins[nb - 1 - idx];
+            if ((long long)(run + c) >= krem) {
+                sh_bin = nb - 1 - idx;
+                sh_above = run;
+                break;
+            }
+            run += c;
+        }
+    }
+    __syncthreads();
+    *bin_out = sh_bin < 0 ? 0 : sh_bin;  // -1 is unreachable when the counts are consistent
+    *above_out = sh_above;
+    __syncthreads();
+}
+
+// Pass 1 over every value: first-digit histogram (one per layer, shared by
+// its problems), the layer's sum for the mean (two FP64 accumulators, fixed
+// assignment), its smallest and largest key. The last block of a layer picks
+// its problems' first digits; the last layer to be picked lays out the
+// candidate lists (greedily, in layer order, while they fit the budget).
+__global__ void __launch_bounds__(kThreads) first_pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                              const KParams kq, SelState* __restrict__ st,
+                                                              LayerState* __restrict__ ls,
+                                                              unsigned int* __restrict__ hist1,
+                                                              double* __restrict__ part_mean,
+                                                              unsigned int* __restrict__ tickets,
+                                                              unsigned long long cand_budget) {
+    extern __shared__ unsigned int sh_hist[];  // [kBins1]
+    __shared__ double sh_red[32];
+    __shared__ unsigned long long sh_red_u[32];
+    __shared__ bool sh_last;
+    __shared__ unsigned long long sh_need[kThreads];
+    const int j = blockIdx.y;
+    const int n_layers = gridDim.y;
+    const unsigned lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kBins1; i += blockDim.x) sh_hist[i] = 0;
+    __syncthreads();
+    const double* row = ylt + (size_t)j * (size_t)n;
+    double s0 = 0.0, s1 = 0.0;
+    unsigned long long kmax = 0, kinv = 0;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
+         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+        double v[kUnroll];
+        bool valid[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+            valid[u] = i < n;
+            v[u] = valid[u] ? __ldcs(row + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (u & 1) s1 += v[u];
+            else s0 += v[u];
+            const unsigned long long key = key_of(v[u]);
+            hist_add(sh_hist, (unsigned)(key >> kShift1), valid[u], lane);
+            if (valid[u]) {
+                kmax = max(kmax, key);
+                kinv = max(kinv, ~key);
+            }
+        }
+    }
+    const double r = block_sum(s0 + s1, sh_red);
+    if (threadIdx.x == 0) part_mean[(size_t)j * gridDim.x + blockIdx.x] = r;
+    const unsigned long long a = block_max_u64(kmax, sh_red_u);
+    const unsigned long long b = block_max_u64(kinv, sh_red_u);
+    if (threadIdx.x == 0) {
+        atomicMax(&ls[j].kmax, a);
+        atomicMax(&ls[j].kinv, b);
+    }
+    __syncthreads();
+    unsigned int* gh = hist1 + (size_t)j * kBins1;
+    for (int i = threadIdx.x; i < kBins1; i += blockDim.x) {
+        const unsigned c = sh_hist[i];
+        if (c) atomicAdd(&gh[i], c);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(&tickets[j], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    // the layer's complete histogram
+    for (int i = threadIdx.x; i < kBins1; i += blockDim.x) sh_hist[i] = __ldcg(&gh[i]);
+    const unsigned long long hi = __ldcg(&ls[j].kmax), lo = ~__ldcg(&ls[j].kinv);
+    __syncthreads();
+    for (int q = 0; q < n_p; ++q) {
+        SelState* sq = &st[j * n_p + q];
+        if (hi == lo) {
+            // a constant layer: every problem is decided by its one key
+            if (threadIdx.x == 0)
+                *sq = SelState{hi, kAllKeyBits, 1, kq.k[q], 0, hi >> kShift1, 1, 0};
+        } else {
+            int bin;
+            unsigned long long above;
+            pick_digit(sh_hist, kBins1, kq.k[q], &bin, &above);
+            if (threadIdx.x == 0)
+                *sq = SelState{(unsigned long long)bin << kShift1, (unsigned long long)(kBins1 - 1) << kShift1,
+                               kq.k[q] - (long long)above, kq.k[q], (long long)above, (unsigned long long)bin, 0, 0};
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // candidate slots: the keys of the distinct buckets the problems selected
+        unsigned long long need = 0;
+        if (hi != lo) {
+            for (int q = 0; q < n_p; ++q) {
+                const unsigned long long bq = st[j * n_p + q].b1;
+                bool seen = false;
+                for (int r = 0; r < q; ++r) seen = seen || st[j * n_p + r].b1 == bq;
+                if (!seen) need += sh_hist[bq];
+            }
+        }
+        ls[j].need = need;
+        tickets[j] = 0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(&tickets[n_layers], 1u) == (unsigned)n_layers - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    // the last layer picked: candidate lists in layer order while they fit
+    unsigned long long run = 0;
+    for (int c0 = 0; c0 < n_layers; c0 += kThreads) {
+        const int jj = c0 + threadIdx.x;
+        sh_need[threadIdx.x] = jj < n_layers ? __ldcg(&ls[jj].need) : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int t = 0; t < kThreads && c0 + t < n_layers; ++t) {
+                const unsigned long long nd = sh_need[t];
+                const bool fits = run + nd <= cand_budget;
+                ls[c0 + t].compact = fits ? 1 : 0;
+                ls[c0 + t].cand_off = fits ? run : 0;
+                if (fits) run += nd;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tickets[n_layers] = 0;
+}
+
+// Passes 2-6. Each block histograms the keys matching each problem's prefix
+// (problems with the same prefix share the histogram of the first of them),
+// from the layer's whole row in pass 2 and in every pass of a layer without
+// a candidate list, else from the candidate list. Pass 2 also writes the
+// candidate lists (keys of the selected first-digit buckets other than 0 and
+// the layer's largest key, which it counts), and the per-block sums of the
+// values above each problem's bucket. The last block of a layer picks the
+// digits; the counted keys enter its histograms and extremes when they match.
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                        SelState* __restrict__ st, LayerState* __restrict__ ls,
+                                                        unsigned long long* __restrict__ cand, int shift, int bits,
+                                                        bool second, unsigned int* __restrict__ ghist,
+                                                        unsigned long long* __restrict__ minmax,
+                                                        double* __restrict__ part_above,
+                                                        unsigned int* __restrict__ tickets) {
+    extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
+    __shared__ double sh_red[32];
+    __shared__ unsigned long long sh_red_u[32];
+    __shared__ bool sh_last;
+    __shared__ int sh_src[kMaxProbs];
+    const int nb = 1 << bits;
+    const int j = blockIdx.y;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned long long pre[NQ], msk[NQ], b1[NQ];
+    bool done[NQ];
+    bool all_done = true;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        pre[q] = q < n_p ? st[j * n_p + q].prefix : 1ULL;  // unused slots never match
+        msk[q] = q < n_p ? st[j * n_p + q].mask : 0ULL;
+        b1[q] = q < n_p ? st[j * n_p + q].b1 : 0ULL;
+        done[q] = q >= n_p || msk[q] == kAllKeyBits;
+        all_done = all_done && done[q];
+    }
+    if (all_done) return;  // the same for every block of the layer: no ticket is taken
+    const bool compact = ls[j].compact != 0;
+    const unsigned long long kmax_l = ls[j].kmax;
+    const bool from_row = second || !compact;
+    const double* src_vals = from_row ? ylt + (size_t)j * (size_t)n
+                                      : reinterpret_cast<const double*>(cand + ls[j].cand_off);
+    const int64_t len = from_row ? n : (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need);
+    const bool writing = second && compact;  // pass 2 writes the layer's candidate list
+    unsigned long long* my_cand = cand + ls[j].cand_off;
+    const unsigned long long cap = ls[j].need;
+    int src[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        src[q] = q;
+#pragma unroll
+        for (int r = NQ - 1; r >= 0; --r)
+            if (r < q && !done[r] && !done[q] && pre[r] == pre[q] && msk[r] == msk[q]) src[q] = r;
+        if (threadIdx.x == 0 && q < n_p) sh_src[q] = src[q];
+    }
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
+    unsigned long long kmx[NQ], kiv[NQ];
+    double sab[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        kmx[q] = 0;
+        kiv[q] = 0;
+        sab[q] = 0.0;
+    }
+    unsigned long long czero = 0, cmax = 0;
+    __syncthreads();
+    const unsigned dmask = (unsigned)nb - 1u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
+         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+        double v[kUnroll];
+        bool valid[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+            valid[u] = i < len;
+            v[u] = valid[u] ? __ldcs(src_vals + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const unsigned long long key = key_of(v[u]);
+            const unsigned dig = (unsigned)(key >> shift) & dmask;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (q < n_p && !done[q] && src[q] == q) {  // the same for the whole block
+                    const bool hit = valid[u] && (key & msk[q]) == pre[q];
+                    any = any || hit;
+                    // after the first digits few warps hold a candidate at all
+                    if (__any_sync(0xffffffffu, hit)) {
+                        hist_add(sh_hist + q * nb, dig, hit, lane);
+                        if (hit) {
+                            kmx[q] = max(kmx[q], key);
+                            kiv[q] = max(kiv[q], ~key);
+                        }
+                    }
+                }
+            }
+            if (writing) {
+                czero += (valid[u] && key == 0ULL) ? 1 : 0;
+                cmax += (valid[u] && key == kmax_l) ? 1 : 0;
+                const bool c = any && key != 0ULL && key != kmax_l;
+                const unsigned m = __ballot_sync(0xffffffffu, c);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    unsigned int base = 0;
+                    if (lane == (unsigned)leader) base = atomicAdd(&ls[j].cand_n, (unsigned)__popc(m));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    const unsigned long long slot = (unsigned long long)base + __popc(m & lt_mask);
+                    if (c && slot < cap) my_cand[slot] = key;
+                }
+                // values above each problem's first-digit bucket, for TVaR
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    if (q < n_p && !done[q]) {
+                        const bool up = valid[u] && (key >> kShift1) > b1[q];
+                        if (__any_sync(0xffffffffu, up) && up) sab[q] += v[u];
+                    }
+                }
+            }
+        }
+    }
+    if (writing) {
+        const unsigned long long z = block_sum_u64(czero, sh_red_u);
+        const unsigned long long m = block_sum_u64(cmax, sh_red_u);
+        if (threadIdx.x == 0) {
+            if (z) atomicAdd(&ls[j].cnt_zero, z);
+            if (m) atomicAdd(&ls[j].cnt_max, m);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (q >= n_p || done[q]) continue;
+            const double s = block_sum(sab[q], sh_red);
+            if (threadIdx.x == 0) part_above[((size_t)j * n_p + q) * gridDim.x + blockIdx.x] = s;
+        }
+    }
+    // a problem that shares its source's candidates shares its extremes
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+        for (int r = 0; r < NQ; ++r)
+            if (r < q && src[q] == r) {
+                kmx[q] = kmx[r];
+                kiv[q] = kiv[r];
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (q >= n_p || done[q]) continue;
+        const unsigned long long a = block_max_u64(kmx[q], sh_red_u);
+        const unsigned long long b = block_max_u64(kiv[q], sh_red_u);
+        if (threadIdx.x == 0) {
+            if (a) atomicMax(&minmax[2 * ((size_t)j * n_p + q)], a);
+            if (b) atomicMax(&minmax[2 * ((size_t)j * n_p + q) + 1], b);
+        }
+    }
+    __syncthreads();
+    unsigned int* gh = ghist + ((size_t)j * n_p) * kMaxBins;
+    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
+        const int q = i >> bits, b = i & (int)dmask;
+        const unsigned c = sh_hist[sh_src[q] * nb + b];  // zero for a decided problem
+        if (c) atomicAdd(&gh[(size_t)q * kMaxBins + b], c);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(&tickets[j], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    // keys counted instead of listed take part from pass 3 on, where they match
+    const bool virt = !second && compact;
+    const unsigned long long cz = virt ? __ldcg(&ls[j].cnt_zero) : 0ULL;
+    const unsigned long long cm = virt ? __ldcg(&ls[j].cnt_max) : 0ULL;
+    for (int q = 0; q < n_p; ++q) {
+        if (done[q]) continue;
+        SelState* sq = &st[j * n_p + q];
+        unsigned long long* mm = &minmax[2 * ((size_t)j * n_p + q)];
+        unsigned long long hi = __ldcg(mm), inv = __ldcg(mm + 1);  // inv == 0: no listed candidate
+        const bool max_in = cm && (kmax_l & msk[q]) == pre[q];
+        const bool zero_in = cz && pre[q] == 0ULL;
+        if (max_in) {
+            hi = max(hi, kmax_l);
+            inv = max(inv, ~kmax_l);
+        }
+        if (zero_in) inv = ~0ULL;  // the smallest key is 0
+        const unsigned long long lo = ~inv;
+        unsigned int* gq = gh + (size_t)q * kMaxBins;
+        if (hi == lo) {
+            // every candidate holds the same key: the k-th largest is decided
+            if (threadIdx.x == 0) {
+                sq->prefix = hi;
+                sq->mask = kAllKeyBits;
+                sq->krem = 1;
+            }
+        } else {
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) sh_hist[i] = __ldcg(gq + i);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (max_in) sh_hist[(kmax_l >> shift) & dmask] += (unsigned)cm;
+                if (zero_in) sh_hist[0] += (unsigned)cz;
+            }
+            __syncthreads();
+            int bin;
+            unsigned long long above;
+            pick_digit(sh_hist, nb, sq->krem, &bin, &above);
+            if (threadIdx.x == 0) {
+                sq->prefix = pre[q] | (unsigned long long)bin << shift;
+                sq->mask = msk[q] | (unsigned long long)dmask << shift;
+                sq->krem -= (long long)above;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) gq[i] = 0;
+        if (threadIdx.x == 0) {
+            mm[0] = 0;
+            mm[1] = 0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tickets[j] = 0;
+}
+
+// Exact sum of keys that share one binary exponent e (the bucket's): their
+// mantissas (with the implicit bit when e > 0) as integers, split at bit 32
+// so that neither half overflows for 2^31 values.
+struct MantSum {
+    unsigned long long hi, lo, cnt;
+};
+
+__device__ __forceinline__ unsigned long long mant_of(unsigned long long key) {
+    const unsigned long long e = key >> 52;
+    return (key & kMant) | (e ? (1ULL << 52) : 0ULL);
+}
+
+// Value of an exact mantissa sum for exponent field e: one rounding.
+__device__ __forceinline__ double mant_value(unsigned long long hi, unsigned long long lo, unsigned long long e) {
+    const unsigned long long th = hi + (lo >> 32), tl = lo & 0xffffffffULL;
+    const double t = fma((double)th, 4294967296.0, (double)tl);
+    return scalbn(t, (int)(e ? e : 1) - 1075);
+}
+
+// The tail, fused with the final reduction. Layers with candidate lists: the
+// candidates of each problem's bucket above its k-th largest key, summed as
+// integers (atomics on exact integers: any order gives the same bits).
+// Layers without: every value above the k-th largest key, summed in FP64 per
+// block in a fixed order (skipped when the k-th largest is the layer's
+// largest key). The last block of the grid reduces every problem in a fixed
+// order (one warp per problem) and writes mean, PML and TVaR.
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) tail_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+                                                        const SelState* __restrict__ st,
+                                                        const LayerState* __restrict__ ls,
+                                                        const unsigned long long* __restrict__ cand,
+                                                        const double* __restrict__ part_mean,
+                                                        const double* __restrict__ part_above,
+                                                        double* __restrict__ part_sum,
+                                                        unsigned long long* __restrict__ part_cnt,
+                                                        unsigned long long* __restrict__ int_acc,
+                                                        unsigned int* __restrict__ ticket, double* mean, double* pml,
+                                                        double* tvar, double* sum_out) {
+    __shared__ double sh_red[32];
+    __shared__ unsigned long long sh_red_u[32];
+    __shared__ bool sh_last;
+    const int j = blockIdx.y;
+    const int n_layers = gridDim.y;
+    const int nblk = gridDim.x;
+    const bool compact = ls[j].compact != 0;
+    const unsigned long long kmax_l = ls[j].kmax;
+    unsigned long long thr[NQ], b1[NQ];
+    bool live[NQ];
+    bool any_live = false;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
+        b1[q] = q < n_p ? st[j * n_p + q].b1 : 0ULL;
+        // nothing lies above the k-th largest key when it is the layer's largest
+        live[q] = q < n_p && !st[j * n_p + q].first_decided && (compact || thr[q] != kmax_l);
+        any_live = any_live || live[q];
+    }
+    if (compact) {
+        const unsigned long long* c = cand + ls[j].cand_off;
+        const int64_t len = any_live ? (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need) : 0;
+        unsigned long long mh[NQ], ml[NQ], mc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) mh[q] = ml[q] = mc[q] = 0;
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
+             i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+            unsigned long long kv[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+                kv[u] = i < len ? __ldcs(c + i) : 0ULL;  // 0: never above a k-th largest key
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const unsigned long long m = mant_of(kv[u]);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (live[q] && (kv[u] >> kShift1) == b1[q] && kv[u] > thr[q]) {
+                        mh[q] += m >> 32;
+                        ml[q] += m & 0xffffffffULL;
+                        mc[q] += 1;
+                    }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (!live[q]) continue;
+            const unsigned long long a = block_sum_u64(mh[q], sh_red_u);
+            const unsigned long long b = block_sum_u64(ml[q], sh_red_u);
+            const unsigned long long cc = block_sum_u64(mc[q], sh_red_u);
+            if (threadIdx.x == 0 && cc) {
+                unsigned long long* acc = int_acc + 3 * ((size_t)j * n_p + q);
+                atomicAdd(acc, a);
+                atomicAdd(acc + 1, b);
+                atomicAdd(acc + 2, cc);
+            }
+        }
+    } else {
+        const double* row = ylt + (size_t)j * (size_t)n;
+        const int64_t len = any_live ? n : 0;
+        double s[NQ];
+        unsigned long long cnt[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            s[q] = 0.0;
+            cnt[q] = 0;
+        }
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
+             i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+            double v[kUnroll];
+            bool valid[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+                valid[u] = i < len;
+                v[u] = valid[u] ? __ldcs(row + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;  // 0: never above
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (live[q] && key > thr[q]) {
+                        s[q] += v[u];
+                        cnt[q] += 1;
+                    }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (q >= n_p) break;
+            const double rs = block_sum(s[q], sh_red);
+            const unsigned long long rc = block_sum_u64(cnt[q], sh_red_u);
+            if (threadIdx.x == 0) {
+                const size_t w = ((size_t)j * n_p + q) * nblk + blockIdx.x;
+                part_sum[w] = rs;
+                part_cnt[w] = rc;
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = wib; i < n_layers * n_p; i += kThreads / 32) {
+        const int jj = i / n_p, q = i % n_p;
+        const SelState sq = st[i];
+        const bool cmp = __ldcg(&ls[jj].compact) != 0;
+        double m = 0.0, s = 0.0;
+        unsigned long long c = 0;
+        for (int b0 = 0; b0 < nblk; b0 += 32 * 8) {
+            // eight partials per lane requested at once, then summed in order
+            double pm[8], ps[8];
+            unsigned long long pc[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int b = b0 + r * 32 + lane;
+                const bool ok = b < nblk;
+                pm[r] = ok && q == 0 ? __ldcg(part_mean + (size_t)jj * nblk + b) : 0.0;
+                ps[r] = ok ? __ldcg((cmp ? part_above : part_sum) + (size_t)i * nblk + b) : 0.0;
+                pc[r] = ok && !cmp ? __ldcg(part_cnt + (size_t)i * nblk + b) : 0ULL;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                m += pm[r];
+                s += ps[r];
+                c += pc[r];
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_xor_sync(0xffffffffu, m, o);
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            if (q == 0 && mean) mean[jj] = m / (double)n;
+            if (q == 0 && sum_out) sum_out[jj] = m;
+            const double v = __longlong_as_double((long long)sq.prefix);
+            if (sq.first_decided) {
+                s = 0.0;  // a constant layer: nothing above its one key
+                c = 0;
+            } else if (cmp) {
+                // above the bucket (pass 2) plus the bucket's keys above the
+                // k-th largest: the listed ones and the counted largest key
+                const unsigned long long* acc = int_acc + 3 * (size_t)i;
+                unsigned long long mh = __ldcg(acc), ml = __ldcg(acc + 1), mc = __ldcg(acc + 2);
+                const unsigned long long kmx = __ldcg(&ls[jj].kmax), cm = __ldcg(&ls[jj].cnt_max);
+                if (cm && (kmx >> kShift1) == sq.b1 && kmx > sq.prefix) {
+                    const unsigned long long mk = mant_of(kmx);
+                    mh += cm * (mk >> 32);
+                    ml += cm * (mk & 0xffffffffULL);
+                    mc += cm;
+                }
+                if (mc) s += mant_value(mh, ml, sq.b1 >> 2);
+                c = (unsigned long long)sq.above1 + mc;
+            }
+            if (pml) pml[i] = v;
+            if (tvar) tvar[i] = (s + (double)(sq.k - (long long)c) * v) / (double)sq.k;
+        }
+    }
+    if (threadIdx.x == 0) *ticket = 0;
 }
 
 // Backward: counts of values above and equal to each PML, then the weights.
@@ -183,370 +828,16 @@ __global__ void __launch_bounds__(kThreads) grad_ylt_kernel(const double* __rest
     }
 }
 
-// Digit pick of one (layer, probability) problem by the whole block: the
-// digit where the count of keys from the top reaches the remaining rank;
-// extends the prefix, clears the problem's bins. Histogram reads bypass L1
-// (the bins were filled by other blocks' atomics).
-__device__ void select_block(SelState* __restrict__ st, unsigned int* __restrict__ h, int shift, int bits,
-                             bool first, long long k0) {
-    __shared__ unsigned int sh_bins[kMaxBins];
-    __shared__ unsigned long long sh_scan[kThreads];
-    __shared__ int sh_bin;
-    __shared__ unsigned long long sh_above;
-    const int nb = 1 << bits;
-    const int per = nb / kThreads > 0 ? nb / kThreads : 1;
-    const long long krem = first ? k0 : st->krem;
-    // every bin requested at once (8 per thread), then cleared for the next pass
-#pragma unroll
-    for (int r = 0; r < kMaxBins / kThreads; ++r) {
-        const int i = r * kThreads + threadIdx.x;
-        if (i < nb) sh_bins[i] = __ldcg(h + i);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
-    // thread i covers descending ranks [i*per, (i+1)*per): bins nb-1-i*per downwards
-    unsigned long long local = 0;
-    if (threadIdx.x * per < nb)
-        for (int r = 0; r < per; ++r) local += sh_bins[nb - 1 - (threadIdx.x * per + r)];
-    sh_scan[threadIdx.x] = local;
-    if (threadIdx.x == 0) sh_bin = -1;
-    __syncthreads();
-    for (int o = 1; o < kThreads; o <<= 1) {
-        const unsigned long long add = threadIdx.x >= (unsigned)o ? sh_scan[threadIdx.x - o] : 0ULL;
-        __syncthreads();
-        sh_scan[threadIdx.x] += add;
-        __syncthreads();
-    }
-    const unsigned long long incl = sh_scan[threadIdx.x];
-    const unsigned long long excl = incl - local;
-    if (threadIdx.x * per < nb && (long long)excl < krem && krem <= (long long)incl) {
-        unsigned long long run = excl;
-        for (int r = 0; r < per; ++r) {
-            const int bin = nb - 1 - (threadIdx.x * per + r);
-            const unsigned c = sh_bins[bin];
-            if ((long long)(run + c) >= krem) {
-                sh_bin = bin;
-                sh_above = run;
-                break;
-            }
-            run += c;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int bin = sh_bin < 0 ? 0 : sh_bin;  // unreachable when counts are consistent
-        const unsigned long long prefix = first ? 0ULL : st->prefix, mask = first ? 0ULL : st->mask;
-        st->prefix = prefix | (unsigned long long)bin << shift;
-        st->mask = mask | (unsigned long long)(nb - 1) << shift;
-        st->krem = krem - (long long)(sh_bin < 0 ? 0 : sh_above);
-        if (first) st->k = k0;
-    }
-    __syncthreads();
-}
-
-// One radix pass fused with its digit pick: grid (blocks_per_layer,
-// n_layers). Every block histograms its keys (as hist_kernel) and flushes
-// them with atomics; the last block of a layer to finish (a ticket counter,
-// after a fence: no block waits for another) picks the digits of the
-// layer's problems and resets the counter. The first pass matches every key
-// (it starts the state from k) and writes the blocks' partial sums (mean).
-template <int NQ>
-__global__ void __launch_bounds__(kThreads) hist_select_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
-                                                               SelState* __restrict__ st, int shift, int bits,
-                                                               bool first, const KParams kq,
-                                                               unsigned int* __restrict__ ghist,
-                                                               unsigned long long* __restrict__ minmax,
-                                                               double* __restrict__ part_sum,
-                                                               unsigned int* __restrict__ tickets) {
-    extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
-    __shared__ double sh_red[32];
-    __shared__ unsigned long long sh_red_u[32];
-    __shared__ bool sh_last;
-    const int nb = 1 << bits;
-    const int j = blockIdx.y;
-    unsigned long long pre[NQ], msk[NQ];
-    bool done[NQ];
-    bool all_done = true;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        pre[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].prefix) : 1ULL;  // unused slots never match
-        msk[q] = q < n_p ? (first ? 0ULL : st[j * n_p + q].mask) : 0ULL;
-        done[q] = q >= n_p || msk[q] == kAllKeyBits;  // decided by an earlier pass
-        all_done = all_done && done[q];
-    }
-    if (all_done) return;  // the same for every block of the layer: no ticket is taken
-    // problems with the same prefix and mask see the same candidates (every
-    // problem in the first pass; later, probabilities whose k-th largest
-    // keys share their leading digits): the first of them, the source,
-    // histograms for all
-    __shared__ int sh_src[kMaxProbs];
-    int src[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        src[q] = q;
-#pragma unroll
-        for (int r = NQ - 1; r >= 0; --r)
-            if (r < q && !done[r] && !done[q] && pre[r] == pre[q] && msk[r] == msk[q]) src[q] = r;
-        if (threadIdx.x == 0 && q < n_p) sh_src[q] = src[q];
-    }
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
-    // largest candidate key and largest complement (the smallest candidate)
-    unsigned long long kmax[NQ], kinv[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        kmax[q] = 0;
-        kinv[q] = 0;
-    }
-    __syncthreads();
-    const double* row = ylt + (size_t)j * (size_t)n;
-    double sum = 0.0;
-    const unsigned dmask = (unsigned)nb - 1u;
-    const unsigned lane = threadIdx.x & 31;
-    // kUnroll values per thread per step, their loads issued together
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
-         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-        double v[kUnroll];
-        bool valid[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-            valid[u] = i < n;
-            v[u] = valid[u] ? row[i] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            if (first) sum += v[u];
-            const unsigned long long key = key_of(v[u]);
-            const unsigned dig = (unsigned)(key >> shift) & dmask;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                if (q < n_p && !done[q] && src[q] == q) {  // the same for the whole block
-                    const bool hit = valid[u] && (key & msk[q]) == pre[q];
-                    // after the first pass few warps hold a candidate at all
-                    if (first || __any_sync(0xffffffffu, hit)) {
-                        // lanes with the same digit add once (losses cluster:
-                        // many trials share a value, such as a capped layer's AggL)
-                        const unsigned peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
-                        if (hit && lane == (unsigned)(__ffs(peers) - 1))
-                            atomicAdd(&sh_hist[q * nb + dig], __popc(peers));
-                        if (hit) {
-                            kmax[q] = max(kmax[q], key);
-                            kinv[q] = max(kinv[q], ~key);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    if (first) {
-        const double r = block_sum(sum, sh_red);
-        if (threadIdx.x == 0) part_sum[(size_t)j * gridDim.x + blockIdx.x] = r;
-    }
-    // a problem that shares its source's candidates shares its extremes
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-#pragma unroll
-        for (int r = 0; r < NQ; ++r)
-            if (r < q && src[q] == r) {
-                kmax[q] = kmax[r];
-                kinv[q] = kinv[r];
-            }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        if (q >= n_p || done[q]) continue;
-        const unsigned long long a = block_max_u64(kmax[q], sh_red_u);
-        const unsigned long long b = block_max_u64(kinv[q], sh_red_u);
-        if (threadIdx.x == 0) {
-            atomicMax(&minmax[2 * ((size_t)j * n_p + q)], a);
-            atomicMax(&minmax[2 * ((size_t)j * n_p + q) + 1], b);
-        }
-    }
-    __syncthreads();
-    unsigned int* gh = ghist + ((size_t)j * n_p) * kMaxBins;
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
-        const int q = i >> bits, b = i & (int)dmask;
-        const unsigned c = sh_hist[sh_src[q] * nb + b];  // zero for a decided problem
-        if (c) atomicAdd(&gh[(size_t)q * kMaxBins + b], c);
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sh_last = atomicAdd(&tickets[j], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-    for (int q = 0; q < n_p; ++q) {
-        if (done[q]) continue;
-        SelState* sq = &st[j * n_p + q];
-        unsigned long long* mm = &minmax[2 * ((size_t)j * n_p + q)];
-        const unsigned long long hi = __ldcg(mm), lo = ~__ldcg(mm + 1);
-        if (hi == lo) {
-            // every candidate holds the same key (a capped layer's AggL, say):
-            // the k-th largest is decided without the remaining digits
-            if (threadIdx.x == 0) {
-                sq->prefix = hi;
-                sq->mask = kAllKeyBits;
-                sq->krem = 1;
-                if (first) sq->k = kq.k[q];
-            }
-            for (int i = threadIdx.x; i < nb; i += blockDim.x) gh[(size_t)q * kMaxBins + i] = 0;
-        } else {
-            select_block(sq, gh + (size_t)q * kMaxBins, shift, bits, first, kq.k[q]);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            mm[0] = 0;
-            mm[1] = 0;
-        }
-    }
-    if (threadIdx.x == 0) tickets[j] = 0;
-}
-
-// The tail sums fused with the final reduction: every block writes its
-// partial count and sum of values strictly above each problem's k-th key;
-// the last block of the grid (ticket counter) sums the partials of every
-// problem in a fixed order (one warp per problem) and writes mean, PML and
-// TVaR.
-template <int NQ>
-__global__ void __launch_bounds__(kThreads) tail_final_kernel(const double* __restrict__ ylt, int64_t n, int n_layers,
-                                                              int n_p, const SelState* __restrict__ st,
-                                                              const double* __restrict__ mean_part,
-                                                              unsigned long long* __restrict__ part_cnt,
-                                                              double* __restrict__ part_sum,
-                                                              unsigned int* __restrict__ ticket, double* mean,
-                                                              double* pml, double* tvar) {
-    __shared__ double sh_red[32];
-    __shared__ unsigned long long sh_red_u[32];
-    __shared__ bool sh_last;
-    const int j = blockIdx.y;
-    const int nblk = gridDim.x;
-    unsigned long long thr[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
-    const double* row = ylt + (size_t)j * (size_t)n;
-    double s[NQ];
-    unsigned long long c[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        s[q] = 0.0;
-        c[q] = 0;
-    }
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
-         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-        double v[kUnroll];
-        bool valid[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-            valid[u] = i < n;
-            v[u] = valid[u] ? row[i] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;  // 0: never above a threshold
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-                if (q < n_p && key > thr[q]) {
-                    s[q] += v[u];
-                    c[q] += 1;
-                }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        if (q >= n_p) break;
-        const double rs = block_sum(s[q], sh_red);
-        const unsigned long long rc = block_sum_u64(c[q], sh_red_u);
-        if (threadIdx.x == 0) {
-            const size_t w = ((size_t)j * n_p + q) * nblk + blockIdx.x;
-            part_sum[w] = rs;
-            part_cnt[w] = rc;
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sh_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int i = wib; i < n_layers * n_p; i += kThreads / 32) {
-        const int jj = i / n_p, q = i % n_p;
-        double m = 0.0, sgt = 0.0;
-        unsigned long long cgt = 0;
-        for (int b0 = 0; b0 < nblk; b0 += 32 * 8) {
-            // eight partials per lane requested at once, then summed in order
-            double pm[8], ps[8];
-            unsigned long long pc[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int b = b0 + r * 32 + lane;
-                const bool ok = b < nblk;
-                pm[r] = ok && q == 0 ? __ldcg(mean_part + (size_t)jj * nblk + b) : 0.0;
-                ps[r] = ok ? __ldcg(part_sum + (size_t)i * nblk + b) : 0.0;
-                pc[r] = ok ? __ldcg(part_cnt + (size_t)i * nblk + b) : 0ULL;
-            }
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                m += pm[r];
-                sgt += ps[r];
-                cgt += pc[r];
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            m += __shfl_xor_sync(0xffffffffu, m, o);
-            sgt += __shfl_xor_sync(0xffffffffu, sgt, o);
-            cgt += __shfl_xor_sync(0xffffffffu, cgt, o);
-        }
-        if (lane == 0) {
-            if (q == 0 && mean) mean[jj] = m / (double)n;
-            const double v = __longlong_as_double((long long)__ldcg(&st[i].prefix));
-            const long long k = __ldcg(&st[i].k);
-            if (pml) pml[i] = v;
-            if (tvar) tvar[i] = (sgt + (double)(k - (long long)cgt) * v) / (double)k;
-        }
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-}
-
-// The metric kernels over caller-provided scratch: six fused radix passes,
-// then the fused tail and final reduction (seven launches). hist and the
-// tickets (contiguous, n_layers + 1 counters after the bins) must be zero.
-cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers, int32_t n_p, const KParams& kq,
-                                  int nblk, SelState* st, unsigned int* hist, unsigned long long* minmax,
-                                  unsigned int* tickets, double* msum, unsigned long long* tcnt, double* tsum,
-                                  double* mean, double* pml, double* tvar, cudaStream_t s) {
-    // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
-    auto hist_k = n_p <= 1 ? hist_select_kernel<1> : n_p <= 2 ? hist_select_kernel<2>
-                : n_p <= 4 ? hist_select_kernel<4> : hist_select_kernel<8>;
-    auto tail_k = n_p <= 1 ? tail_final_kernel<1> : n_p <= 2 ? tail_final_kernel<2>
-                : n_p <= 4 ? tail_final_kernel<4> : tail_final_kernel<8>;
-    cudaError_t err = cudaSuccess;
-    for (int i = 0; i < kPasses && !err; ++i) {
-        const int bits = pass_bits(i);
-        const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
-        if (shm > 48 * 1024 && (err = cudaFuncSetAttribute(hist_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
-            break;
-        hist_k<<<dim3(nblk, n_layers), kThreads, shm, s>>>(ylt, n, n_p, st, pass_shift(i), bits, i == 0, kq, hist,
-                                                           minmax, msum, tickets);
-        err = cudaGetLastError();
-    }
-    if (err) return err;
-    tail_k<<<dim3(nblk, n_layers), kThreads, 0, s>>>(ylt, n, n_layers, n_p, st, msum, tcnt, tsum, tickets + n_layers,
-                                                     mean, pml, tvar);
-    return cudaGetLastError();
-}
-
 int blocks_per_layer(int64_t n, int n_layers) {
     int dev = 0, sms = 148, l2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    // about 16 values per thread (4 steps of kUnroll)
-    int64_t want = (n + (int64_t)kThreads * 16 - 1) / ((int64_t)kThreads * 16);
-    // a YLT larger than L2 streams from HBM in every pass, and more blocks
-    // keep more of its loads in flight (8 per SM); one that L2 holds is
-    // re-read from L2, where each block's fixed cost (clearing, flushing
+    // about 32 values per thread (4 steps of kUnroll)
+    int64_t want = (n + (int64_t)kThreads * 32 - 1) / ((int64_t)kThreads * 32);
+    // a YLT larger than L2 streams from HBM in the two full passes, and more
+    // blocks keep more of its loads in flight (8 per SM); one that L2 holds
+    // is re-read from L2, where each block's fixed cost (clearing, flushing
     // and ticketing its histograms) weighs more (4 per SM)
     const bool streamed = (double)n * (double)n_layers * sizeof(double) > (double)l2;
     const int64_t per_sm = streamed ? 8 : 4;
@@ -555,6 +846,87 @@ int blocks_per_layer(int64_t n, int n_layers) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch of one metrics call, in bytes from its start. The region [zero,
+// zero + zero_bytes) must be zero when the call starts; the rest is written
+// before it is read. The candidate lists take cand_slots 8-byte keys.
+struct MetricsLayout {
+    size_t st, ls, hist1, hist, minmax, tickets, above, iacc, pmean, psum, pcnt, cand;
+    size_t zero, zero_bytes, total;
+};
+
+MetricsLayout metrics_layout(int64_t n, int32_t n_layers, int32_t n_p, int nblk, uint64_t cand_slots) {
+    (void)n;
+    const size_t L = (size_t)n_layers, np = (size_t)n_layers * n_p, nb = (size_t)nblk;
+    MetricsLayout m{};
+    m.st = 0;
+    m.ls = align256(m.st + sizeof(SelState) * np);
+    m.hist1 = align256(m.ls + sizeof(LayerState) * L);
+    m.hist = align256(m.hist1 + sizeof(unsigned int) * kBins1 * L);
+    m.minmax = align256(m.hist + sizeof(unsigned int) * kMaxBins * np);
+    m.tickets = align256(m.minmax + sizeof(unsigned long long) * 2 * np);
+    m.above = align256(m.tickets + sizeof(unsigned int) * (L + 2));
+    m.iacc = align256(m.above + sizeof(double) * np * nb);
+    m.pmean = align256(m.iacc + sizeof(unsigned long long) * 3 * np);
+    m.zero = m.ls;
+    m.zero_bytes = m.pmean - m.ls;
+    m.psum = align256(m.pmean + sizeof(double) * L * nb);
+    m.pcnt = align256(m.psum + sizeof(double) * np * nb);
+    m.cand = align256(m.pcnt + sizeof(unsigned long long) * np * nb);
+    m.total = align256(m.cand + sizeof(unsigned long long) * (size_t)cand_slots);
+    return m;
+}
+
+// Candidate slots the allocating path reserves: an eighth of the YLT (the
+// buckets the problems select hold a few percent of a layer's trials once 0
+// and the layer's largest key are left out), at least 65,536, at most the
+// whole YLT.
+uint64_t default_cand_slots(int64_t n, int32_t n_layers) {
+    const uint64_t all = (uint64_t)n * (uint64_t)n_layers;
+    return std::min<uint64_t>(all, std::max<uint64_t>(all / 8, 65536));
+}
+
+// The metric kernels over a caller's scratch laid out by metrics_layout:
+// clear, pass 1, passes 2-6, tail with the final reduction (eight steps on
+// the stream, seven of them launches).
+cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers, int32_t n_p, const KParams& kq,
+                                  int nblk, char* w, const MetricsLayout& m, uint64_t cand_slots, double* mean,
+                                  double* pml, double* tvar, double* sum_out, cudaStream_t s) {
+    auto* st = (SelState*)(w + m.st);
+    auto* ls = (LayerState*)(w + m.ls);
+    auto* hist1 = (unsigned int*)(w + m.hist1);
+    auto* hist = (unsigned int*)(w + m.hist);
+    auto* minmax = (unsigned long long*)(w + m.minmax);
+    auto* tickets = (unsigned int*)(w + m.tickets);
+    auto* above = (double*)(w + m.above);
+    auto* iacc = (unsigned long long*)(w + m.iacc);
+    auto* pmean = (double*)(w + m.pmean);
+    auto* psum = (double*)(w + m.psum);
+    auto* pcnt = (unsigned long long*)(w + m.pcnt);
+    auto* cand = (unsigned long long*)(w + m.cand);
+    cudaError_t err = cudaMemsetAsync(w + m.zero, 0, m.zero_bytes, s);
+    if (err) return err;
+    const dim3 grid(nblk, n_layers);
+    first_pass_kernel<<<grid, kThreads, sizeof(unsigned int) * kBins1, s>>>(ylt, n, n_p, kq, st, ls, hist1, pmean,
+                                                                            tickets, cand_slots);
+    if ((err = cudaGetLastError())) return err;
+    // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
+    auto pass_k = n_p <= 1 ? pass_kernel<1> : n_p <= 2 ? pass_kernel<2> : n_p <= 4 ? pass_kernel<4> : pass_kernel<8>;
+    auto tail_k = n_p <= 1 ? tail_kernel<1> : n_p <= 2 ? tail_kernel<2> : n_p <= 4 ? tail_kernel<4> : tail_kernel<8>;
+    for (int i = 1; i < kPasses; ++i) {
+        const int bits = pass_bits(i);
+        const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
+        if (shm > 48 * 1024 &&
+            (err = cudaFuncSetAttribute(pass_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
+            return err;
+        pass_k<<<grid, kThreads, shm, s>>>(ylt, n, n_p, st, ls, cand, pass_shift(i), bits, i == 1, hist, minmax,
+                                           above, tickets);
+        if ((err = cudaGetLastError())) return err;
+    }
+    tail_k<<<grid, kThreads, 0, s>>>(ylt, n, n_p, st, ls, cand, pmean, above, psum, pcnt, iacc,
+                                     tickets + n_layers + 1, mean, pml, tvar, sum_out);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -566,37 +938,26 @@ int64_t tail_count(double p, int64_t n) {
     return std::min<int64_t>(n, std::max<int64_t>(1, k));
 }
 
-cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
-                        double* mean, double* pml, double* tvar, cudaStream_t s) {
+cudaError_t metrics_run_k(const double* ylt, int64_t n, int32_t n_layers, const int64_t* k, int32_t n_p,
+                          double* mean, double* pml, double* tvar, double* sum_out, cudaStream_t s) {
     const int nblk = blocks_per_layer(n, n_layers);
-    const int n_prob = n_layers * n_p;
-    // scratch: state, histograms and tickets (zeroed together), partial sums
-    const size_t o_st = 0;
-    const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
-    // bins, then per problem the candidates' largest key and complement, then
-    // the tickets: zeroed together
-    const size_t hist_bytes = sizeof(unsigned int) * kMaxBins * (size_t)n_prob +
-                              sizeof(unsigned long long) * 2 * (size_t)n_prob + sizeof(unsigned int) * (n_layers + 1);
-    const size_t o_ms = align256(o_h + hist_bytes);
-    const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
-    const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
-    const size_t total = align256(o_ts + sizeof(double) * (size_t)n_prob * nblk);
+    const uint64_t slots = default_cand_slots(n, n_layers);
+    const MetricsLayout m = metrics_layout(n, n_layers, n_p, nblk, slots);
     char* w = nullptr;
-    cudaError_t err = cudaMallocAsync((void**)&w, total, s);
+    cudaError_t err = cudaMallocAsync((void**)&w, m.total, s);
     if (err != cudaSuccess) return err;
     KParams kq = {};
-    for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs[q], n);
-    auto* hist = (unsigned int*)(w + o_h);
-    err = cudaMemsetAsync(hist, 0, hist_bytes, s);
-    if (!err)
-        err = launch_metric_kernels(ylt, n, n_layers, n_p, kq, nblk, (SelState*)(w + o_st), hist,
-                                    (unsigned long long*)(hist + kMaxBins * (size_t)n_prob),
-                                    (unsigned int*)((unsigned long long*)(hist + kMaxBins * (size_t)n_prob) +
-                                                    2 * (size_t)n_prob),
-                                    (double*)(w + o_ms),
-                                    (unsigned long long*)(w + o_tc), (double*)(w + o_ts), mean, pml, tvar, s);
+    for (int q = 0; q < n_p; ++q) kq.k[q] = std::min<int64_t>(n, std::max<int64_t>(1, k[q]));
+    err = launch_metric_kernels(ylt, n, n_layers, n_p, kq, nblk, w, m, slots, mean, pml, tvar, sum_out, s);
     const cudaError_t e2 = cudaFreeAsync(w, s);
     return err ? err : e2;
+}
+
+cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
+                        double* mean, double* pml, double* tvar, cudaStream_t s) {
+    int64_t k[kMaxProbs];
+    for (int q = 0; q < n_p; ++q) k[q] = tail_count(probs[q], n);
+    return metrics_run_k(ylt, n, n_layers, k, n_p, mean, pml, tvar, nullptr, s);
 }
 
 cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
@@ -644,7 +1005,7 @@ cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers,
 // library defines at file scope, for callers that cannot allocate device
 // memory (see include/art.h). The array lives in every device's copy of this
 // module; host code never dereferences its name, it asks the runtime for the
-// device address once per device.
+// device address of the current device's copy.
 #include <mutex>
 
 namespace art {
@@ -655,23 +1016,64 @@ namespace {
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up on
-// the first call per device (with that device current) and cached.
+struct NoAllocAddr {
+    unsigned char* addr = nullptr;
+    unsigned long long ctx_id = 0;  // the context the address belongs to
+};
+NoAllocAddr g_noalloc[kNoAllocMaxDevices];
+
+// Id of the current device's context (unique over the process's life, so a
+// context recreated after cudaDeviceReset gets a new one); 0 if the driver
+// cannot tell. Taken from the driver through the runtime's entry-point
+// lookup, without linking the driver library.
+unsigned long long current_context_id() {
+    typedef int (*GetCurrent)(void**);
+    typedef int (*GetId)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device: looked up with
+// the device current on the first call, and again whenever the device's
+// context has changed since (cudaDeviceReset, or a reset of the primary
+// context by another framework, recreates the module and its array), or
+// whenever the context cannot be identified.
 cudaError_t noalloc_scratch(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_metrics_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+    NoAllocAddr& a = g_noalloc[dev];
+    const unsigned long long ctx = current_context_id();
+    if (a.addr && ctx != 0 && a.ctx_id == ctx) {
+        *out = a.addr;
+        return cudaSuccess;
     }
-    *out = g_noalloc_addr[dev];
+    // the lookup makes the device's primary context current if it was not
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_metrics_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    a.addr = static_cast<unsigned char*>(ptr);
+    a.ctx_id = current_context_id();
+    *out = a.addr;
     return cudaSuccess;
 }
 
@@ -688,18 +1090,14 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     for (int q = 0; q < n_p; ++q)
         if (!(probs_host[q] > 0.0 && probs_host[q] < 1.0)) return ART_EINVAL;
     const int nblk = blocks_per_layer(n_trials, n_layers);
-    const int n_prob = n_layers * n_p;
-    const size_t o_st = 0;
-    const size_t o_h = align256(o_st + sizeof(SelState) * n_prob);
-    // bins, then per problem the candidates' largest key and complement, then
-    // the tickets: zeroed together
-    const size_t hist_bytes = sizeof(unsigned int) * kMaxBins * (size_t)n_prob +
-                              sizeof(unsigned long long) * 2 * (size_t)n_prob + sizeof(unsigned int) * (n_layers + 1);
-    const size_t o_ms = align256(o_h + hist_bytes);
-    const size_t o_tc = align256(o_ms + sizeof(double) * (size_t)n_layers * nblk);
-    const size_t o_ts = align256(o_tc + sizeof(unsigned long long) * (size_t)n_prob * nblk);
-    const size_t total = align256(o_ts + sizeof(double) * (size_t)n_prob * nblk);
-    if (total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
+    // the fixed part must fit; what is left holds candidate lists (layers
+    // whose lists do not fit read their whole row in every pass instead)
+    const MetricsLayout fixed = metrics_layout(n_trials, n_layers, n_p, nblk, 0);
+    if (fixed.total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
+    const uint64_t slots = std::min<uint64_t>(((size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES - fixed.total) / 8,
+                                              default_cand_slots(n_trials, n_layers));
+    const MetricsLayout m = metrics_layout(n_trials, n_layers, n_p, nblk, slots);
+    if (m.total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
     unsigned char* w = nullptr;
     cudaError_t err = noalloc_scratch(&w);
     if (err != cudaSuccess) {
@@ -708,18 +1106,10 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     }
     KParams kq = {};
     for (int q = 0; q < n_p; ++q) kq.k[q] = tail_count(probs_host[q], n_trials);
-    auto* hist = (unsigned int*)(w + o_h);
-    // the scratch keeps the previous call's contents: the histograms and the
-    // tickets must start at zero
-    err = cudaMemsetAsync(hist, 0, hist_bytes, stream);
-    if (!err)
-        err = launch_metric_kernels(ylt_dev, n_trials, n_layers, n_p, kq, nblk, (SelState*)(w + o_st), hist,
-                                    (unsigned long long*)(hist + kMaxBins * (size_t)n_prob),
-                                    (unsigned int*)((unsigned long long*)(hist + kMaxBins * (size_t)n_prob) +
-                                                    2 * (size_t)n_prob),
-                                    (double*)(w + o_ms),
-                                    (unsigned long long*)(w + o_tc), (double*)(w + o_ts), mean_dev, pml_dev,
-                                    tvar_dev, stream);
+    // the scratch keeps the previous call's contents: the launcher clears
+    // what must start at zero
+    err = launch_metric_kernels(ylt_dev, n_trials, n_layers, n_p, kq, nblk, reinterpret_cast<char*>(w), m, slots,
+                                mean_dev, pml_dev, tvar_dev, nullptr, stream);
     if (err != cudaSuccess) {
         set_last_error(err);
         return ART_ECUDA;

@@ -189,13 +189,19 @@ def _portfolio(catalogue, tables, mult, ded, lim, layer_lists, occ_ret, occ_lim,
                      agg_ret=np.asarray(agg_ret, dtype=np.float64), agg_lim=np.asarray(agg_lim, dtype=np.float64))
 
 
-def make(name: str, n_trials: Optional[int] = None, with_timestamps: bool = False) -> Workload:
+def make(name: str, n_trials: Optional[int] = None, with_timestamps: bool = False, shard: int = 0) -> Workload:
     """Build a named workload (c0, c0u, c1, c1u, c2, c3, c4); n_trials, when
-    given, keeps the first n_trials trials of the full YET."""
+    given, keeps the first n_trials trials of the full YET. shard s > 0 draws
+    the YET (and its timestamps) from stream 3 + s instead: the same
+    portfolio with another YET of the same recipe, one per GPU of a run that
+    splits its trials between GPUs (shard 0 is the workload itself)."""
     base = name.rstrip("u")
     cfg = int(base[1:])
     seed = SEED_BASE + cfg
-    r_elt, r_layer, r_yet, r_ts = _streams(seed, 4)
+    streams = _streams(seed, 4 + max(0, int(shard)))
+    r_elt, r_layer, r_yet, r_ts = streams[:4]
+    if shard > 0:
+        r_yet = r_ts = streams[3 + shard]
     probs = np.array([0.99])
 
     if base in ("c0", "c1", "c3"):

@@ -112,3 +112,14 @@ def test_traffic_comes_from_a_json_record_of_the_current_sources(tmp_path):
     (tmp_path / "ylt_skip_c1.json").write_text(json.dumps(dict(rec, source_hash="0" * 16)))
     assert bench.recorded_traffic("ylt_skip", "c1", str(tmp_path)) is None  # stale sources
     assert bench.recorded_traffic("ylt_plain", "c1", str(tmp_path)) is None  # no record
+
+
+def test_first_layers_keeps_a_consistent_prefix_of_the_portfolio():
+    w = workloads.make("c0u", n_trials=20)
+    big = workloads.random_case(903, n_elt=12, n_layers=9, n_trials=5)
+    sub = bench.first_layers(big, 4).portfolio
+    port = big.portfolio
+    assert sub.n_layers == 4 and sub.layer_elt_off[-1] == sub.layer_elt_ids.size
+    assert np.array_equal(sub.layer_elt_ids, port.layer_elt_ids[:port.layer_elt_off[4]])
+    assert np.array_equal(sub.agg_lim, port.agg_lim[:4]) and sub.elt_losses is port.elt_losses
+    assert bench.first_layers(w, 5).portfolio.n_layers == 1  # at most the layers there are

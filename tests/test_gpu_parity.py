@@ -122,6 +122,18 @@ def test_config1_sampled_plain_and_batched(c1u):
         assert torch.all(ylt >= 0) and torch.all(ylt <= w.portfolio.agg_lim[0])
 
 
+def test_config1_full_ylt_against_oracle(c1u):
+    """Every one of the 1,000,000 trials of the paper-scale one-layer
+    workload (unsaturated terms): the skip variant the bench times and the
+    plain one-layer-per-launch variant, element by element against the FP64
+    oracle (about 1.6e10 lookups on the host cores)."""
+    w, p, yet = c1u
+    ref, gross, _ = oracle.ylt(w.oracle_problem())
+    for v in (art.ART_VARIANT_SKIP, art.ART_VARIANT_PLAIN):
+        ylt, _ = run_ylt(p, w, v, yet=yet)
+        assert_ylt_close(ylt.cpu().numpy(), ref, gross, f"c1u variant {v}, all trials")
+
+
 def test_config1_metrics_against_oracle_on_same_ylt(c1u):
     """The metrics kernels against the oracle's full-sort metrics on the same
     (GPU) YLT: the k-th largest is selected exactly."""
@@ -336,7 +348,7 @@ def test_update_terms_and_rounding():
         p.close()
 
 
-@pytest.mark.parametrize("name,n_sample", [("c2", 400), ("c4", 250)])
+@pytest.mark.parametrize("name,n_sample", [("c2", 5000), ("c4", 5000)])
 def test_multilayer_workloads_sampled(name, n_sample):
     """The batching (CSR, 64 layers over a 256-ELT pool) and precision
     (128 layers over a 512-ELT pool) workloads at full size: every variant,

@@ -119,3 +119,22 @@ def test_pool_workloads_spread_over_the_aggregate_branches(name):
     zero, mid, cap, _ = _branches(name, 300)
     assert 0.15 < zero.mean() < 0.4 and 0.15 < cap.mean() < 0.4 and mid.mean() > 0.35
     assert (mid >= 0.1).mean() > 0.45
+
+
+def test_shards_share_the_portfolio_and_draw_their_own_yet():
+    """shard 0 is the workload itself; shard s > 0 keeps the portfolio and
+    draws another YET of the same recipe, reproducibly."""
+    a = workloads.make("c0u", n_trials=300)
+    b = workloads.make("c0u", n_trials=300, shard=0)
+    c = workloads.make("c0u", n_trials=300, shard=1)
+    c2 = workloads.make("c0u", n_trials=300, shard=1)
+    d = workloads.make("c0u", n_trials=300, shard=2)
+    assert np.array_equal(a.yet.event_ids, b.yet.event_ids)
+    assert np.array_equal(c.yet.event_ids, c2.yet.event_ids)
+    assert not np.array_equal(a.yet.event_ids, c.yet.event_ids)
+    assert not np.array_equal(c.yet.event_ids, d.yet.event_ids)
+    for w in (c, d):
+        assert np.array_equal(w.portfolio.elt_losses, a.portfolio.elt_losses)
+        assert np.array_equal(w.portfolio.agg_ret, a.portfolio.agg_ret)
+        assert w.yet.event_ids.shape == a.yet.event_ids.shape
+        assert w.yet.event_ids.min() >= 0 and w.yet.event_ids.max() < a.portfolio.catalogue_size

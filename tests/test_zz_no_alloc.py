@@ -1,4 +1,4 @@
-"""art_metrics_noalloc against art_metrics.
+"""art_metrics_noalloc against art_metrics and against the FP64 oracle.
 
 art_metrics_noalloc serves callers that cannot allocate device memory while
 they run (a fixed memory budget reserved at start-up, a device allocator
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1308_2572_gb300 import art
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,11 @@ def test_noalloc_metrics_match_allocating_entry_point_on_two_calls_in_a_row():
         np.testing.assert_array_equal(got[1], ref[1])            # the k-th largest is selected exactly
         np.testing.assert_allclose(got[2], ref[2], rtol=1e-12)    # TVaR
         np.testing.assert_allclose(got[0], ref[0], rtol=1e-12)    # mean
+        # and against the oracle's full sort of the same table
+        om, op, ot = oracle.metrics(y.cpu().numpy(), p)
+        np.testing.assert_array_equal(got[1], op)
+        np.testing.assert_allclose(got[2], ot, rtol=1e-12)
+        np.testing.assert_allclose(got[0], om, rtol=1e-12)
 
 
 def test_noalloc_metrics_reject_requests_beyond_the_static_scratch():
