@@ -258,9 +258,10 @@ ART_API art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const in
  *                host outputs, each may be NULL.
  * Limits: those of art_run_ylt_host and of art_metrics (1 <= T <= 2^31 - 1,
  * n_layers <= 65535). The portfolio owns a device array for the whole YLT
- * ([n_layers][T] FP64, grown on demand, freed with the portfolio) besides
- * the staging buffers; the metrics' scratch comes from the stream-ordered
- * allocator. Blocks until the results are in host memory. Results equal
+ * ([n_layers][T] FP64) and the metrics' scratch besides the staging buffers,
+ * grown on demand and freed with the portfolio, so that repeated calls of
+ * the same size allocate nothing. Blocks until the results are in host
+ * memory. Results equal
  * art_run_ylt followed by art_metrics. Errors: ART_EINVAL, ART_EUNSUPPORTED,
  * ART_ECUDA (including a failed allocation).
  */

@@ -509,6 +509,7 @@ void free_portfolio(art_portfolio* p) {
     }
     cudaFree(p->host_ylt);
     cudaFree(p->host_out);
+    cudaFree(p->host_scratch);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     delete p;
@@ -979,13 +980,24 @@ art_status art_run_ylt_host_metrics(art_portfolio* p, int64_t n_trials, const in
         p->host_ylt_cap = need_ylt;
         p->host_out_cap = need_out;
     }
+    // the metrics' scratch too, so that repeated calls allocate nothing
+    const size_t need_scratch = metrics_scratch_bytes(n_trials, (int32_t)L, n_p);
+    if (need_scratch > p->host_scratch_cap) {
+        cudaStreamSynchronize(stream);
+        cudaFree(p->host_scratch);
+        p->host_scratch = nullptr;
+        p->host_scratch_cap = 0;
+        if ((e = cudaMalloc(&p->host_scratch, need_scratch))) return fail(e);
+        p->host_scratch_cap = need_scratch;
+    }
     // chunks of the YET through the forward; the YLT stays on the device too
     st = host_run(p, n_trials, event_ids_host, trial_off_host, events_per_trial, ylt_host, p->host_ylt, stream);
     if (st) return st;
     double* d_mean = p->host_out;
     double* d_pml = d_mean + L;
     double* d_tvar = d_pml + L * n_p;
-    if ((e = metrics_run(p->host_ylt, n_trials, (int32_t)L, probs_host, n_p, d_mean, d_pml, d_tvar, stream)))
+    if ((e = metrics_run(p->host_ylt, n_trials, (int32_t)L, probs_host, n_p, d_mean, d_pml, d_tvar, stream,
+                         p->host_scratch, p->host_scratch_cap)))
         return fail(e);
     if (mean_host && (e = cudaMemcpyAsync(mean_host, d_mean, sizeof(double) * L, cudaMemcpyDeviceToHost, stream)))
         return fail(e);

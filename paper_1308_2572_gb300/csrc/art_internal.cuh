@@ -269,6 +269,8 @@ struct art_portfolio {
     double* host_ylt = nullptr;
     double* host_out = nullptr;
     int64_t host_ylt_cap = 0, host_out_cap = 0;
+    void* host_scratch = nullptr;  // the metrics' scratch of that path
+    size_t host_scratch_cap = 0;
 
     // cached graph of one batched launch
     cudaGraphExec_t graph_exec = nullptr;
@@ -299,12 +301,18 @@ cudaError_t launch_adjoint(art_portfolio* p, const YetArgs& y, const uint8_t* br
                            double* grad_terms, double* grad_mult, cudaStream_t s);
 cudaError_t launch_adjoint_groups(art_portfolio* p, const YetArgs& y, const uint8_t* branch, const double* g,
                                   double* grad_terms, double* grad_mult, cudaStream_t s);
+// The metrics over scratch of at least metrics_scratch_bytes(...) bytes
+// (scratch NULL or smaller: taken from the stream-ordered allocator and
+// released on the stream).
 cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
-                        double* mean, double* pml, double* tvar, cudaStream_t s);
+                        double* mean, double* pml, double* tvar, cudaStream_t s, void* scratch = nullptr,
+                        size_t scratch_bytes = 0);
 // The same with the ranks k given (clamped to [1, n]) instead of
 // probabilities; sum_out (may be NULL) receives each layer's FP64 loss sum.
 cudaError_t metrics_run_k(const double* ylt, int64_t n, int32_t n_layers, const int64_t* k, int32_t n_p,
-                          double* mean, double* pml, double* tvar, double* sum_out, cudaStream_t s);
+                          double* mean, double* pml, double* tvar, double* sum_out, cudaStream_t s,
+                          void* scratch = nullptr, size_t scratch_bytes = 0);
+size_t metrics_scratch_bytes(int64_t n, int32_t n_layers, int32_t n_p);
 cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs,
                                  int32_t n_p, const double* pml, const double* gmean, const double* gtvar,
                                  double* gylt, cudaStream_t s);

@@ -11,28 +11,34 @@
 // every (layer, probability) problem at once, the prefix of the k-th largest
 // key: a first digit of 13 bits (the binary exponent and two leading mantissa
 // bits), then digits of 11, 11, 11, 11 and 6 bits. Each pass is one launch:
-// its blocks histogram the keys that match the prefix found so far
-// (shared-memory histograms with warp-aggregated atomics, flushed to global
-// with atomics), and the last block of each layer to finish (a ticket counter
-// after a fence; no block waits for another) picks the digit where the count
-// from the top crosses the remaining rank. A problem whose candidates all
-// hold one key is decided at once.
+// its blocks histogram the keys that match the prefix found so far, and the
+// last block of each layer to finish (a ticket counter after a fence; no
+// block waits for another) picks the digit where the count from the top
+// crosses the remaining rank. A problem whose candidates all hold one key is
+// decided at once.
 //
-// Only the first two passes read the whole YLT. The first also sums each
-// layer for the mean and records its smallest and largest key; its last block
-// lays out, per layer, a candidate list as long as the first-digit buckets
-// its problems selected (while the lists fit the scratch). The second pass
-// copies into that list every key of those buckets other than 0 and the
-// layer's largest key -- the two values that repeat most (trials without a
-// loss, trials at the aggregate cap), which are only counted -- and sums, in
-// a fixed order, the values above each problem's bucket. The remaining
-// passes and the tail read the candidate list alone, adding the counted keys
-// to the histograms where they match. The tail sums the candidates above the
-// k-th largest key of the problem's bucket as integers: they share one binary
-// exponent, so their mantissas add exactly and in any order. TVaR is
-// (sum_gt + (k - count_gt) PML) / k. A layer whose candidates do not fit
-// keeps reading its whole row in every pass, and its tail sums in a fixed
-// order. Every sum is deterministic.
+// Only the first two passes read the whole YLT. Pass 1 histograms the first
+// digit and finds each layer's smallest and largest key (zeros are counted in
+// registers). Its last blocks lay out, per layer, a candidate list as long as
+// the keys at or above the lowest first-digit bucket the layer's problems
+// selected (in layer order, while the lists fit the scratch). Pass 2 sums
+// each layer for the mean and copies into the list every key at or above
+// that bucket other than the layer's largest key (trials at the aggregate
+// cap, the value that repeats most), which it only counts. The remaining
+// passes read the lists (the counted keys enter a histogram where they match
+// the prefix), and the tail sums, per problem, the list's keys above the
+// k-th largest key, plus the counted largest keys when they lie above it.
+// TVaR = (sum_gt + (k - count_gt) PML) / k. A layer whose list does not fit
+// histograms its second digit in pass 2 and reads its whole row in every
+// later pass.
+//
+// Every sum is an exact integer: a value's 53-bit mantissa, shifted to its
+// place in a 192-bit fixed-point number whose unit is 2^-108 times the
+// layer's largest binary exponent, added with carries (values below the
+// unit keep the bits above it). Integer additions give the same bits in any
+// order, so blocks add their sums with atomics, and the streaming passes use
+// no FP64 arithmetic (of which this GPU has little). One conversion to FP64
+// (three roundings) ends each sum.
 #include <algorithm>
 #include <cmath>
 
@@ -44,7 +50,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;        // values per thread whose loads are in flight together
-constexpr int kPasses = 6;
+constexpr int kPasses = 6;        // digits of the radix select
 constexpr int kBins1 = 8192;      // first digit: key bits 62..50
 constexpr int kMaxBins = 2048;    // later digits: 11 bits (the last one 6)
 constexpr int kShift1 = 50;
@@ -52,6 +58,7 @@ __host__ __device__ constexpr int pass_shift(int i) { return i == 0 ? kShift1 : 
 __host__ __device__ constexpr int pass_bits(int i) { return i == 0 ? 13 : (i < 5 ? 11 : 6); }
 constexpr unsigned long long kAllKeyBits = 0x7fffffffffffffffULL;  // a decided problem's mask
 constexpr unsigned long long kMant = (1ULL << 52) - 1;
+constexpr int kFixBits = 108;     // fixed-point unit: 2^(e_ref - 1075 - kFixBits)
 
 struct KParams {
     long long k[kMaxProbs];
@@ -63,24 +70,118 @@ struct SelState {
     unsigned long long mask;    // which bits prefix holds
     long long krem;             // rank of the k-th largest among the keys matching prefix
     long long k;
-    long long above1;           // keys above the first-digit bucket
-    unsigned long long b1;      // the first-digit bucket (key >> 50)
-    int first_decided;          // decided in the first pass (a constant layer)
-    int pad_;
 };
 
-// Per-layer state; every field but need, cand_off and compact starts at zero.
+// Per-layer state; every field but need, cand_off, compact and stage starts
+// at zero.
 struct LayerState {
-    unsigned long long kmax, kinv;         // largest key, complement of the smallest (first pass)
-    unsigned long long cnt_zero, cnt_max;  // keys equal to 0 / to kmax (second pass, compacted layers)
-    unsigned long long need;               // candidate slots the selected buckets hold (first pass)
-    unsigned long long cand_off;           // the layer's candidate list in the scratch
-    unsigned int cand_n;                   // candidates written (second pass)
-    int compact;                           // later passes read the candidate list
+    unsigned long long kmax, kinv;         // largest key, complement of the smallest (pass 1)
+    unsigned long long cnt_zero, cnt_max;  // keys equal to 0 (pass 1) / to kmax (pass 2)
+    unsigned long long need;               // list slots: keys at or above the lowest bucket (pass 1)
+    unsigned long long lo_bucket;          // that bucket (key >> 50)
+    unsigned long long cand_off;           // the layer's list in the scratch
+    unsigned int cand_n;                   // keys listed (pass 2)
+    int compact;                           // later passes read the list
+    int stage;                             // digits picked so far (kPasses: every problem decided)
+    int pad_;
 };
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// Exponent of a layer's fixed-point unit: its largest key's binary exponent
+// field (at least 1, the subnormals' scale).
+__device__ __forceinline__ int ref_exp(unsigned long long kmax) { return max(1, (int)(kmax >> 52)); }
+
+// An exact 192-bit sum in units of 2^(e_ref - 1075 - kFixBits).
+struct Fix {
+    unsigned long long w0, w1, w2;
+};
+
+// The key's value in those units as three words (the mantissa shifted to its
+// place; bits below the unit dropped). e_ref is at least the key's exponent.
+__device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, unsigned long long& a0,
+                                          unsigned long long& a1, unsigned long long& a2) {
+    const int e = (int)(key >> 52);
+    unsigned long long m = (key & kMant) | (e ? (1ULL << 52) : 0ULL);
+    int sh = max(e, 1) - e_ref + kFixBits;  // <= kFixBits
+    if (sh < 0) {
+        m = -sh < 64 ? m >> -sh : 0ULL;
+        sh = 0;
+    }
+    const int b = sh & 63;
+    const unsigned long long lo = m << b, hi = b ? m >> (64 - b) : 0ULL;
+    const bool w1 = sh >= 64;
+    a0 = w1 ? 0ULL : lo;
+    a1 = w1 ? lo : hi;
+    a2 = w1 ? hi : 0ULL;
+}
+
+__device__ __forceinline__ void fix_add3(Fix& f, unsigned long long a0, unsigned long long a1, unsigned long long a2) {
+    f.w0 += a0;
+    const unsigned long long c0 = f.w0 < a0 ? 1ULL : 0ULL;
+    const unsigned long long t = a1 + c0;
+    const unsigned long long c0b = t < a1 ? 1ULL : 0ULL;
+    f.w1 += t;
+    const unsigned long long c1 = f.w1 < t ? 1ULL : 0ULL;
+    f.w2 += a2 + c0b + c1;
+}
+
+__device__ __forceinline__ void fix_add(Fix& f, unsigned long long key, int e_ref) {
+    unsigned long long a0, a1, a2;
+    fix_words(key, e_ref, a0, a1, a2);
+    fix_add3(f, a0, a1, a2);
+}
+
+// f += c * key (c < 2^32), exactly.
+__device__ __forceinline__ void fix_add_times(Fix& f, unsigned long long key, int e_ref, unsigned long long c) {
+    unsigned long long a0, a1, a2;
+    fix_words(key, e_ref, a0, a1, a2);
+    const unsigned long long p0 = a0 * c, p0h = __umul64hi(a0, c);
+    const unsigned long long p1 = a1 * c, p1h = __umul64hi(a1, c);
+    const unsigned long long p2 = a2 * c;
+    const unsigned long long r1 = p0h + p1;
+    const unsigned long long cr = r1 < p1 ? 1ULL : 0ULL;
+    fix_add3(f, p0, r1, p1h + p2 + cr);
+}
+
+// Sum over the warp (valid in every lane).
+__device__ __forceinline__ Fix fix_warp_sum(Fix f) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, f.w0, o);
+        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, f.w1, o);
+        const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, f.w2, o);
+        fix_add3(f, b0, b1, b2);
+    }
+    return f;
+}
+
+// g[0..2] += f with integer atomics and carries (the running total stays
+// below 2^192, so no carry leaves the top word).
+__device__ __forceinline__ void fix_atomic(unsigned long long* g, const Fix& f) {
+    if (!(f.w0 | f.w1 | f.w2)) return;
+    const unsigned long long o0 = atomicAdd(g, f.w0);
+    const unsigned long long c0 = o0 + f.w0 < o0 ? 1ULL : 0ULL;
+    const unsigned long long t = f.w1 + c0;
+    const unsigned long long c0b = t < f.w1 ? 1ULL : 0ULL;
+    const unsigned long long o1 = atomicAdd(g + 1, t);
+    const unsigned long long c1 = o1 + t < o1 ? 1ULL : 0ULL;
+    const unsigned long long hi = f.w2 + c0b + c1;
+    if (hi) atomicAdd(g + 2, hi);
+}
+
+// Block sum of a fixed-point value into g (one atomic triple per warp).
+__device__ __forceinline__ void fix_block_atomic(unsigned long long* g, Fix f) {
+    f = fix_warp_sum(f);
+    if ((threadIdx.x & 31) == 0) fix_atomic(g, f);
+}
+
+// The FP64 value of a fixed-point sum.
+__device__ __forceinline__ double fix_value(const Fix& f, int e_ref) {
+    const double two64 = 18446744073709551616.0;
+    const double t = fma(fma((double)f.w2, two64, (double)f.w1), two64, (double)f.w0);
+    return scalbn(t, e_ref - 1075 - kFixBits);
 }
 
 // Block-wide maximum of a 64-bit value (valid in thread 0).
@@ -96,19 +197,6 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
     return r;
 }
 
-// Block-wide sum of a double in a fixed order (warp tree, then warps in order).
-__device__ double block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
-    return r;  // valid in thread 0
-}
-
 __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -122,9 +210,8 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
 }
 
 // Histogram add for the lanes with `hit`, warp-aggregated: when every such
-// lane has the same digit (losses cluster: a capped layer, zero trials) one
-// lane adds them all; otherwise lanes with equal digits add once each.
-// Called by the whole warp.
+// lane has the same digit one lane adds them all; otherwise lanes with equal
+// digits add once each. Called by the whole warp.
 __device__ __forceinline__ void hist_add(unsigned int* h, unsigned dig, bool hit, unsigned lane) {
     const unsigned act = __ballot_sync(0xffffffffu, hit);
     if (!act) return;
@@ -187,31 +274,28 @@ __device__ void pick_digit(const unsigned int* bins, int nb, long long krem, int
     __syncthreads();
 }
 
-// Pass 1 over every value: first-digit histogram (one per layer, shared by
-// its problems), the layer's sum for the mean (two FP64 accumulators, fixed
-// assignment), its smallest and largest key. The last block of a layer picks
-// its problems' first digits; the last layer to be picked lays out the
-// candidate lists (greedily, in layer order, while they fit the budget).
-__global__ void __launch_bounds__(kThreads) first_pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+// Pass 1 over every value: the first-digit histogram (one per layer, shared
+// by its problems; zeros counted in registers, other keys added to the
+// shared-memory histogram one lane at a time), the smallest and largest key.
+// The last block of a layer picks its problems' first digits and the list
+// length; the last layer picked lays out the lists, greedily in layer order
+// while they fit the budget.
+__global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                               const KParams kq, SelState* __restrict__ st,
                                                               LayerState* __restrict__ ls,
                                                               unsigned int* __restrict__ hist1,
-                                                              double* __restrict__ part_mean,
                                                               unsigned int* __restrict__ tickets,
                                                               unsigned long long cand_budget) {
     extern __shared__ unsigned int sh_hist[];  // [kBins1]
-    __shared__ double sh_red[32];
     __shared__ unsigned long long sh_red_u[32];
     __shared__ bool sh_last;
     __shared__ unsigned long long sh_need[kThreads];
     const int j = blockIdx.y;
     const int n_layers = gridDim.y;
-    const unsigned lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kBins1; i += blockDim.x) sh_hist[i] = 0;
     __syncthreads();
     const double* row = ylt + (size_t)j * (size_t)n;
-    double s0 = 0.0, s1 = 0.0;
-    unsigned long long kmax = 0, kinv = 0;
+    unsigned long long kmax = 0, kinv = 0, zeros = 0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
          i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
         double v[kUnroll];
@@ -224,23 +308,25 @@ __global__ void __launch_bounds__(kThreads) first_pass_kernel(const double* __re
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            if (u & 1) s1 += v[u];
-            else s0 += v[u];
             const unsigned long long key = key_of(v[u]);
-            hist_add(sh_hist, (unsigned)(key >> kShift1), valid[u], lane);
             if (valid[u]) {
+                if (key) atomicAdd(&sh_hist[key >> kShift1], 1u);
+                else ++zeros;
                 kmax = max(kmax, key);
                 kinv = max(kinv, ~key);
             }
         }
     }
-    const double r = block_sum(s0 + s1, sh_red);
-    if (threadIdx.x == 0) part_mean[(size_t)j * gridDim.x + blockIdx.x] = r;
     const unsigned long long a = block_max_u64(kmax, sh_red_u);
     const unsigned long long b = block_max_u64(kinv, sh_red_u);
+    const unsigned long long z = block_sum_u64(zeros, sh_red_u);
     if (threadIdx.x == 0) {
         atomicMax(&ls[j].kmax, a);
         atomicMax(&ls[j].kinv, b);
+        if (z) {
+            atomicAdd(&ls[j].cnt_zero, z);
+            sh_hist[0] += (unsigned)z;
+        }
     }
     __syncthreads();
     unsigned int* gh = hist1 + (size_t)j * kBins1;
@@ -258,34 +344,31 @@ __global__ void __launch_bounds__(kThreads) first_pass_kernel(const double* __re
     for (int i = threadIdx.x; i < kBins1; i += blockDim.x) sh_hist[i] = __ldcg(&gh[i]);
     const unsigned long long hi = __ldcg(&ls[j].kmax), lo = ~__ldcg(&ls[j].kinv);
     __syncthreads();
+    int lowest = kBins1;
     for (int q = 0; q < n_p; ++q) {
         SelState* sq = &st[j * n_p + q];
         if (hi == lo) {
             // a constant layer: every problem is decided by its one key
-            if (threadIdx.x == 0)
-                *sq = SelState{hi, kAllKeyBits, 1, kq.k[q], 0, hi >> kShift1, 1, 0};
+            if (threadIdx.x == 0) *sq = SelState{hi, kAllKeyBits, 1, kq.k[q]};
         } else {
             int bin;
             unsigned long long above;
             pick_digit(sh_hist, kBins1, kq.k[q], &bin, &above);
+            lowest = min(lowest, bin);
             if (threadIdx.x == 0)
                 *sq = SelState{(unsigned long long)bin << kShift1, (unsigned long long)(kBins1 - 1) << kShift1,
-                               kq.k[q] - (long long)above, kq.k[q], (long long)above, (unsigned long long)bin, 0, 0};
+                               kq.k[q] - (long long)above, kq.k[q]};
         }
     }
-    __syncthreads();
+    // list slots: every key at or above the lowest selected bucket
+    unsigned long long need = 0;
+    if (hi != lo)
+        for (int i = lowest + (int)threadIdx.x; i < kBins1; i += blockDim.x) need += sh_hist[i];
+    need = block_sum_u64(need, sh_red_u);
     if (threadIdx.x == 0) {
-        // candidate slots: the keys of the distinct buckets the problems selected
-        unsigned long long need = 0;
-        if (hi != lo) {
-            for (int q = 0; q < n_p; ++q) {
-                const unsigned long long bq = st[j * n_p + q].b1;
-                bool seen = false;
-                for (int r = 0; r < q; ++r) seen = seen || st[j * n_p + r].b1 == bq;
-                if (!seen) need += sh_hist[bq];
-            }
-        }
         ls[j].need = need;
+        ls[j].lo_bucket = hi != lo ? (unsigned long long)lowest : 0ULL;
+        ls[j].stage = hi != lo ? 1 : kPasses;
         tickets[j] = 0;
     }
     __threadfence();
@@ -294,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) first_pass_kernel(const double* __re
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
-    // the last layer picked: candidate lists in layer order while they fit
+    // the last layer picked: the lists in layer order while they fit
     unsigned long long run = 0;
     for (int c0 = 0; c0 < n_layers; c0 += kThreads) {
         const int jj = c0 + threadIdx.x;
@@ -314,51 +397,53 @@ __global__ void __launch_bounds__(kThreads) first_pass_kernel(const double* __re
     if (threadIdx.x == 0) tickets[n_layers] = 0;
 }
 
-// Passes 2-6. Each block histograms the keys matching each problem's prefix
-// (problems with the same prefix share the histogram of the first of them),
-// from the layer's whole row in pass 2 and in every pass of a layer without
-// a candidate list, else from the candidate list. Pass 2 also writes the
-// candidate lists (keys of the selected first-digit buckets other than 0 and
-// the layer's largest key, which it counts), and the per-block sums of the
-// values above each problem's bucket. The last block of a layer picks the
-// digits; the counted keys enter its histograms and extremes when they match.
+// Passes 2-7, one digit per layer and launch. Pass 2 (second) reads every
+// value: it adds each layer's sum, counts the layer's largest keys and, for a
+// layer with a list, writes the list; a layer without one histograms its
+// next digit there. Later passes histogram each layer's next digit from its
+// list or its row. Problems with the same prefix share the histogram of the
+// first of them. The last block of a layer picks the digits; the keys
+// counted instead of listed enter its histograms and extremes where they
+// match.
 template <int NQ>
-__global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+__global__ void __launch_bounds__(kThreads, 4) pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                         SelState* __restrict__ st, LayerState* __restrict__ ls,
-                                                        unsigned long long* __restrict__ cand, int shift, int bits,
-                                                        bool second, unsigned int* __restrict__ ghist,
+                                                        unsigned long long* __restrict__ cand, bool second,
+                                                        unsigned int* __restrict__ ghist,
                                                         unsigned long long* __restrict__ minmax,
-                                                        double* __restrict__ part_above,
+                                                        unsigned long long* __restrict__ msum,
                                                         unsigned int* __restrict__ tickets) {
     extern __shared__ unsigned int sh_hist[];  // [n_p][1 << bits]
-    __shared__ double sh_red[32];
     __shared__ unsigned long long sh_red_u[32];
     __shared__ bool sh_last;
     __shared__ int sh_src[kMaxProbs];
-    const int nb = 1 << bits;
     const int j = blockIdx.y;
     const unsigned lane = threadIdx.x & 31;
-    unsigned long long pre[NQ], msk[NQ], b1[NQ];
+    const int stage = ls[j].stage;
+    const bool compact = ls[j].compact != 0;
+    const unsigned long long kmax_l = ls[j].kmax;
+    // pass 2 always runs (the layer sums); later passes only while a digit is left
+    if (stage >= kPasses && !second) return;  // the same for every block of the layer: no ticket
+    const bool histo = stage < kPasses && !(second && compact);
+    const int shift = pass_shift(min(stage, kPasses - 1)), bits = pass_bits(min(stage, kPasses - 1));
+    const int nb = 1 << bits;
+    unsigned long long pre[NQ], msk[NQ];
     bool done[NQ];
-    bool all_done = true;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         pre[q] = q < n_p ? st[j * n_p + q].prefix : 1ULL;  // unused slots never match
         msk[q] = q < n_p ? st[j * n_p + q].mask : 0ULL;
-        b1[q] = q < n_p ? st[j * n_p + q].b1 : 0ULL;
-        done[q] = q >= n_p || msk[q] == kAllKeyBits;
-        all_done = all_done && done[q];
+        done[q] = !histo || q >= n_p || msk[q] == kAllKeyBits;
     }
-    if (all_done) return;  // the same for every block of the layer: no ticket is taken
-    const bool compact = ls[j].compact != 0;
-    const unsigned long long kmax_l = ls[j].kmax;
     const bool from_row = second || !compact;
     const double* src_vals = from_row ? ylt + (size_t)j * (size_t)n
                                       : reinterpret_cast<const double*>(cand + ls[j].cand_off);
     const int64_t len = from_row ? n : (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need);
-    const bool writing = second && compact;  // pass 2 writes the layer's candidate list
+    const bool writing = second && compact && stage < kPasses;  // pass 2 writes the layer's list
     unsigned long long* my_cand = cand + ls[j].cand_off;
     const unsigned long long cap = ls[j].need;
+    const unsigned long long lo_bucket = ls[j].lo_bucket;
+    const int e_ref = ref_exp(kmax_l);
     int src[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -368,16 +453,16 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict
             if (r < q && !done[r] && !done[q] && pre[r] == pre[q] && msk[r] == msk[q]) src[q] = r;
         if (threadIdx.x == 0 && q < n_p) sh_src[q] = src[q];
     }
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
+    if (histo)
+        for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
     unsigned long long kmx[NQ], kiv[NQ];
-    double sab[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         kmx[q] = 0;
         kiv[q] = 0;
-        sab[q] = 0.0;
     }
-    unsigned long long czero = 0, cmax = 0;
+    Fix sum{0, 0, 0};
+    unsigned long long cmax = 0;
     __syncthreads();
     const unsigned dmask = (unsigned)nb - 1u;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -393,28 +478,13 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const unsigned long long key = key_of(v[u]);
-            const unsigned dig = (unsigned)(key >> shift) & dmask;
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                if (q < n_p && !done[q] && src[q] == q) {  // the same for the whole block
-                    const bool hit = valid[u] && (key & msk[q]) == pre[q];
-                    any = any || hit;
-                    // after the first digits few warps hold a candidate at all
-                    if (__any_sync(0xffffffffu, hit)) {
-                        hist_add(sh_hist + q * nb, dig, hit, lane);
-                        if (hit) {
-                            kmx[q] = max(kmx[q], key);
-                            kiv[q] = max(kiv[q], ~key);
-                        }
-                    }
-                }
+            const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;
+            if (second) {
+                fix_add(sum, key, e_ref);  // invalid slots add 0
+                cmax += (valid[u] && key == kmax_l) ? 1 : 0;
             }
             if (writing) {
-                czero += (valid[u] && key == 0ULL) ? 1 : 0;
-                cmax += (valid[u] && key == kmax_l) ? 1 : 0;
-                const bool c = any && key != 0ULL && key != kmax_l;
+                const bool c = key >> kShift1 >= lo_bucket && key != 0ULL && key != kmax_l;
                 const unsigned m = __ballot_sync(0xffffffffu, c);
                 if (m) {
                     const int leader = __ffs(m) - 1;
@@ -424,31 +494,32 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict
                     const unsigned long long slot = (unsigned long long)base + __popc(m & lt_mask);
                     if (c && slot < cap) my_cand[slot] = key;
                 }
-                // values above each problem's first-digit bucket, for TVaR
+            }
+            if (histo) {
+                const unsigned dig = (unsigned)(key >> shift) & dmask;
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    if (q < n_p && !done[q]) {
-                        const bool up = valid[u] && (key >> kShift1) > b1[q];
-                        if (__any_sync(0xffffffffu, up) && up) sab[q] += v[u];
+                    if (q < n_p && !done[q] && src[q] == q) {  // the same for the whole block
+                        const bool hit = valid[u] && (key & msk[q]) == pre[q];
+                        // after the first digits few warps hold a candidate at all
+                        if (__any_sync(0xffffffffu, hit)) {
+                            hist_add(sh_hist + q * nb, dig, hit, lane);
+                            if (hit) {
+                                kmx[q] = max(kmx[q], key);
+                                kiv[q] = max(kiv[q], ~key);
+                            }
+                        }
                     }
                 }
             }
         }
     }
-    if (writing) {
-        const unsigned long long z = block_sum_u64(czero, sh_red_u);
+    if (second) {
+        fix_block_atomic(msum + 3 * (size_t)j, sum);
         const unsigned long long m = block_sum_u64(cmax, sh_red_u);
-        if (threadIdx.x == 0) {
-            if (z) atomicAdd(&ls[j].cnt_zero, z);
-            if (m) atomicAdd(&ls[j].cnt_max, m);
-        }
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (q >= n_p || done[q]) continue;
-            const double s = block_sum(sab[q], sh_red);
-            if (threadIdx.x == 0) part_above[((size_t)j * n_p + q) * gridDim.x + blockIdx.x] = s;
-        }
+        if (threadIdx.x == 0 && m) atomicAdd(&ls[j].cnt_max, m);
     }
+    if (!histo) return;  // nothing to pick: no ticket is taken by any block of the layer
     // a problem that shares its source's candidates shares its extremes
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -482,8 +553,8 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
-    // keys counted instead of listed take part from pass 3 on, where they match
-    const bool virt = !second && compact;
+    // keys counted instead of listed take part where they match
+    const bool virt = !from_row;
     const unsigned long long cz = virt ? __ldcg(&ls[j].cnt_zero) : 0ULL;
     const unsigned long long cm = virt ? __ldcg(&ls[j].cnt_max) : 0ULL;
     for (int q = 0; q < n_p; ++q) {
@@ -532,147 +603,83 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const double* __restrict
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) tickets[j] = 0;
+    if (threadIdx.x == 0) {
+        ls[j].stage = stage + 1;
+        tickets[j] = 0;
+    }
 }
 
-// Exact sum of keys that share one binary exponent e (the bucket's): their
-// mantissas (with the implicit bit when e > 0) as integers, split at bit 32
-// so that neither half overflows for 2^31 values.
-struct MantSum {
-    unsigned long long hi, lo, cnt;
-};
-
-__device__ __forceinline__ unsigned long long mant_of(unsigned long long key) {
-    const unsigned long long e = key >> 52;
-    return (key & kMant) | (e ? (1ULL << 52) : 0ULL);
-}
-
-// Value of an exact mantissa sum for exponent field e: one rounding.
-__device__ __forceinline__ double mant_value(unsigned long long hi, unsigned long long lo, unsigned long long e) {
-    const unsigned long long th = hi + (lo >> 32), tl = lo & 0xffffffffULL;
-    const double t = fma((double)th, 4294967296.0, (double)tl);
-    return scalbn(t, (int)(e ? e : 1) - 1075);
-}
-
-// The tail, fused with the final reduction. Layers with candidate lists: the
-// candidates of each problem's bucket above its k-th largest key, summed as
-// integers (atomics on exact integers: any order gives the same bits).
-// Layers without: every value above the k-th largest key, summed in FP64 per
-// block in a fixed order (skipped when the k-th largest is the layer's
-// largest key). The last block of the grid reduces every problem in a fixed
-// order (one warp per problem) and writes mean, PML and TVaR.
+// The tail, fused with the final reduction. Per problem, the keys above its
+// k-th largest key and their exact fixed-point sum, from the layer's list
+// (plus the counted largest keys when they lie above it) or from its row;
+// nothing is read for a problem whose k-th largest is the layer's largest
+// key. Blocks add their integer sums with atomics. The last block of the grid
+// converts every problem's sums (one warp per problem) and writes mean, PML
+// and TVaR (and, if asked, each layer's sum).
 template <int NQ>
-__global__ void __launch_bounds__(kThreads) tail_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+__global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                         const SelState* __restrict__ st,
                                                         const LayerState* __restrict__ ls,
                                                         const unsigned long long* __restrict__ cand,
-                                                        const double* __restrict__ part_mean,
-                                                        const double* __restrict__ part_above,
-                                                        double* __restrict__ part_sum,
-                                                        unsigned long long* __restrict__ part_cnt,
-                                                        unsigned long long* __restrict__ int_acc,
+                                                        const unsigned long long* __restrict__ msum,
+                                                        unsigned long long* __restrict__ tsum,
                                                         unsigned int* __restrict__ ticket, double* mean, double* pml,
                                                         double* tvar, double* sum_out) {
-    __shared__ double sh_red[32];
     __shared__ unsigned long long sh_red_u[32];
     __shared__ bool sh_last;
     const int j = blockIdx.y;
     const int n_layers = gridDim.y;
-    const int nblk = gridDim.x;
     const bool compact = ls[j].compact != 0;
     const unsigned long long kmax_l = ls[j].kmax;
-    unsigned long long thr[NQ], b1[NQ];
+    const int e_ref = ref_exp(kmax_l);
+    unsigned long long thr[NQ];
     bool live[NQ];
     bool any_live = false;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         thr[q] = q < n_p ? st[j * n_p + q].prefix : ~0ULL;
-        b1[q] = q < n_p ? st[j * n_p + q].b1 : 0ULL;
-        // nothing lies above the k-th largest key when it is the layer's largest
-        live[q] = q < n_p && !st[j * n_p + q].first_decided && (compact || thr[q] != kmax_l);
+        live[q] = q < n_p && thr[q] < kmax_l;  // nothing lies above the layer's largest key
         any_live = any_live || live[q];
     }
-    if (compact) {
-        const unsigned long long* c = cand + ls[j].cand_off;
-        const int64_t len = any_live ? (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need) : 0;
-        unsigned long long mh[NQ], ml[NQ], mc[NQ];
+    const double* src_vals = compact ? reinterpret_cast<const double*>(cand + ls[j].cand_off)
+                                     : ylt + (size_t)j * (size_t)n;
+    const int64_t len = !any_live ? 0
+                        : compact ? (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need) : n;
+    Fix s[NQ];
+    unsigned long long c[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) mh[q] = ml[q] = mc[q] = 0;
-        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
-             i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-            unsigned long long kv[kUnroll];
+    for (int q = 0; q < NQ; ++q) {
+        s[q] = Fix{0, 0, 0};
+        c[q] = 0;
+    }
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
+         i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
+        double v[kUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-                kv[u] = i < len ? __ldcs(c + i) : 0ULL;  // 0: never above a k-th largest key
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const unsigned long long m = mant_of(kv[u]);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    if (live[q] && (kv[u] >> kShift1) == b1[q] && kv[u] > thr[q]) {
-                        mh[q] += m >> 32;
-                        ml[q] += m & 0xffffffffULL;
-                        mc[q] += 1;
-                    }
-            }
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+            v[u] = i < len ? __ldcs(src_vals + i) : 0.0;  // 0: never above a k-th largest key
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (!live[q]) continue;
-            const unsigned long long a = block_sum_u64(mh[q], sh_red_u);
-            const unsigned long long b = block_sum_u64(ml[q], sh_red_u);
-            const unsigned long long cc = block_sum_u64(mc[q], sh_red_u);
-            if (threadIdx.x == 0 && cc) {
-                unsigned long long* acc = int_acc + 3 * ((size_t)j * n_p + q);
-                atomicAdd(acc, a);
-                atomicAdd(acc + 1, b);
-                atomicAdd(acc + 2, cc);
-            }
+        for (int u = 0; u < kUnroll; ++u) {
+            const unsigned long long key = key_of(v[u]);
+            unsigned long long a0, a1, a2;
+            fix_words(key, e_ref, a0, a1, a2);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (live[q] && key > thr[q]) {
+                    fix_add3(s[q], a0, a1, a2);
+                    c[q] += 1;
+                }
         }
-    } else {
-        const double* row = ylt + (size_t)j * (size_t)n;
-        const int64_t len = any_live ? n : 0;
-        double s[NQ];
-        unsigned long long cnt[NQ];
+    }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            s[q] = 0.0;
-            cnt[q] = 0;
-        }
-        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
-             i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-            double v[kUnroll];
-            bool valid[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-                valid[u] = i < len;
-                v[u] = valid[u] ? __ldcs(row + i) : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;  // 0: never above
-#pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    if (live[q] && key > thr[q]) {
-                        s[q] += v[u];
-                        cnt[q] += 1;
-                    }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (q >= n_p) break;
-            const double rs = block_sum(s[q], sh_red);
-            const unsigned long long rc = block_sum_u64(cnt[q], sh_red_u);
-            if (threadIdx.x == 0) {
-                const size_t w = ((size_t)j * n_p + q) * nblk + blockIdx.x;
-                part_sum[w] = rs;
-                part_cnt[w] = rc;
-            }
-        }
+    for (int q = 0; q < NQ; ++q) {
+        if (!live[q]) continue;
+        unsigned long long* g = tsum + 4 * ((size_t)j * n_p + q);
+        fix_block_atomic(g, s[q]);
+        const unsigned long long cc = block_sum_u64(c[q], sh_red_u);
+        if (threadIdx.x == 0 && cc) atomicAdd(g + 3, cc);
     }
     __threadfence();
     __syncthreads();
@@ -682,60 +689,30 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const double* __restrict
     __threadfence();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = wib; i < n_layers * n_p; i += kThreads / 32) {
+        if (lane != 0) continue;
         const int jj = i / n_p, q = i % n_p;
         const SelState sq = st[i];
-        const bool cmp = __ldcg(&ls[jj].compact) != 0;
-        double m = 0.0, s = 0.0;
-        unsigned long long c = 0;
-        for (int b0 = 0; b0 < nblk; b0 += 32 * 8) {
-            // eight partials per lane requested at once, then summed in order
-            double pm[8], ps[8];
-            unsigned long long pc[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int b = b0 + r * 32 + lane;
-                const bool ok = b < nblk;
-                pm[r] = ok && q == 0 ? __ldcg(part_mean + (size_t)jj * nblk + b) : 0.0;
-                ps[r] = ok ? __ldcg((cmp ? part_above : part_sum) + (size_t)i * nblk + b) : 0.0;
-                pc[r] = ok && !cmp ? __ldcg(part_cnt + (size_t)i * nblk + b) : 0ULL;
-            }
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                m += pm[r];
-                s += ps[r];
-                c += pc[r];
-            }
+        const unsigned long long kmx = __ldcg(&ls[jj].kmax);
+        const int er = ref_exp(kmx);
+        if (q == 0) {
+            const Fix ms{__ldcg(msum + 3 * (size_t)jj), __ldcg(msum + 3 * (size_t)jj + 1),
+                         __ldcg(msum + 3 * (size_t)jj + 2)};
+            const double total = fix_value(ms, er);
+            if (mean) mean[jj] = total / (double)n;
+            if (sum_out) sum_out[jj] = total;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            m += __shfl_xor_sync(0xffffffffu, m, o);
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
+        const unsigned long long* g = tsum + 4 * (size_t)i;
+        Fix f{__ldcg(g), __ldcg(g + 1), __ldcg(g + 2)};
+        unsigned long long cnt = __ldcg(g + 3);
+        if (__ldcg(&ls[jj].compact) && kmx > sq.prefix) {
+            // the layer's largest keys were counted, not listed
+            const unsigned long long cm = __ldcg(&ls[jj].cnt_max);
+            fix_add_times(f, kmx, er, cm);
+            cnt += cm;
         }
-        if (lane == 0) {
-            if (q == 0 && mean) mean[jj] = m / (double)n;
-            if (q == 0 && sum_out) sum_out[jj] = m;
-            const double v = __longlong_as_double((long long)sq.prefix);
-            if (sq.first_decided) {
-                s = 0.0;  // a constant layer: nothing above its one key
-                c = 0;
-            } else if (cmp) {
-                // above the bucket (pass 2) plus the bucket's keys above the
-                // k-th largest: the listed ones and the counted largest key
-                const unsigned long long* acc = int_acc + 3 * (size_t)i;
-                unsigned long long mh = __ldcg(acc), ml = __ldcg(acc + 1), mc = __ldcg(acc + 2);
-                const unsigned long long kmx = __ldcg(&ls[jj].kmax), cm = __ldcg(&ls[jj].cnt_max);
-                if (cm && (kmx >> kShift1) == sq.b1 && kmx > sq.prefix) {
-                    const unsigned long long mk = mant_of(kmx);
-                    mh += cm * (mk >> 32);
-                    ml += cm * (mk & 0xffffffffULL);
-                    mc += cm;
-                }
-                if (mc) s += mant_value(mh, ml, sq.b1 >> 2);
-                c = (unsigned long long)sq.above1 + mc;
-            }
-            if (pml) pml[i] = v;
-            if (tvar) tvar[i] = (s + (double)(sq.k - (long long)c) * v) / (double)sq.k;
-        }
+        const double v = __longlong_as_double((long long)sq.prefix);
+        if (pml) pml[i] = v;
+        if (tvar) tvar[i] = (fix_value(f, er) + (double)(sq.k - (long long)cnt) * v) / (double)sq.k;
     }
     if (threadIdx.x == 0) *ticket = 0;
 }
@@ -851,13 +828,12 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // zero + zero_bytes) must be zero when the call starts; the rest is written
 // before it is read. The candidate lists take cand_slots 8-byte keys.
 struct MetricsLayout {
-    size_t st, ls, hist1, hist, minmax, tickets, above, iacc, pmean, psum, pcnt, cand;
+    size_t st, ls, hist1, hist, minmax, tickets, msum, tsum, cand;
     size_t zero, zero_bytes, total;
 };
 
-MetricsLayout metrics_layout(int64_t n, int32_t n_layers, int32_t n_p, int nblk, uint64_t cand_slots) {
-    (void)n;
-    const size_t L = (size_t)n_layers, np = (size_t)n_layers * n_p, nb = (size_t)nblk;
+MetricsLayout metrics_layout(int32_t n_layers, int32_t n_p, uint64_t cand_slots) {
+    const size_t L = (size_t)n_layers, np = (size_t)n_layers * n_p;
     MetricsLayout m{};
     m.st = 0;
     m.ls = align256(m.st + sizeof(SelState) * np);
@@ -865,30 +841,26 @@ MetricsLayout metrics_layout(int64_t n, int32_t n_layers, int32_t n_p, int nblk,
     m.hist = align256(m.hist1 + sizeof(unsigned int) * kBins1 * L);
     m.minmax = align256(m.hist + sizeof(unsigned int) * kMaxBins * np);
     m.tickets = align256(m.minmax + sizeof(unsigned long long) * 2 * np);
-    m.above = align256(m.tickets + sizeof(unsigned int) * (L + 2));
-    m.iacc = align256(m.above + sizeof(double) * np * nb);
-    m.pmean = align256(m.iacc + sizeof(unsigned long long) * 3 * np);
+    m.msum = align256(m.tickets + sizeof(unsigned int) * (L + 2));
+    m.tsum = align256(m.msum + sizeof(unsigned long long) * 3 * L);
+    m.cand = align256(m.tsum + sizeof(unsigned long long) * 4 * np);
     m.zero = m.ls;
-    m.zero_bytes = m.pmean - m.ls;
-    m.psum = align256(m.pmean + sizeof(double) * L * nb);
-    m.pcnt = align256(m.psum + sizeof(double) * np * nb);
-    m.cand = align256(m.pcnt + sizeof(unsigned long long) * np * nb);
+    m.zero_bytes = m.cand - m.ls;
     m.total = align256(m.cand + sizeof(unsigned long long) * (size_t)cand_slots);
     return m;
 }
 
 // Candidate slots the allocating path reserves: an eighth of the YLT (the
-// buckets the problems select hold a few percent of a layer's trials once 0
-// and the layer's largest key are left out), at least 65,536, at most the
-// whole YLT.
+// lists hold the top few percent of a layer's trials, its largest key left
+// out), at least 65,536, at most the whole YLT.
 uint64_t default_cand_slots(int64_t n, int32_t n_layers) {
     const uint64_t all = (uint64_t)n * (uint64_t)n_layers;
     return std::min<uint64_t>(all, std::max<uint64_t>(all / 8, 65536));
 }
 
 // The metric kernels over a caller's scratch laid out by metrics_layout:
-// clear, pass 1, passes 2-6, tail with the final reduction (eight steps on
-// the stream, seven of them launches).
+// clear, pass 1, passes 2-7, the tail with the final reduction (nine steps
+// on the stream, eight of them launches).
 cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers, int32_t n_p, const KParams& kq,
                                   int nblk, char* w, const MetricsLayout& m, uint64_t cand_slots, double* mean,
                                   double* pml, double* tvar, double* sum_out, cudaStream_t s) {
@@ -898,33 +870,28 @@ cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers
     auto* hist = (unsigned int*)(w + m.hist);
     auto* minmax = (unsigned long long*)(w + m.minmax);
     auto* tickets = (unsigned int*)(w + m.tickets);
-    auto* above = (double*)(w + m.above);
-    auto* iacc = (unsigned long long*)(w + m.iacc);
-    auto* pmean = (double*)(w + m.pmean);
-    auto* psum = (double*)(w + m.psum);
-    auto* pcnt = (unsigned long long*)(w + m.pcnt);
+    auto* msum = (unsigned long long*)(w + m.msum);
+    auto* tsum = (unsigned long long*)(w + m.tsum);
     auto* cand = (unsigned long long*)(w + m.cand);
     cudaError_t err = cudaMemsetAsync(w + m.zero, 0, m.zero_bytes, s);
     if (err) return err;
     const dim3 grid(nblk, n_layers);
-    first_pass_kernel<<<grid, kThreads, sizeof(unsigned int) * kBins1, s>>>(ylt, n, n_p, kq, st, ls, hist1, pmean,
-                                                                            tickets, cand_slots);
+    first_pass_kernel<<<grid, kThreads, sizeof(unsigned int) * kBins1, s>>>(ylt, n, n_p, kq, st, ls, hist1, tickets,
+                                                                            cand_slots);
     if ((err = cudaGetLastError())) return err;
     // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
     auto pass_k = n_p <= 1 ? pass_kernel<1> : n_p <= 2 ? pass_kernel<2> : n_p <= 4 ? pass_kernel<4> : pass_kernel<8>;
     auto tail_k = n_p <= 1 ? tail_kernel<1> : n_p <= 2 ? tail_kernel<2> : n_p <= 4 ? tail_kernel<4> : tail_kernel<8>;
-    for (int i = 1; i < kPasses; ++i) {
-        const int bits = pass_bits(i);
-        const size_t shm = sizeof(unsigned int) * (size_t)n_p << bits;
-        if (shm > 48 * 1024 &&
-            (err = cudaFuncSetAttribute(pass_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
-            return err;
-        pass_k<<<grid, kThreads, shm, s>>>(ylt, n, n_p, st, ls, cand, pass_shift(i), bits, i == 1, hist, minmax,
-                                           above, tickets);
+    const size_t shm = sizeof(unsigned int) * (size_t)n_p * kMaxBins;
+    if (shm > 48 * 1024 && (err = cudaFuncSetAttribute(pass_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)))
+        return err;
+    // pass 2, then one launch per digit a layer's list may still need
+    for (int i = 0; i < kPasses; ++i) {
+        pass_k<<<grid, kThreads, shm, s>>>(ylt, n, n_p, st, ls, cand, i == 0, hist, minmax, msum, tickets);
         if ((err = cudaGetLastError())) return err;
     }
-    tail_k<<<grid, kThreads, 0, s>>>(ylt, n, n_p, st, ls, cand, pmean, above, psum, pcnt, iacc,
-                                     tickets + n_layers + 1, mean, pml, tvar, sum_out);
+    tail_k<<<grid, kThreads, 0, s>>>(ylt, n, n_p, st, ls, cand, msum, tsum, tickets + n_layers + 1, mean, pml, tvar,
+                                     sum_out);
     return cudaGetLastError();
 }
 
@@ -938,26 +905,33 @@ int64_t tail_count(double p, int64_t n) {
     return std::min<int64_t>(n, std::max<int64_t>(1, k));
 }
 
+size_t metrics_scratch_bytes(int64_t n, int32_t n_layers, int32_t n_p) {
+    return metrics_layout(n_layers, n_p, default_cand_slots(n, n_layers)).total;
+}
+
 cudaError_t metrics_run_k(const double* ylt, int64_t n, int32_t n_layers, const int64_t* k, int32_t n_p,
-                          double* mean, double* pml, double* tvar, double* sum_out, cudaStream_t s) {
+                          double* mean, double* pml, double* tvar, double* sum_out, cudaStream_t s,
+                          void* scratch, size_t scratch_bytes) {
     const int nblk = blocks_per_layer(n, n_layers);
     const uint64_t slots = default_cand_slots(n, n_layers);
-    const MetricsLayout m = metrics_layout(n, n_layers, n_p, nblk, slots);
-    char* w = nullptr;
-    cudaError_t err = cudaMallocAsync((void**)&w, m.total, s);
+    const MetricsLayout m = metrics_layout(n_layers, n_p, slots);
+    char* w = static_cast<char*>(scratch);
+    const bool own = !w || scratch_bytes < m.total;
+    cudaError_t err = own ? cudaMallocAsync((void**)&w, m.total, s) : cudaSuccess;
     if (err != cudaSuccess) return err;
     KParams kq = {};
     for (int q = 0; q < n_p; ++q) kq.k[q] = std::min<int64_t>(n, std::max<int64_t>(1, k[q]));
     err = launch_metric_kernels(ylt, n, n_layers, n_p, kq, nblk, w, m, slots, mean, pml, tvar, sum_out, s);
-    const cudaError_t e2 = cudaFreeAsync(w, s);
+    const cudaError_t e2 = own ? cudaFreeAsync(w, s) : cudaSuccess;
     return err ? err : e2;
 }
 
 cudaError_t metrics_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
-                        double* mean, double* pml, double* tvar, cudaStream_t s) {
+                        double* mean, double* pml, double* tvar, cudaStream_t s, void* scratch,
+                        size_t scratch_bytes) {
     int64_t k[kMaxProbs];
     for (int q = 0; q < n_p; ++q) k[q] = tail_count(probs[q], n);
-    return metrics_run_k(ylt, n, n_layers, k, n_p, mean, pml, tvar, nullptr, s);
+    return metrics_run_k(ylt, n, n_layers, k, n_p, mean, pml, tvar, nullptr, s, scratch, scratch_bytes);
 }
 
 cudaError_t metrics_backward_run(const double* ylt, int64_t n, int32_t n_layers, const double* probs, int32_t n_p,
@@ -1092,11 +1066,11 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     const int nblk = blocks_per_layer(n_trials, n_layers);
     // the fixed part must fit; what is left holds candidate lists (layers
     // whose lists do not fit read their whole row in every pass instead)
-    const MetricsLayout fixed = metrics_layout(n_trials, n_layers, n_p, nblk, 0);
+    const MetricsLayout fixed = metrics_layout(n_layers, n_p, 0);
     if (fixed.total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
     const uint64_t slots = std::min<uint64_t>(((size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES - fixed.total) / 8,
                                               default_cand_slots(n_trials, n_layers));
-    const MetricsLayout m = metrics_layout(n_trials, n_layers, n_p, nblk, slots);
+    const MetricsLayout m = metrics_layout(n_layers, n_p, slots);
     if (m.total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
     unsigned char* w = nullptr;
     cudaError_t err = noalloc_scratch(&w);
