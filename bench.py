@@ -605,12 +605,23 @@ def extra_workload(name: str, dev, probes: dict, hbm: float, l2_size: float) -> 
             art.art_metrics(y64, T, L, probs, m64, p64, t64, stream)
             art.art_metrics(ylt, T, L, probs, mean, pml, tvar, stream)
             torch.cuda.synchronize(dev)
-            relerr = lambda a, b: float(((a - b).abs() / b.abs().clamp_min(1e-300)).max())
+            relv = lambda a, b: torch.where(a == b, torch.zeros_like(a), (a - b).abs() / b.abs().clamp_min(1e-300))
+            relerr = lambda a, b: float(relv(a, b).max())
+            # the worst PML: its layer's aggregate over the PML bounds the
+            # relative error that FP32 occurrence losses (relative rounding
+            # 2^-24 each) can leave in Y = S - AggR
+            rp = relv(pml, p64)
+            wj, wq = divmod(int(torch.argmax(rp)), n_p)
+            amp = (float(port.agg_ret[wj]) + float(p64[wj, wq])) / max(float(p64[wj, wq]), 1e-300)
             rec["precision_vs_all_fp64"] = {
                 "trials": T, "max_abs_dy_over_gross": float(rel.max()),
                 "pml_rel_err_by_prob": {str(pr): relerr(pml[:, q], p64[:, q]) for q, pr in enumerate(probs)},
                 "tvar_rel_err_by_prob": {str(pr): relerr(tvar[:, q], t64[:, q]) for q, pr in enumerate(probs)},
                 "mean_rel_err": relerr(mean, m64),
+                "worst_pml": {"layer": wj, "prob": probs[wq], "pml": float(p64[wj, wq]),
+                              "agg_ret": float(port.agg_ret[wj]), "aggregate_over_pml": amp,
+                              "rel_err": float(rp[wj, wq]),
+                              "rel_err_over_2^-24_x_aggregate_over_pml": float(rp[wj, wq]) / (amp * 2.0 ** -24)},
                 "note": f"mixed ({chosen}) against the all-FP64 GPU variant on every (layer, trial)"}
             del y64, gross, rel
     finally:

@@ -328,12 +328,14 @@ ART_API art_status art_metrics(const double* ylt_dev, int64_t n_trials, int32_t 
  * stream-ordered allocator it uses one scratch array that the library
  * defines in device memory at file scope, ART_METRICS_NOALLOC_SCRATCH_BYTES
  * (8 MiB) in size; every GPU that loads the library holds those 8 MiB until
- * the process exits. The scratch needed is about
- *   n_layers * n_p * (8 KiB + 32 B + 16 B * b) + n_layers * 8 B * b
- * with b = min(ceil(n_trials / 4096), ceil(c * SMs / n_layers)) blocks per
- * layer, c = 8 when the YLT is larger than the device's L2 and 4 otherwise;
- * a call that needs more returns ART_EINVAL and enqueues nothing (in
- * practice, n_layers * n_p above about 1000).
+ * the process exits. The fixed part of the scratch is about
+ *   n_layers * 32.1 KiB + n_layers * n_p * 8.1 KiB
+ * (a first-digit histogram per layer, a digit histogram per problem); a
+ * call that needs more returns ART_EINVAL and enqueues nothing (in
+ * practice, more than about 200 layers at one probability, 140 at three,
+ * 80 at eight). What the fixed part leaves holds the candidate lists; a
+ * layer whose list does not fit reads its whole row in every pass, which
+ * gives the same results more slowly.
  *
  * The first call on each device looks up that device's address of the
  * scratch array (cudaGetSymbolAddress, with the device current); make that

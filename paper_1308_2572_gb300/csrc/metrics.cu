@@ -19,18 +19,19 @@
 //
 // Only the first two passes read the whole YLT. Pass 1 histograms the first
 // digit and finds each layer's smallest and largest key (zeros are counted in
-// registers). Its last blocks lay out, per layer, a candidate list as long as
-// the keys at or above the lowest first-digit bucket the layer's problems
-// selected (in layer order, while the lists fit the scratch). Pass 2 sums
-// each layer for the mean and copies into the list every key at or above
-// that bucket other than the layer's largest key (trials at the aggregate
-// cap, the value that repeats most), which it only counts. The remaining
-// passes read the lists (the counted keys enter a histogram where they match
-// the prefix), and the tail sums, per problem, the list's keys above the
-// k-th largest key, plus the counted largest keys when they lie above it.
-// TVaR = (sum_gt + (k - count_gt) PML) / k. A layer whose list does not fit
-// histograms its second digit in pass 2 and reads its whole row in every
-// later pass.
+// registers). Its last blocks lay out, per layer and in layer order while
+// they fit the scratch, a candidate list: every key at or above the lowest
+// first-digit bucket the layer's problems selected, or, when that does not
+// fit, the keys of the selected buckets only. Pass 2 sums each layer for the
+// mean and writes the lists, leaving out 0 and the layer's largest key
+// (trials without a loss and trials at the aggregate cap, the values that
+// repeat most), which it only counts. The remaining passes read the lists
+// (the counted keys enter a histogram where they match the prefix). The tail
+// sums, per problem, the keys above the k-th largest key: from a list of
+// every key above the lowest bucket (plus the counted largest keys when they
+// lie above it), else from the row. TVaR = (sum_gt + (k - count_gt) PML) / k.
+// A layer without a list histograms its second digit in pass 2 and reads its
+// whole row in every later pass.
 //
 // Every sum is an exact integer: a value's 53-bit mantissa, shifted to its
 // place in a 192-bit fixed-point number whose unit is 2^-108 times the
@@ -76,15 +77,21 @@ struct SelState {
 // at zero.
 struct LayerState {
     unsigned long long kmax, kinv;         // largest key, complement of the smallest (pass 1)
-    unsigned long long cnt_zero, cnt_max;  // keys equal to 0 (pass 1) / to kmax (pass 2)
-    unsigned long long need;               // list slots: keys at or above the lowest bucket (pass 1)
-    unsigned long long lo_bucket;          // that bucket (key >> 50)
+    unsigned long long cnt_zero, cnt_max;  // keys equal to 0 / to kmax (pass 1)
+    unsigned long long need;               // list slots (pass 1): keys at or above the lowest bucket,
+    unsigned long long need_sel;           //   or keys of the selected buckets only
+    unsigned long long lo_bucket;          // the lowest selected bucket (key >> 50)
     unsigned long long cand_off;           // the layer's list in the scratch
     unsigned int cand_n;                   // keys listed (pass 2)
-    int compact;                           // later passes read the list
+    int compact;                           // kListAll, kListSelected or kListNone
     int stage;                             // digits picked so far (kPasses: every problem decided)
-    int pad_;
 };
+
+// What a layer's list holds: every key at or above its lowest selected
+// first-digit bucket (the selection and the tail read the list), the keys
+// of its selected buckets only (the selection reads the list, the tail the
+// row), or nothing (every pass reads the row).
+enum { kListNone = 0, kListAll = 1, kListSelected = 2 };
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
@@ -280,10 +287,11 @@ __device__ void pick_digit(const unsigned int* bins, int nb, long long krem, int
 // The last block of a layer picks its problems' first digits and the list
 // length; the last layer picked lays out the lists, greedily in layer order
 // while they fit the budget.
-__global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+__global__ void __launch_bounds__(kThreads, 5) first_pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                               const KParams kq, SelState* __restrict__ st,
                                                               LayerState* __restrict__ ls,
                                                               unsigned int* __restrict__ hist1,
+                                                              unsigned long long* __restrict__ part_max,
                                                               unsigned int* __restrict__ tickets,
                                                               unsigned long long cand_budget) {
     extern __shared__ unsigned int sh_hist[];  // [kBins1]
@@ -295,7 +303,8 @@ __global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* _
     for (int i = threadIdx.x; i < kBins1; i += blockDim.x) sh_hist[i] = 0;
     __syncthreads();
     const double* row = ylt + (size_t)j * (size_t)n;
-    unsigned long long kmax = 0, kinv = 0, zeros = 0;
+    // the thread's largest key and how often it holds it; the smallest key
+    unsigned long long kmax = 0, cmax = 0, kinv = 0, zeros = 0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
          i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
         double v[kUnroll];
@@ -312,15 +321,23 @@ __global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* _
             if (valid[u]) {
                 if (key) atomicAdd(&sh_hist[key >> kShift1], 1u);
                 else ++zeros;
+                cmax = key > kmax ? 1ULL : cmax + (key == kmax ? 1ULL : 0ULL);
                 kmax = max(kmax, key);
                 kinv = max(kinv, ~key);
             }
         }
     }
     const unsigned long long a = block_max_u64(kmax, sh_red_u);
+    __shared__ unsigned long long sh_bmax;
+    if (threadIdx.x == 0) sh_bmax = a;
+    __syncthreads();
+    // how often the block holds its largest key
+    const unsigned long long ca = block_sum_u64(kmax == sh_bmax ? cmax : 0ULL, sh_red_u);
     const unsigned long long b = block_max_u64(kinv, sh_red_u);
     const unsigned long long z = block_sum_u64(zeros, sh_red_u);
     if (threadIdx.x == 0) {
+        part_max[2 * ((size_t)j * gridDim.x + blockIdx.x)] = a;
+        part_max[2 * ((size_t)j * gridDim.x + blockIdx.x) + 1] = ca;
         atomicMax(&ls[j].kmax, a);
         atomicMax(&ls[j].kinv, b);
         if (z) {
@@ -360,12 +377,36 @@ __global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* _
                                kq.k[q] - (long long)above, kq.k[q]};
         }
     }
-    // list slots: every key at or above the lowest selected bucket
+    // how often the layer holds its largest key: the blocks holding it
+    unsigned long long cm = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        if (__ldcg(&part_max[2 * ((size_t)j * gridDim.x + b)]) == hi)
+            cm += __ldcg(&part_max[2 * ((size_t)j * gridDim.x + b) + 1]);
+    cm = block_sum_u64(cm, sh_red_u);
+    // list slots: every key at or above the lowest selected bucket other
+    // than 0 and the largest key (counted, not listed)
     unsigned long long need = 0;
     if (hi != lo)
         for (int i = lowest + (int)threadIdx.x; i < kBins1; i += blockDim.x) need += sh_hist[i];
     need = block_sum_u64(need, sh_red_u);
     if (threadIdx.x == 0) {
+        const unsigned long long cz = __ldcg(&ls[j].cnt_zero);
+        unsigned long long need_sel = 0;  // or the keys of the selected buckets only
+        if (hi != lo) {
+            need -= cm + (lowest == 0 ? cz : 0ULL);
+            bool max_sel = false, zero_sel = false;
+            for (int q = 0; q < n_p; ++q) {
+                const unsigned long long bq = st[j * n_p + q].prefix >> kShift1;
+                bool seen = false;
+                for (int r = 0; r < q; ++r) seen = seen || (st[j * n_p + r].prefix >> kShift1) == bq;
+                if (!seen) need_sel += sh_hist[bq];
+                max_sel = max_sel || bq == (hi >> kShift1);
+                zero_sel = zero_sel || bq == 0;
+            }
+            need_sel -= (max_sel ? cm : 0ULL) + (zero_sel ? cz : 0ULL);
+        }
+        ls[j].cnt_max = cm;
+        ls[j].need_sel = need_sel;
         ls[j].need = need;
         ls[j].lo_bucket = hi != lo ? (unsigned long long)lowest : 0ULL;
         ls[j].stage = hi != lo ? 1 : kPasses;
@@ -385,11 +426,15 @@ __global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* _
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int t = 0; t < kThreads && c0 + t < n_layers; ++t) {
-                const unsigned long long nd = sh_need[t];
-                const bool fits = run + nd <= cand_budget;
-                ls[c0 + t].compact = fits ? 1 : 0;
-                ls[c0 + t].cand_off = fits ? run : 0;
-                if (fits) run += nd;
+                LayerState& l = ls[c0 + t];
+                const unsigned long long nd = sh_need[t], ns = __ldcg(&l.need_sel);
+                const int mode = run + nd <= cand_budget ? kListAll : run + ns <= cand_budget ? kListSelected
+                                                                                                : kListNone;
+                const unsigned long long len = mode == kListAll ? nd : mode == kListSelected ? ns : 0ULL;
+                l.compact = mode;
+                l.need = len;
+                l.cand_off = run;
+                run += len;
             }
         }
         __syncthreads();
@@ -406,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 6) first_pass_kernel(const double* _
 // counted instead of listed enter its histograms and extremes where they
 // match.
 template <int NQ>
-__global__ void __launch_bounds__(kThreads, 4) pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
+__global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const double* __restrict__ ylt, int64_t n, int n_p,
                                                         SelState* __restrict__ st, LayerState* __restrict__ ls,
                                                         unsigned long long* __restrict__ cand, bool second,
                                                         unsigned int* __restrict__ ghist,
@@ -420,7 +465,8 @@ __global__ void __launch_bounds__(kThreads, 4) pass_kernel(const double* __restr
     const int j = blockIdx.y;
     const unsigned lane = threadIdx.x & 31;
     const int stage = ls[j].stage;
-    const bool compact = ls[j].compact != 0;
+    const int mode = ls[j].compact;
+    const bool compact = mode != kListNone;
     const unsigned long long kmax_l = ls[j].kmax;
     // pass 2 always runs (the layer sums); later passes only while a digit is left
     if (stage >= kPasses && !second) return;  // the same for every block of the layer: no ticket
@@ -462,7 +508,6 @@ __global__ void __launch_bounds__(kThreads, 4) pass_kernel(const double* __restr
         kiv[q] = 0;
     }
     Fix sum{0, 0, 0};
-    unsigned long long cmax = 0;
     __syncthreads();
     const unsigned dmask = (unsigned)nb - 1u;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -476,25 +521,39 @@ __global__ void __launch_bounds__(kThreads, 4) pass_kernel(const double* __restr
             valid[u] = i < len;
             v[u] = valid[u] ? __ldcs(src_vals + i) : 0.0;
         }
+        if (writing) {
+            // the step's list entries: one counter update per warp and step
+            unsigned m[kUnroll];
+            unsigned tot = 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;
+                bool in = key >> kShift1 >= lo_bucket;
+                if (mode == kListSelected) {
+                    in = false;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        in = in || (q < n_p && msk[q] != kAllKeyBits && (key & msk[q]) == pre[q]);
+                }
+                m[u] = __ballot_sync(0xffffffffu, in && key != 0ULL && key != kmax_l);
+                tot += __popc(m[u]);
+            }
+            if (tot) {
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(&ls[j].cand_n, tot);
+                base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const unsigned long long slot = (unsigned long long)base + __popc(m[u] & lt_mask);
+                    if (((m[u] >> lane) & 1u) && slot < cap) my_cand[slot] = key_of(v[u]);
+                    base += __popc(m[u]);
+                }
+            }
+        }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;
-            if (second) {
-                fix_add(sum, key, e_ref);  // invalid slots add 0
-                cmax += (valid[u] && key == kmax_l) ? 1 : 0;
-            }
-            if (writing) {
-                const bool c = key >> kShift1 >= lo_bucket && key != 0ULL && key != kmax_l;
-                const unsigned m = __ballot_sync(0xffffffffu, c);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    unsigned int base = 0;
-                    if (lane == (unsigned)leader) base = atomicAdd(&ls[j].cand_n, (unsigned)__popc(m));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    const unsigned long long slot = (unsigned long long)base + __popc(m & lt_mask);
-                    if (c && slot < cap) my_cand[slot] = key;
-                }
-            }
+            if (second) fix_add(sum, key, e_ref);  // invalid slots add 0
             if (histo) {
                 const unsigned dig = (unsigned)(key >> shift) & dmask;
 #pragma unroll
@@ -514,11 +573,7 @@ __global__ void __launch_bounds__(kThreads, 4) pass_kernel(const double* __restr
             }
         }
     }
-    if (second) {
-        fix_block_atomic(msum + 3 * (size_t)j, sum);
-        const unsigned long long m = block_sum_u64(cmax, sh_red_u);
-        if (threadIdx.x == 0 && m) atomicAdd(&ls[j].cnt_max, m);
-    }
+    if (second) fix_block_atomic(msum + 3 * (size_t)j, sum);
     if (!histo) return;  // nothing to pick: no ticket is taken by any block of the layer
     // a problem that shares its source's candidates shares its extremes
 #pragma unroll
@@ -629,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
     __shared__ bool sh_last;
     const int j = blockIdx.y;
     const int n_layers = gridDim.y;
-    const bool compact = ls[j].compact != 0;
+    const bool compact = ls[j].compact == kListAll;  // the list holds every key above the k-th largest
     const unsigned long long kmax_l = ls[j].kmax;
     const int e_ref = ref_exp(kmax_l);
     unsigned long long thr[NQ];
@@ -704,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
         const unsigned long long* g = tsum + 4 * (size_t)i;
         Fix f{__ldcg(g), __ldcg(g + 1), __ldcg(g + 2)};
         unsigned long long cnt = __ldcg(g + 3);
-        if (__ldcg(&ls[jj].compact) && kmx > sq.prefix) {
+        if (__ldcg(&ls[jj].compact) == kListAll && kmx > sq.prefix) {
             // the layer's largest keys were counted, not listed
             const unsigned long long cm = __ldcg(&ls[jj].cnt_max);
             fix_add_times(f, kmx, er, cm);
@@ -828,14 +883,15 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // zero + zero_bytes) must be zero when the call starts; the rest is written
 // before it is read. The candidate lists take cand_slots 8-byte keys.
 struct MetricsLayout {
-    size_t st, ls, hist1, hist, minmax, tickets, msum, tsum, cand;
+    size_t pmax, st, ls, hist1, hist, minmax, tickets, msum, tsum, cand;
     size_t zero, zero_bytes, total;
 };
 
-MetricsLayout metrics_layout(int32_t n_layers, int32_t n_p, uint64_t cand_slots) {
+MetricsLayout metrics_layout(int32_t n_layers, int32_t n_p, int nblk, uint64_t cand_slots) {
     const size_t L = (size_t)n_layers, np = (size_t)n_layers * n_p;
     MetricsLayout m{};
-    m.st = 0;
+    m.pmax = 0;
+    m.st = align256(m.pmax + sizeof(unsigned long long) * 2 * L * (size_t)nblk);
     m.ls = align256(m.st + sizeof(SelState) * np);
     m.hist1 = align256(m.ls + sizeof(LayerState) * L);
     m.hist = align256(m.hist1 + sizeof(unsigned int) * kBins1 * L);
@@ -864,6 +920,7 @@ uint64_t default_cand_slots(int64_t n, int32_t n_layers) {
 cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers, int32_t n_p, const KParams& kq,
                                   int nblk, char* w, const MetricsLayout& m, uint64_t cand_slots, double* mean,
                                   double* pml, double* tvar, double* sum_out, cudaStream_t s) {
+    auto* pmax = (unsigned long long*)(w + m.pmax);
     auto* st = (SelState*)(w + m.st);
     auto* ls = (LayerState*)(w + m.ls);
     auto* hist1 = (unsigned int*)(w + m.hist1);
@@ -876,8 +933,8 @@ cudaError_t launch_metric_kernels(const double* ylt, int64_t n, int32_t n_layers
     cudaError_t err = cudaMemsetAsync(w + m.zero, 0, m.zero_bytes, s);
     if (err) return err;
     const dim3 grid(nblk, n_layers);
-    first_pass_kernel<<<grid, kThreads, sizeof(unsigned int) * kBins1, s>>>(ylt, n, n_p, kq, st, ls, hist1, tickets,
-                                                                            cand_slots);
+    first_pass_kernel<<<grid, kThreads, sizeof(unsigned int) * kBins1, s>>>(ylt, n, n_p, kq, st, ls, hist1, pmax,
+                                                                            tickets, cand_slots);
     if ((err = cudaGetLastError())) return err;
     // the probability loops are compiled for 1, 2, 4 or 8 problems per layer
     auto pass_k = n_p <= 1 ? pass_kernel<1> : n_p <= 2 ? pass_kernel<2> : n_p <= 4 ? pass_kernel<4> : pass_kernel<8>;
@@ -906,7 +963,7 @@ int64_t tail_count(double p, int64_t n) {
 }
 
 size_t metrics_scratch_bytes(int64_t n, int32_t n_layers, int32_t n_p) {
-    return metrics_layout(n_layers, n_p, default_cand_slots(n, n_layers)).total;
+    return metrics_layout(n_layers, n_p, blocks_per_layer(n, n_layers), default_cand_slots(n, n_layers)).total;
 }
 
 cudaError_t metrics_run_k(const double* ylt, int64_t n, int32_t n_layers, const int64_t* k, int32_t n_p,
@@ -914,7 +971,7 @@ cudaError_t metrics_run_k(const double* ylt, int64_t n, int32_t n_layers, const 
                           void* scratch, size_t scratch_bytes) {
     const int nblk = blocks_per_layer(n, n_layers);
     const uint64_t slots = default_cand_slots(n, n_layers);
-    const MetricsLayout m = metrics_layout(n_layers, n_p, slots);
+    const MetricsLayout m = metrics_layout(n_layers, n_p, nblk, slots);
     char* w = static_cast<char*>(scratch);
     const bool own = !w || scratch_bytes < m.total;
     cudaError_t err = own ? cudaMallocAsync((void**)&w, m.total, s) : cudaSuccess;
@@ -1066,11 +1123,11 @@ extern "C" art_status art_metrics_noalloc(const double* ylt_dev, int64_t n_trial
     const int nblk = blocks_per_layer(n_trials, n_layers);
     // the fixed part must fit; what is left holds candidate lists (layers
     // whose lists do not fit read their whole row in every pass instead)
-    const MetricsLayout fixed = metrics_layout(n_layers, n_p, 0);
+    const MetricsLayout fixed = metrics_layout(n_layers, n_p, nblk, 0);
     if (fixed.total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
     const uint64_t slots = std::min<uint64_t>(((size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES - fixed.total) / 8,
                                               default_cand_slots(n_trials, n_layers));
-    const MetricsLayout m = metrics_layout(n_layers, n_p, slots);
+    const MetricsLayout m = metrics_layout(n_layers, n_p, nblk, slots);
     if (m.total > (size_t)ART_METRICS_NOALLOC_SCRATCH_BYTES) return ART_EINVAL;
     unsigned char* w = nullptr;
     cudaError_t err = noalloc_scratch(&w);

@@ -282,11 +282,6 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGrou
         }
         int qn = 0;  // warp-uniform queue length, < 32 between steps
         bool capped_exit = false;
-        // COMPACT: each batch's row is added at the next batch, so that its
-        // gather completes while the warp tests further events (the order of
-        // the additions is unchanged)
-        float pend[COMPACT ? LP : 1];
-        bool has_pend = false;  // warp-uniform
         if (n == 0 && tn < y.n_trials) load_chunk<E, VEC>(tidn, 0, nn, lane, pre);
         for (int32_t c0 = 0; c0 < n; c0 += 32 * E) {
             int32_t id[E];
@@ -341,10 +336,7 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGrou
                         qn -= 32;
                         float o[LP];
                         ld_occ_row<LP>(g.occ, mine, o);
-                        if (has_pend) add_occ<LT>(pend, hi, lo);
-#pragma unroll
-                        for (int j = 0; j < LP; ++j) pend[j] = o[j];
-                        has_pend = true;
+                        add_occ<LT>(o, hi, lo);
                         __syncwarp();
                     }
                 }
@@ -376,7 +368,6 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGrou
             }
         }
         if constexpr (COMPACT) {
-            if (has_pend && !capped_exit) add_occ<LT>(pend, hi, lo);
             __syncwarp();
             if (lane < qn) {
                 float o[LP];

@@ -232,26 +232,15 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
             sum[j] = 0.0;
             sum2[j] = 0.0;
         }
-        // each batch's row is added at the next batch, so that its gather
-        // completes while the warp tests further events (the order of the
-        // additions is unchanged)
-        double pend[LT];
-        bool has_pend = false;  // warp-uniform
-        auto add_pend = [&]() {
-#pragma unroll
-            for (int j = 0; j < LT; ++j) {
-                if (odd) sum2[j] += pend[j];
-                else sum[j] += pend[j];
-            }
-            odd = !odd;
-        };
         auto add_row = [&](uint32_t id) {
             double o[LT];
             ld_row64<LT>(g.occ64, id, o);
-            if (has_pend) add_pend();
 #pragma unroll
-            for (int j = 0; j < LT; ++j) pend[j] = o[j];
-            has_pend = true;
+            for (int j = 0; j < LT; ++j) {
+                if (odd) sum2[j] += o[j];
+                else sum[j] += o[j];
+            }
+            odd = !odd;
         };
         // ids of a chunk of 32 * E events from c0; empty slots read as -1
         auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
@@ -330,11 +319,8 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
                 }
             }
         }
-        if (has_pend && !capped_exit) add_pend();
-        has_pend = false;
         __syncwarp();
         if (lane < qn) add_row((uint32_t)q[lane]);
-        if (has_pend) add_pend();  // the last partial batch (its lanes only)
         __syncwarp();
         double mine = 0.0;
 #pragma unroll
