@@ -828,7 +828,8 @@ def main():
                 art.art_run_ylt_host_metrics(p, T, ids_h, off_h, K, probs, ylt=ylt_h, mean=mean_h, pml=pml_h,
                                              tvar=tvar_h, stream=stream)
 
-        e2e_step()  # grows the staging and device YLT buffers
+        for _ in range(args.warmup):  # the first calls grow the staging, YLT and scratch buffers
+            e2e_step()
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)

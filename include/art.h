@@ -113,7 +113,9 @@ enum {
 /* Flags. */
 enum {
     ART_FLAG_L2_PERSIST = 1,  /* set a persisting L2 access-policy window over the hot
-                                 table on the stream passed to each run call          */
+                                 table on the stream passed to each run call (the skip
+                                 variant: over each occurrence group's table during
+                                 that group's pass; the window is cleared afterwards) */
     ART_FLAG_GRAPH = 2,       /* art_run_ylt captures its launches (any variant) in a CUDA
                                  graph once per argument set and replays it            */
     ART_FLAG_EARLY_EXIT = 4   /* skip variant: stop reading a trial once every layer of the

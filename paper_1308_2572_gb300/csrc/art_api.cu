@@ -822,7 +822,9 @@ art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t* event_
         e = cudaGraphLaunch(p->graph_exec, stream);
         return e ? fail(e) : ART_OK;
     }
-    const bool window = (p->flags & ART_FLAG_L2_PERSIST) != 0 && variant != ART_VARIANT_PLAIN;
+    // the skip variant sets its own windows, one per occurrence group
+    const bool window = (p->flags & ART_FLAG_L2_PERSIST) != 0 && variant != ART_VARIANT_PLAIN &&
+                        variant != ART_VARIANT_SKIP;
     if (window) set_window(stream, variant == ART_VARIANT_FP64 ? (const void*)p->pool64 : (const void*)p->pool,
                            variant == ART_VARIANT_FP64 ? p->pool64_bytes : p->pool_bytes);
     e = run_forward(p, variant, y, ylt_dev, branch_dev, stream);

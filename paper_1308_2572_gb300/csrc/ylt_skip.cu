@@ -548,7 +548,12 @@ cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t
     // steps 2-3 once per catalogue event, with the terms as they are now
     cudaError_t err = build ? build_occurrence(p, s) : cudaSuccess;
     if (err != cudaSuccess || y.n_trials == 0) return err;
+    // ART_FLAG_L2_PERSIST: a persisting window over the table each group
+    // pass gathers from, so that the id stream does not evict it
+    const bool window = (p->flags & ART_FLAG_L2_PERSIST) != 0;
+    const size_t table_bytes = sizeof(float) * ((size_t)p->catalogue + 1) * (size_t)p->og_lp;
     for (const OccGroupArgs& g : p->ogroups) {
+        if (window && (err = set_window(s, g.occ, table_bytes))) return err;
         switch (p->og_lp) {
             case 1: err = launch_group<1, 1>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
             case 2: err = launch_group<2, 2>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;
@@ -558,7 +563,7 @@ cudaError_t launch_skip(art_portfolio* p, const YetArgs& y, double* ylt, uint8_t
         }
         if (err != cudaSuccess) return err;
     }
-    return cudaSuccess;
+    return window ? set_window(s, nullptr, 0) : cudaSuccess;
 }
 
 }  // namespace art
