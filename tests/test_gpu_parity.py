@@ -286,6 +286,30 @@ def test_host_buffers_with_metrics_match_device_path():
             p.close()
 
 
+def test_l2_persist_flag_keeps_results():
+    """ART_FLAG_L2_PERSIST (a persisting L2 window per occurrence group for
+    the skip variant, over the pool table for the batched ones) changes no
+    bit of the YLT, launched directly and from a captured graph."""
+    w = workloads.random_case(208, catalogue=40009, n_elt=30, n_layers=19, n_trials=3000, max_len=200,
+                              nnz_frac=0.05)
+    ref_p = art.portfolio_from_workload(w, layouts=ALL_LAYOUTS)
+    p = art.portfolio_from_workload(w, layouts=ALL_LAYOUTS, flags=art.ART_FLAG_L2_PERSIST)
+    try:
+        yet = device_yet(w)
+        for v in (art.ART_VARIANT_SKIP, art.ART_VARIANT_BATCHED, art.ART_VARIANT_SPARSE):
+            want, _ = run_ylt(ref_p, w, v, yet=yet)
+            got, _ = run_ylt(p, w, v, yet=yet)
+            assert torch.equal(got, want), v
+            art.art_set_flags(p, art.ART_FLAG_L2_PERSIST | art.ART_FLAG_GRAPH)
+            for _ in range(2):
+                got, _ = run_ylt(p, w, v, yet=yet)
+                assert torch.equal(got, want), ("graph", v)
+            art.art_set_flags(p, art.ART_FLAG_L2_PERSIST)
+    finally:
+        p.close()
+        ref_p.close()
+
+
 def test_out_of_range_ids_flag_without_trapping():
     w = workloads.random_case(203, n_trials=50, min_len=5, max_len=20)
     ids = w.yet.event_ids.copy()
