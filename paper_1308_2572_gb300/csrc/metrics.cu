@@ -33,13 +33,14 @@
 // A layer without a list histograms its second digit in pass 2 and reads its
 // whole row in every later pass.
 //
-// Every sum is an exact integer: a value's 53-bit mantissa, shifted to its
-// place in a 192-bit fixed-point number whose unit is 2^-108 times the
-// layer's largest binary exponent, added with carries (values below the
-// unit keep the bits above it). Integer additions give the same bits in any
-// order, so blocks add their sums with atomics, and the streaming passes use
-// no FP64 arithmetic (of which this GPU has little). One conversion to FP64
-// (three roundings) ends each sum.
+// Every sum is an integer: a value's 53-bit mantissa, shifted to its place
+// in a 128-bit fixed-point number whose unit is 2^-96 of the layer's largest
+// binary power, added with a carry (bits below the unit are dropped: each
+// sum holds the layer's largest loss, so that is at most 2^-96 N of it).
+// Integer additions give the same bits in any order, so blocks add their
+// sums with atomics, and the streaming passes use no FP64 arithmetic (of
+// which this GPU has little). One conversion to FP64 (two roundings) ends
+// each sum.
 #include <algorithm>
 #include <cmath>
 
@@ -59,7 +60,7 @@ __host__ __device__ constexpr int pass_shift(int i) { return i == 0 ? kShift1 : 
 __host__ __device__ constexpr int pass_bits(int i) { return i == 0 ? 13 : (i < 5 ? 11 : 6); }
 constexpr unsigned long long kAllKeyBits = 0x7fffffffffffffffULL;  // a decided problem's mask
 constexpr unsigned long long kMant = (1ULL << 52) - 1;
-constexpr int kFixBits = 108;     // fixed-point unit: 2^(e_ref - 1075 - kFixBits)
+constexpr int kFixBits = 44;      // fixed-point unit: 2^(e_ref - 1075 - kFixBits)
 
 struct KParams {
     long long k[kMaxProbs];
@@ -101,15 +102,20 @@ __device__ __forceinline__ unsigned long long key_of(double v) {
 // field (at least 1, the subnormals' scale).
 __device__ __forceinline__ int ref_exp(unsigned long long kmax) { return max(1, (int)(kmax >> 52)); }
 
-// An exact 192-bit sum in units of 2^(e_ref - 1075 - kFixBits).
+// A fixed-point sum: a 128-bit integer in units of 2^(e_ref - 1075 - kFixBits),
+// e_ref the layer's largest binary exponent. A key's mantissa shifted to its
+// place is below 2^(53 + kFixBits), so 2^31 of them stay below 2^128; bits
+// below the unit are dropped, at most N units in all, which is 2^-96 N of the
+// layer's largest loss -- and every sum taken here holds that loss (the
+// mean's, and the sum of each problem's largest keys).
 struct Fix {
-    unsigned long long w0, w1, w2;
+    unsigned long long lo, hi;
 };
 
-// The key's value in those units as three words (the mantissa shifted to its
-// place; bits below the unit dropped). e_ref is at least the key's exponent.
+// The key's value in those units as two words. e_ref is at least the key's
+// exponent.
 __device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, unsigned long long& a0,
-                                          unsigned long long& a1, unsigned long long& a2) {
+                                          unsigned long long& a1) {
     const int e = (int)(key >> 52);
     unsigned long long m = (key & kMant) | (e ? (1ULL << 52) : 0ULL);
     int sh = max(e, 1) - e_ref + kFixBits;  // <= kFixBits
@@ -117,68 +123,47 @@ __device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, uns
         m = -sh < 64 ? m >> -sh : 0ULL;
         sh = 0;
     }
-    const int b = sh & 63;
-    const unsigned long long lo = m << b, hi = b ? m >> (64 - b) : 0ULL;
-    const bool w1 = sh >= 64;
-    a0 = w1 ? 0ULL : lo;
-    a1 = w1 ? lo : hi;
-    a2 = w1 ? hi : 0ULL;
+    a0 = m << sh;
+    a1 = sh > 11 ? m >> (64 - sh) : 0ULL;
 }
 
-__device__ __forceinline__ void fix_add3(Fix& f, unsigned long long a0, unsigned long long a1, unsigned long long a2) {
-    f.w0 += a0;
-    const unsigned long long c0 = f.w0 < a0 ? 1ULL : 0ULL;
-    const unsigned long long t = a1 + c0;
-    const unsigned long long c0b = t < a1 ? 1ULL : 0ULL;
-    f.w1 += t;
-    const unsigned long long c1 = f.w1 < t ? 1ULL : 0ULL;
-    f.w2 += a2 + c0b + c1;
+__device__ __forceinline__ void fix_add2(Fix& f, unsigned long long a0, unsigned long long a1) {
+    f.lo += a0;
+    f.hi += a1 + (f.lo < a0 ? 1ULL : 0ULL);
 }
 
 __device__ __forceinline__ void fix_add(Fix& f, unsigned long long key, int e_ref) {
-    unsigned long long a0, a1, a2;
-    fix_words(key, e_ref, a0, a1, a2);
-    fix_add3(f, a0, a1, a2);
+    unsigned long long a0, a1;
+    fix_words(key, e_ref, a0, a1);
+    fix_add2(f, a0, a1);
 }
 
 // f += c * key (c < 2^32), exactly.
 __device__ __forceinline__ void fix_add_times(Fix& f, unsigned long long key, int e_ref, unsigned long long c) {
-    unsigned long long a0, a1, a2;
-    fix_words(key, e_ref, a0, a1, a2);
-    const unsigned long long p0 = a0 * c, p0h = __umul64hi(a0, c);
-    const unsigned long long p1 = a1 * c, p1h = __umul64hi(a1, c);
-    const unsigned long long p2 = a2 * c;
-    const unsigned long long r1 = p0h + p1;
-    const unsigned long long cr = r1 < p1 ? 1ULL : 0ULL;
-    fix_add3(f, p0, r1, p1h + p2 + cr);
+    unsigned long long a0, a1;
+    fix_words(key, e_ref, a0, a1);
+    fix_add2(f, a0 * c, __umul64hi(a0, c) + a1 * c);
 }
 
 // Sum over the warp (valid in every lane).
 __device__ __forceinline__ Fix fix_warp_sum(Fix f) {
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, f.w0, o);
-        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, f.w1, o);
-        const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, f.w2, o);
-        fix_add3(f, b0, b1, b2);
+        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, f.lo, o);
+        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, f.hi, o);
+        fix_add2(f, b0, b1);
     }
     return f;
 }
 
-// g[0..2] += f with integer atomics and carries (the running total stays
-// below 2^192, so no carry leaves the top word).
+// g[0..1] += f with integer atomics and the carry.
 __device__ __forceinline__ void fix_atomic(unsigned long long* g, const Fix& f) {
-    if (!(f.w0 | f.w1 | f.w2)) return;
-    const unsigned long long o0 = atomicAdd(g, f.w0);
-    const unsigned long long c0 = o0 + f.w0 < o0 ? 1ULL : 0ULL;
-    const unsigned long long t = f.w1 + c0;
-    const unsigned long long c0b = t < f.w1 ? 1ULL : 0ULL;
-    const unsigned long long o1 = atomicAdd(g + 1, t);
-    const unsigned long long c1 = o1 + t < o1 ? 1ULL : 0ULL;
-    const unsigned long long hi = f.w2 + c0b + c1;
-    if (hi) atomicAdd(g + 2, hi);
+    if (!(f.lo | f.hi)) return;
+    const unsigned long long o0 = atomicAdd(g, f.lo);
+    const unsigned long long hi = f.hi + (o0 + f.lo < o0 ? 1ULL : 0ULL);
+    if (hi) atomicAdd(g + 1, hi);
 }
 
-// Block sum of a fixed-point value into g (one atomic triple per warp).
+// Block sum of a fixed-point value into g (one atomic pair per warp).
 __device__ __forceinline__ void fix_block_atomic(unsigned long long* g, Fix f) {
     f = fix_warp_sum(f);
     if ((threadIdx.x & 31) == 0) fix_atomic(g, f);
@@ -186,8 +171,7 @@ __device__ __forceinline__ void fix_block_atomic(unsigned long long* g, Fix f) {
 
 // The FP64 value of a fixed-point sum.
 __device__ __forceinline__ double fix_value(const Fix& f, int e_ref) {
-    const double two64 = 18446744073709551616.0;
-    const double t = fma(fma((double)f.w2, two64, (double)f.w1), two64, (double)f.w0);
+    const double t = fma((double)f.hi, 18446744073709551616.0, (double)f.lo);
     return scalbn(t, e_ref - 1075 - kFixBits);
 }
 
@@ -499,7 +483,9 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
             if (r < q && !done[r] && !done[q] && pre[r] == pre[q] && msk[r] == msk[q]) src[q] = r;
         if (threadIdx.x == 0 && q < n_p) sh_src[q] = src[q];
     }
-    if (histo)
+    // a block with no value to read (a short list) only takes its ticket
+    const bool idle = (int64_t)blockIdx.x * blockDim.x * kUnroll >= len;
+    if (histo && !idle)
         for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) sh_hist[i] = 0;
     unsigned long long kmx[NQ], kiv[NQ];
 #pragma unroll
@@ -507,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
         kmx[q] = 0;
         kiv[q] = 0;
     }
-    Fix sum{0, 0, 0};
+    Fix sum{0, 0};
     __syncthreads();
     const unsigned dmask = (unsigned)nb - 1u;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -573,34 +559,36 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
             }
         }
     }
-    if (second) fix_block_atomic(msum + 3 * (size_t)j, sum);
+    if (second) fix_block_atomic(msum + 2 * (size_t)j, sum);
     if (!histo) return;  // nothing to pick: no ticket is taken by any block of the layer
-    // a problem that shares its source's candidates shares its extremes
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-#pragma unroll
-        for (int r = 0; r < NQ; ++r)
-            if (r < q && src[q] == r) {
-                kmx[q] = kmx[r];
-                kiv[q] = kiv[r];
-            }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        if (q >= n_p || done[q]) continue;
-        const unsigned long long a = block_max_u64(kmx[q], sh_red_u);
-        const unsigned long long b = block_max_u64(kiv[q], sh_red_u);
-        if (threadIdx.x == 0) {
-            if (a) atomicMax(&minmax[2 * ((size_t)j * n_p + q)], a);
-            if (b) atomicMax(&minmax[2 * ((size_t)j * n_p + q) + 1], b);
-        }
-    }
-    __syncthreads();
     unsigned int* gh = ghist + ((size_t)j * n_p) * kMaxBins;
-    for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
-        const int q = i >> bits, b = i & (int)dmask;
-        const unsigned c = sh_hist[sh_src[q] * nb + b];  // zero for a decided problem
-        if (c) atomicAdd(&gh[(size_t)q * kMaxBins + b], c);
+    if (!idle) {
+        // a problem that shares its source's candidates shares its extremes
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+            for (int r = 0; r < NQ; ++r)
+                if (r < q && src[q] == r) {
+                    kmx[q] = kmx[r];
+                    kiv[q] = kiv[r];
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (q >= n_p || done[q]) continue;
+            const unsigned long long a = block_max_u64(kmx[q], sh_red_u);
+            const unsigned long long b = block_max_u64(kiv[q], sh_red_u);
+            if (threadIdx.x == 0) {
+                if (a) atomicMax(&minmax[2 * ((size_t)j * n_p + q)], a);
+                if (b) atomicMax(&minmax[2 * ((size_t)j * n_p + q) + 1], b);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_p * nb; i += blockDim.x) {
+            const int q = i >> bits, b = i & (int)dmask;
+            const unsigned c = sh_hist[sh_src[q] * nb + b];  // zero for a decided problem
+            if (c) atomicAdd(&gh[(size_t)q * kMaxBins + b], c);
+        }
     }
     __threadfence();
     __syncthreads();
@@ -704,7 +692,7 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
     unsigned long long c[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        s[q] = Fix{0, 0, 0};
+        s[q] = Fix{0, 0};
         c[q] = 0;
     }
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
@@ -718,12 +706,12 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const unsigned long long key = key_of(v[u]);
-            unsigned long long a0, a1, a2;
-            fix_words(key, e_ref, a0, a1, a2);
+            unsigned long long a0, a1;
+            fix_words(key, e_ref, a0, a1);
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
                 if (live[q] && key > thr[q]) {
-                    fix_add3(s[q], a0, a1, a2);
+                    fix_add2(s[q], a0, a1);
                     c[q] += 1;
                 }
         }
@@ -731,10 +719,10 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         if (!live[q]) continue;
-        unsigned long long* g = tsum + 4 * ((size_t)j * n_p + q);
+        unsigned long long* g = tsum + 3 * ((size_t)j * n_p + q);
         fix_block_atomic(g, s[q]);
         const unsigned long long cc = block_sum_u64(c[q], sh_red_u);
-        if (threadIdx.x == 0 && cc) atomicAdd(g + 3, cc);
+        if (threadIdx.x == 0 && cc) atomicAdd(g + 2, cc);
     }
     __threadfence();
     __syncthreads();
@@ -742,23 +730,21 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int i = wib; i < n_layers * n_p; i += kThreads / 32) {
-        if (lane != 0) continue;
+    // every problem's sums converted, one thread per problem
+    for (int i = threadIdx.x; i < n_layers * n_p; i += blockDim.x) {
         const int jj = i / n_p, q = i % n_p;
         const SelState sq = st[i];
         const unsigned long long kmx = __ldcg(&ls[jj].kmax);
         const int er = ref_exp(kmx);
         if (q == 0) {
-            const Fix ms{__ldcg(msum + 3 * (size_t)jj), __ldcg(msum + 3 * (size_t)jj + 1),
-                         __ldcg(msum + 3 * (size_t)jj + 2)};
+            const Fix ms{__ldcg(msum + 2 * (size_t)jj), __ldcg(msum + 2 * (size_t)jj + 1)};
             const double total = fix_value(ms, er);
             if (mean) mean[jj] = total / (double)n;
             if (sum_out) sum_out[jj] = total;
         }
-        const unsigned long long* g = tsum + 4 * (size_t)i;
-        Fix f{__ldcg(g), __ldcg(g + 1), __ldcg(g + 2)};
-        unsigned long long cnt = __ldcg(g + 3);
+        const unsigned long long* g = tsum + 3 * (size_t)i;
+        Fix f{__ldcg(g), __ldcg(g + 1)};
+        unsigned long long cnt = __ldcg(g + 2);
         if (__ldcg(&ls[jj].compact) == kListAll && kmx > sq.prefix) {
             // the layer's largest keys were counted, not listed
             const unsigned long long cm = __ldcg(&ls[jj].cnt_max);
@@ -898,8 +884,8 @@ MetricsLayout metrics_layout(int32_t n_layers, int32_t n_p, int nblk, uint64_t c
     m.minmax = align256(m.hist + sizeof(unsigned int) * kMaxBins * np);
     m.tickets = align256(m.minmax + sizeof(unsigned long long) * 2 * np);
     m.msum = align256(m.tickets + sizeof(unsigned int) * (L + 2));
-    m.tsum = align256(m.msum + sizeof(unsigned long long) * 3 * L);
-    m.cand = align256(m.tsum + sizeof(unsigned long long) * 4 * np);
+    m.tsum = align256(m.msum + sizeof(unsigned long long) * 2 * L);
+    m.cand = align256(m.tsum + sizeof(unsigned long long) * 3 * np);
     m.zero = m.ls;
     m.zero_bytes = m.cand - m.ls;
     m.total = align256(m.cand + sizeof(unsigned long long) * (size_t)cand_slots);
