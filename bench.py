@@ -648,8 +648,9 @@ def main():
                     help="further workloads timed after the headline (comma list, or none)")
     ap.add_argument("--graph", action="store_true",
                     help="ART_FLAG_GRAPH: the forward's launches replay from a captured CUDA graph")
-    ap.add_argument("--l2-persist", action="store_true",
-                    help="persisting L2 access-policy window over the hot table (ART_FLAG_L2_PERSIST)")
+    ap.add_argument("--no-l2-persist", action="store_true",
+                    help="no persisting L2 access-policy window over the gathered table (ART_FLAG_L2_PERSIST is "
+                         "set by default: 5% off the one-layer forward)")
     ap.add_argument("--trials", type=int, default=0,
                     help="keep only the first N trials (small cases for profiling; 0 = the full workload)")
     ap.add_argument("--layers", type=int, default=0,
@@ -696,6 +697,7 @@ def main():
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
     if args.config == "c3":
         layouts |= art.ART_LAYOUT_GROUP  # the adjoint reads the group tables
+    args.l2_persist = not args.no_l2_persist
     base_flags = (art.ART_FLAG_L2_PERSIST if args.l2_persist else 0) | (art.ART_FLAG_GRAPH if args.graph else 0)
     p = art.portfolio_from_workload(w, device=dev, layouts=layouts, flags=base_flags)
     ids = torch.from_numpy(yet.event_ids).to(dev)

@@ -98,6 +98,12 @@ __device__ __forceinline__ unsigned long long key_of(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
 
+// The key of p[i] read as a 64-bit integer (streaming: each value is read
+// once per pass), so that no FP64 instruction touches it.
+__device__ __forceinline__ unsigned long long ld_key(const unsigned long long* p, int64_t i) {
+    return __ldcs(p + i) & 0x7fffffffffffffffULL;
+}
+
 // Exponent of a layer's fixed-point unit: its largest key's binary exponent
 // field (at least 1, the subnormals' scale).
 __device__ __forceinline__ int ref_exp(unsigned long long kmax) { return max(1, (int)(kmax >> 52)); }
@@ -286,31 +292,42 @@ __global__ void __launch_bounds__(kThreads, 5) first_pass_kernel(const double* _
     const int n_layers = gridDim.y;
     for (int i = threadIdx.x; i < kBins1; i += blockDim.x) sh_hist[i] = 0;
     __syncthreads();
-    const double* row = ylt + (size_t)j * (size_t)n;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(ylt) + (size_t)j * (size_t)n;
     // the thread's largest key and how often it holds it; the smallest key
     unsigned long long kmax = 0, cmax = 0, kinv = 0, zeros = 0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < n;
          i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-        double v[kUnroll];
+        unsigned long long kv[kUnroll];
         bool valid[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
             valid[u] = i < n;
-            v[u] = valid[u] ? __ldcs(row + i) : 0.0;
+            kv[u] = valid[u] ? ld_key(row, i) : 0ULL;
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const unsigned long long key = key_of(v[u]);
+            const unsigned long long key = kv[u];
             if (valid[u]) {
-                if (key) atomicAdd(&sh_hist[key >> kShift1], 1u);
-                else ++zeros;
-                cmax = key > kmax ? 1ULL : cmax + (key == kmax ? 1ULL : 0ULL);
-                kmax = max(kmax, key);
+                // zeros and the thread's running largest key (trials at the
+                // aggregate cap) are counted in registers; a new largest key
+                // hands the old one's count to the histogram
+                if (key == 0ULL) {
+                    ++zeros;
+                } else if (key == kmax) {
+                    ++cmax;
+                } else if (key > kmax) {
+                    if (cmax) atomicAdd(&sh_hist[kmax >> kShift1], (unsigned)cmax);
+                    kmax = key;
+                    cmax = 1;
+                } else {
+                    atomicAdd(&sh_hist[key >> kShift1], 1u);
+                }
                 kinv = max(kinv, ~key);
             }
         }
     }
+    if (cmax) atomicAdd(&sh_hist[kmax >> kShift1], (unsigned)cmax);
     const unsigned long long a = block_max_u64(kmax, sh_red_u);
     __shared__ unsigned long long sh_bmax;
     if (threadIdx.x == 0) sh_bmax = a;
@@ -466,8 +483,9 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
         done[q] = !histo || q >= n_p || msk[q] == kAllKeyBits;
     }
     const bool from_row = second || !compact;
-    const double* src_vals = from_row ? ylt + (size_t)j * (size_t)n
-                                      : reinterpret_cast<const double*>(cand + ls[j].cand_off);
+    const unsigned long long* src_vals = from_row
+                                             ? reinterpret_cast<const unsigned long long*>(ylt) + (size_t)j * (size_t)n
+                                             : cand + ls[j].cand_off;
     const int64_t len = from_row ? n : (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need);
     const bool writing = second && compact && stage < kPasses;  // pass 2 writes the layer's list
     unsigned long long* my_cand = cand + ls[j].cand_off;
@@ -499,13 +517,13 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
          i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-        double v[kUnroll];
+        unsigned long long kv[kUnroll];  // keys (0 past the end)
         bool valid[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
             valid[u] = i < len;
-            v[u] = valid[u] ? __ldcs(src_vals + i) : 0.0;
+            kv[u] = valid[u] ? ld_key(src_vals, i) : 0ULL;
         }
         if (writing) {
             // the step's list entries: one counter update per warp and step
@@ -513,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
             unsigned tot = 0;
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;
+                const unsigned long long key = kv[u];
                 bool in = key >> kShift1 >= lo_bucket;
                 if (mode == kListSelected) {
                     in = false;
@@ -531,14 +549,14 @@ __global__ void __launch_bounds__(kThreads, NQ == 2 ? 3 : 4) pass_kernel(const d
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     const unsigned long long slot = (unsigned long long)base + __popc(m[u] & lt_mask);
-                    if (((m[u] >> lane) & 1u) && slot < cap) my_cand[slot] = key_of(v[u]);
+                    if (((m[u] >> lane) & 1u) && slot < cap) my_cand[slot] = kv[u];
                     base += __popc(m[u]);
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const unsigned long long key = valid[u] ? key_of(v[u]) : 0ULL;
+            const unsigned long long key = kv[u];
             if (second) fix_add(sum, key, e_ref);  // invalid slots add 0
             if (histo) {
                 const unsigned dig = (unsigned)(key >> shift) & dmask;
@@ -684,8 +702,9 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
         live[q] = q < n_p && thr[q] < kmax_l;  // nothing lies above the layer's largest key
         any_live = any_live || live[q];
     }
-    const double* src_vals = compact ? reinterpret_cast<const double*>(cand + ls[j].cand_off)
-                                     : ylt + (size_t)j * (size_t)n;
+    const unsigned long long* src_vals = compact
+                                             ? cand + ls[j].cand_off
+                                             : reinterpret_cast<const unsigned long long*>(ylt) + (size_t)j * (size_t)n;
     const int64_t len = !any_live ? 0
                         : compact ? (int64_t)min((unsigned long long)ls[j].cand_n, ls[j].need) : n;
     Fix s[NQ];
@@ -697,15 +716,15 @@ __global__ void __launch_bounds__(kThreads, NQ <= 4 ? 4 : 2) tail_kernel(const d
     }
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kUnroll; i0 < len;
          i0 += (int64_t)gridDim.x * blockDim.x * kUnroll) {
-        double v[kUnroll];
+        unsigned long long kv[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-            v[u] = i < len ? __ldcs(src_vals + i) : 0.0;  // 0: never above a k-th largest key
+            kv[u] = i < len ? ld_key(src_vals, i) : 0ULL;  // 0: never above a k-th largest key
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const unsigned long long key = key_of(v[u]);
+            const unsigned long long key = kv[u];
             unsigned long long a0, a1;
             fix_words(key, e_ref, a0, a1);
 #pragma unroll
