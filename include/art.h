@@ -80,8 +80,10 @@ enum {
     ART_VARIANT_BATCHED = 2,  /* one persistent launch over all layers (pool table)       */
     ART_VARIANT_FP64 = 3,     /* all-FP64 arithmetic: per call, FP64 occurrence losses of
                                  every catalogue event, then one trial pass per run of
-                                 <= 8 layers with FP64 sums (ART_LAYOUT_OCC64); else
-                                 batched over the FP64 pool (ART_LAYOUT_POOL64)           */
+                                 <= 4 layers that sums them exactly (integer fixed point,
+                                 one FP64 rounding per trial) and applies the aggregate
+                                 terms in FP64 (ART_LAYOUT_OCC64); else batched over the
+                                 FP64 pool with FP64 sums (ART_LAYOUT_POOL64)             */
     ART_VARIANT_SKIP = 4,     /* per call, the occurrence loss of every catalogue event
                                  for every layer (one build launch from the per-layer
                                  tables), then one trial pass per run of <= 8 layers that

@@ -398,6 +398,12 @@ cudaError_t build_occ_groups(art_portfolio* p) {
             }
         }
         if (e) return e;
+        if ((e = cudaMalloc(&p->d_occ64_max, sizeof(unsigned long long) * ng64))) return e;
+        if ((e = cudaMemset(p->d_occ64_max, 0, sizeof(unsigned long long) * ng64))) return e;
+        for (int32_t gi = 0; gi < ng64; ++gi) {
+            p->ogroups64[gi].maxkey = p->d_occ64_max + gi;
+            bg64[gi].maxkey = p->d_occ64_max + gi;
+        }
         if (p->pool_np > 0) {  // slots of each FP64 group holding each pool ELT (for the CSR build)
             std::vector<uint8_t> sm((size_t)ng64 * p->pool_np, 0);
             for (int32_t gi = 0; gi < ng64; ++gi)
@@ -483,6 +489,7 @@ void free_portfolio(art_portfolio* p) {
     for (uint32_t* b : p->og_bits64) cudaFree(b);
     cudaFree(p->d_ogroups64);
     cudaFree(p->d_occ64_ptrs);
+    cudaFree(p->d_occ64_max);
     cudaFree(p->d_slotmask64);
     cudaFree(p->pool);
     cudaFree(p->pool64);

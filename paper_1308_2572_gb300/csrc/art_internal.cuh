@@ -85,6 +85,91 @@ __device__ __forceinline__ void trial_range(const YetArgs& y, int64_t t, int64_t
 // Streaming loads (evict-first) for the YET, read exactly once per pass.
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 
+// Exact sums of non-negative FP64 values (the metrics' sums, the all-FP64
+// forward's aggregates). A value's bit pattern (its "key") orders like the
+// value; constexprs and helpers below work on keys.
+constexpr unsigned long long kMant = (1ULL << 52) - 1;
+constexpr int kFixBits = 44;  // fixed-point unit: 2^(e_ref - 1075 - kFixBits)
+
+// Exponent of a fixed-point unit's reference: the largest key's binary
+// exponent field (at least 1, the subnormals' scale).
+__device__ __forceinline__ int ref_exp(unsigned long long kmax) { return max(1, (int)(kmax >> 52)); }
+
+// A fixed-point sum: a 128-bit integer in units of 2^(e_ref - 1075 - kFixBits),
+// e_ref the reference exponent of the summed values (that of the largest
+// value that may occur). A key's mantissa shifted to its place is below
+// 2^(53 + kFixBits), so 2^31 of them stay below 2^128. Bits below the unit
+// are dropped: at most one unit, 2^-96 of the reference value, per term
+// (the metrics' sums all hold the reference value itself; the all-FP64
+// forward's aggregate sums at most a trial's events). Integer additions give
+// the same bits in any order.
+struct Fix {
+    unsigned long long lo, hi;
+};
+
+// The key's value in those units as two words. e_ref is at least the key's
+// exponent.
+__device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, unsigned long long& a0,
+                                          unsigned long long& a1) {
+    const int e = (int)(key >> 52);
+    unsigned long long m = (key & kMant) | (e ? (1ULL << 52) : 0ULL);
+    int sh = max(e, 1) - e_ref + kFixBits;  // <= kFixBits
+    if (sh < 0) {
+        m = -sh < 64 ? m >> -sh : 0ULL;
+        sh = 0;
+    }
+    a0 = m << sh;
+    a1 = sh > 11 ? m >> (64 - sh) : 0ULL;
+}
+
+__device__ __forceinline__ void fix_add2(Fix& f, unsigned long long a0, unsigned long long a1) {
+    f.lo += a0;
+    f.hi += a1 + (f.lo < a0 ? 1ULL : 0ULL);
+}
+
+__device__ __forceinline__ void fix_add(Fix& f, unsigned long long key, int e_ref) {
+    unsigned long long a0, a1;
+    fix_words(key, e_ref, a0, a1);
+    fix_add2(f, a0, a1);
+}
+
+// f += c * key (c < 2^32), exactly.
+__device__ __forceinline__ void fix_add_times(Fix& f, unsigned long long key, int e_ref, unsigned long long c) {
+    unsigned long long a0, a1;
+    fix_words(key, e_ref, a0, a1);
+    fix_add2(f, a0 * c, __umul64hi(a0, c) + a1 * c);
+}
+
+// Sum over the warp (valid in every lane).
+__device__ __forceinline__ Fix fix_warp_sum(Fix f) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, f.lo, o);
+        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, f.hi, o);
+        fix_add2(f, b0, b1);
+    }
+    return f;
+}
+
+// g[0..1] += f with integer atomics and the carry.
+__device__ __forceinline__ void fix_atomic(unsigned long long* g, const Fix& f) {
+    if (!(f.lo | f.hi)) return;
+    const unsigned long long o0 = atomicAdd(g, f.lo);
+    const unsigned long long hi = f.hi + (o0 + f.lo < o0 ? 1ULL : 0ULL);
+    if (hi) atomicAdd(g + 1, hi);
+}
+
+// Block sum of a fixed-point value into g (one atomic pair per warp).
+__device__ __forceinline__ void fix_block_atomic(unsigned long long* g, Fix f) {
+    f = fix_warp_sum(f);
+    if ((threadIdx.x & 31) == 0) fix_atomic(g, f);
+}
+
+// The FP64 value of a fixed-point sum.
+__device__ __forceinline__ double fix_value(const Fix& f, int e_ref) {
+    const double t = fma((double)f.hi, 18446744073709551616.0, (double)f.lo);
+    return scalbn(t, e_ref - 1075 - kFixBits);
+}
+
 // Batched layout description shared by the host and the batched kernels.
 struct BatchedArgs {
     const void* pool;          // [C][pool_np] FP32 or FP64
@@ -154,6 +239,7 @@ constexpr int kMaxOcc64Layers = 4;  // layers per FP64 occurrence group
 struct OccGroupArgs {
     const float* occ;          // [C + 1][lt_pad] FP32
     const double* occ64;       // [C + 1][lt_pad] FP64 (the all-FP64 tables)
+    const unsigned long long* maxkey;  // the FP64 table's largest entry (its key), written by the build
     const uint32_t* occ_bits;  // bits 0 .. C, zero-padded to whole 16-byte groups
     int32_t layer[kMaxOccLayers];
     double agg_ret[kMaxOccLayers], agg_lim[kMaxOccLayers];
@@ -176,6 +262,7 @@ struct LayerBuildArgs {
 struct OccBuildGroup {
     float* occ;
     uint32_t* occ_bits;
+    unsigned long long* maxkey;  // FP64 groups: the table's largest entry (atomic maximum of keys)
     int32_t layer[kMaxOccLayers];
     int32_t n_layers;
 };
@@ -229,6 +316,7 @@ struct art_portfolio {
     std::vector<uint32_t*> og_bits64;
     art::OccBuildGroup* d_ogroups64 = nullptr;  // bitmaps of the FP64 tables
     double** d_occ64_ptrs = nullptr;            // [n_ogroups64]
+    unsigned long long* d_occ64_max = nullptr;  // [n_ogroups64]: each FP64 table's largest entry
     int32_t og_lp64 = 0;                        // slots per row of the FP64 tables (1, 2 or 4)
     uint8_t* d_slotmask64 = nullptr;            // [n_ogroups64][pool_np]: slots of the group holding the ELT
     int64_t occ64_bytes = 0;

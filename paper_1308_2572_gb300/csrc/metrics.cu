@@ -59,8 +59,6 @@ constexpr int kShift1 = 50;
 __host__ __device__ constexpr int pass_shift(int i) { return i == 0 ? kShift1 : (i < 5 ? kShift1 - 11 * i : 0); }
 __host__ __device__ constexpr int pass_bits(int i) { return i == 0 ? 13 : (i < 5 ? 11 : 6); }
 constexpr unsigned long long kAllKeyBits = 0x7fffffffffffffffULL;  // a decided problem's mask
-constexpr unsigned long long kMant = (1ULL << 52) - 1;
-constexpr int kFixBits = 44;      // fixed-point unit: 2^(e_ref - 1075 - kFixBits)
 
 struct KParams {
     long long k[kMaxProbs];
@@ -104,82 +102,6 @@ __device__ __forceinline__ unsigned long long ld_key(const unsigned long long* p
     return __ldcs(p + i) & 0x7fffffffffffffffULL;
 }
 
-// Exponent of a layer's fixed-point unit: its largest key's binary exponent
-// field (at least 1, the subnormals' scale).
-__device__ __forceinline__ int ref_exp(unsigned long long kmax) { return max(1, (int)(kmax >> 52)); }
-
-// A fixed-point sum: a 128-bit integer in units of 2^(e_ref - 1075 - kFixBits),
-// e_ref the layer's largest binary exponent. A key's mantissa shifted to its
-// place is below 2^(53 + kFixBits), so 2^31 of them stay below 2^128; bits
-// below the unit are dropped, at most N units in all, which is 2^-96 N of the
-// layer's largest loss -- and every sum taken here holds that loss (the
-// mean's, and the sum of each problem's largest keys).
-struct Fix {
-    unsigned long long lo, hi;
-};
-
-// The key's value in those units as two words. e_ref is at least the key's
-// exponent.
-__device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, unsigned long long& a0,
-                                          unsigned long long& a1) {
-    const int e = (int)(key >> 52);
-    unsigned long long m = (key & kMant) | (e ? (1ULL << 52) : 0ULL);
-    int sh = max(e, 1) - e_ref + kFixBits;  // <= kFixBits
-    if (sh < 0) {
-        m = -sh < 64 ? m >> -sh : 0ULL;
-        sh = 0;
-    }
-    a0 = m << sh;
-    a1 = sh > 11 ? m >> (64 - sh) : 0ULL;
-}
-
-__device__ __forceinline__ void fix_add2(Fix& f, unsigned long long a0, unsigned long long a1) {
-    f.lo += a0;
-    f.hi += a1 + (f.lo < a0 ? 1ULL : 0ULL);
-}
-
-__device__ __forceinline__ void fix_add(Fix& f, unsigned long long key, int e_ref) {
-    unsigned long long a0, a1;
-    fix_words(key, e_ref, a0, a1);
-    fix_add2(f, a0, a1);
-}
-
-// f += c * key (c < 2^32), exactly.
-__device__ __forceinline__ void fix_add_times(Fix& f, unsigned long long key, int e_ref, unsigned long long c) {
-    unsigned long long a0, a1;
-    fix_words(key, e_ref, a0, a1);
-    fix_add2(f, a0 * c, __umul64hi(a0, c) + a1 * c);
-}
-
-// Sum over the warp (valid in every lane).
-__device__ __forceinline__ Fix fix_warp_sum(Fix f) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, f.lo, o);
-        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, f.hi, o);
-        fix_add2(f, b0, b1);
-    }
-    return f;
-}
-
-// g[0..1] += f with integer atomics and the carry.
-__device__ __forceinline__ void fix_atomic(unsigned long long* g, const Fix& f) {
-    if (!(f.lo | f.hi)) return;
-    const unsigned long long o0 = atomicAdd(g, f.lo);
-    const unsigned long long hi = f.hi + (o0 + f.lo < o0 ? 1ULL : 0ULL);
-    if (hi) atomicAdd(g + 1, hi);
-}
-
-// Block sum of a fixed-point value into g (one atomic pair per warp).
-__device__ __forceinline__ void fix_block_atomic(unsigned long long* g, Fix f) {
-    f = fix_warp_sum(f);
-    if ((threadIdx.x & 31) == 0) fix_atomic(g, f);
-}
-
-// The FP64 value of a fixed-point sum.
-__device__ __forceinline__ double fix_value(const Fix& f, int e_ref) {
-    const double t = fma((double)f.hi, 18446744073709551616.0, (double)f.lo);
-    return scalbn(t, e_ref - 1075 - kFixBits);
-}
 
 // Block-wide maximum of a 64-bit value (valid in thread 0).
 __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {

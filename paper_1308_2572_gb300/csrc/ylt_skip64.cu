@@ -21,11 +21,15 @@
 // fold-only hit gathers a zero row), a warp per trial streaming its ids with
 // the next chunk requested before the current one is processed, and a
 // per-warp queue of the events whose bit is set, evaluated 32 at a time (lane
-// = event): one row of X (8 * LP bytes) and an FP64 add per layer. The lanes'
-// FP64 sums are reduced across the warp (xor shuffles, so every lane holds
-// every layer's total) and lane j applies layer j's aggregate terms in FP64.
-// The FP64 pipe of this part (about 0.53 TFLOP/s for adds) bounds it: this is
-// the reference-precision path, not the throughput path.
+// = event): one row of X (8 * LP bytes) added to the lane's per-layer sums.
+// The sums are exact: each FP64 occurrence loss is added as an integer to a
+// 128-bit fixed-point number whose unit is 2^-96 of the group table's largest
+// entry (the build records it), so the aggregate S is the exact sum of the
+// trial's FP64 occurrence losses up to one unit per event, rounded to FP64
+// once; the lanes' sums are reduced across the warp (xor shuffles: every lane
+// holds every layer's total) and lane j applies layer j's aggregate terms in
+// FP64. Integer adds replace the FP64 adds of a sequential sum, of which this
+// part has about 0.53 TFLOP/s.
 #include <algorithm>
 #include <limits>
 
@@ -44,6 +48,12 @@ __device__ __forceinline__ uint32_t ld_bits_global(const uint32_t* p) {
     uint32_t v;
     asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
+}
+
+// The table's largest entry: a warp maximum of the keys, one atomic per warp.
+__device__ __forceinline__ void note_max(unsigned long long* maxkey, unsigned long long mk) {
+    for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    if ((threadIdx.x & 31) == 0 && mk) atomicMax(maxkey, mk);
 }
 
 // Row id of X: LP doubles (LP = 1, 2, 4 or 8), 16-byte loads not kept in L1.
@@ -76,6 +86,7 @@ __global__ void __launch_bounds__(256) build_occ64_kernel(const LayerBuildArgs* 
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool nz = false;
+    unsigned long long mk = 0;  // the largest entry this thread writes (its key: entries are >= 0)
     if (i < catalogue) {
         double o[LP];
 #pragma unroll
@@ -116,7 +127,10 @@ __global__ void __launch_bounds__(256) build_occ64_kernel(const LayerBuildArgs* 
 #pragma unroll
             for (int q = 0; q < LP / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(o[2 * q], o[2 * q + 1]);
         }
+#pragma unroll
+        for (int s = 0; s < LP; ++s) mk = max(mk, (unsigned long long)__double_as_longlong(o[s]));
     }
+    note_max(grp.maxkey, mk);
     const unsigned m = __ballot_sync(0xffffffffu, nz);
     if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
 }
@@ -139,6 +153,7 @@ __global__ void __launch_bounds__(256) build_occ64_csr_kernel(const uint32_t* __
     const uint8_t* sm = slotmask + (size_t)blockIdx.y * np;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool nz = false;
+    unsigned long long mk = 0;  // the largest entry this thread writes (its key: entries are >= 0)
     if (i < catalogue) {
         double x[LP];
 #pragma unroll
@@ -169,7 +184,10 @@ __global__ void __launch_bounds__(256) build_occ64_csr_kernel(const uint32_t* __
 #pragma unroll
             for (int q = 0; q < LP / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(o[2 * q], o[2 * q + 1]);
         }
+#pragma unroll
+        for (int s = 0; s < LP; ++s) mk = max(mk, (unsigned long long)__double_as_longlong(o[s]));
     }
+    note_max(grp.maxkey, mk);
     const unsigned m = __ballot_sync(0xffffffffu, nz);
     if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
 }
@@ -218,29 +236,21 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
             my_lim = g.agg_lim[j];
         }
 
+    // the fixed-point unit: 2^-96 of the group table's largest entry
+    const int e_ref = ref_exp(__ldcg(g.maxkey));
     for (int64_t t = (int64_t)blockIdx.x * k64Warps + wib; t < y.n_trials; t += n_warps) {
         int64_t b, e;
         bool bo;
         trial_range(y, t, b, e, bo);
         bad_off_seen |= bo;
-        // two partial sums per layer, alternating by batch, halve the chains
-        // of dependent FP64 adds (the FP64 unit's latency is long)
-        double sum[LT], sum2[LT];
-        bool odd = false;
+        Fix acc[LT];  // the lane's exact per-layer sums
 #pragma unroll
-        for (int j = 0; j < LT; ++j) {
-            sum[j] = 0.0;
-            sum2[j] = 0.0;
-        }
+        for (int j = 0; j < LT; ++j) acc[j] = Fix{0, 0};
         auto add_row = [&](uint32_t id) {
             double o[LT];
             ld_row64<LT>(g.occ64, id, o);
 #pragma unroll
-            for (int j = 0; j < LT; ++j) {
-                if (odd) sum2[j] += o[j];
-                else sum[j] += o[j];
-            }
-            odd = !odd;
+            for (int j = 0; j < LT; ++j) fix_add(acc[j], (unsigned long long)__double_as_longlong(o[j]), e_ref);
         };
         // ids of a chunk of 32 * E events from c0; empty slots read as -1
         auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
@@ -307,9 +317,7 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
                 bool all = true;
 #pragma unroll
                 for (int j = 0; j < LT; ++j) {
-                    double v = sum[j] + sum2[j];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                    const double v = fix_value(fix_warp_sum(acc[j]), e_ref);
                     if (j < g.n_layers) all = all && (v - g.agg_ret[j] >= g.agg_lim[j]);
                 }
                 if (all) {
@@ -325,10 +333,8 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
         double mine = 0.0;
 #pragma unroll
         for (int j = 0; j < LT; ++j) {
-            double v = sum[j] + sum2[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-            if (lane == j) mine = v;
+            const Fix tot = fix_warp_sum(acc[j]);
+            if (lane == j) mine = fix_value(tot, e_ref);
         }
         if (lane < g.n_layers) {
             const size_t wi = (size_t)my_layer * (size_t)y.n_trials + (size_t)t;
@@ -373,6 +379,8 @@ cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8
     const bool csr = p->sp_ptr && p->d_slotmask64 && p->d_elt_terms64 && p->d_occ;
     const SparseEntry* en = reinterpret_cast<const SparseEntry*>(p->sp_entries);
     if (build) {
+        cudaError_t me = cudaMemsetAsync(p->d_occ64_max, 0, sizeof(unsigned long long) * p->ogroups64.size(), s);
+        if (me != cudaSuccess) return me;
         if (csr) {
             switch (p->og_lp64) {
                 case 1: build_occ64_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms64, p->pool_np, p->d_slotmask64, p->d_occ, p->d_ogroups64, p->d_occ64_ptrs, p->catalogue, words); break;
