@@ -164,10 +164,14 @@ __device__ __forceinline__ void fix_block_atomic(unsigned long long* g, Fix f) {
     if ((threadIdx.x & 31) == 0) fix_atomic(g, f);
 }
 
-// The FP64 value of a fixed-point sum.
+// The FP64 value of a fixed-point sum. The scaling by the unit 2^n is one
+// multiplication by 2^n (exact: t is an integer below 2^128, so the product
+// is normal or overflows as scalbn's does) when 2^n is a normal double, else
+// scalbn.
 __device__ __forceinline__ double fix_value(const Fix& f, int e_ref) {
     const double t = fma((double)f.hi, 18446744073709551616.0, (double)f.lo);
-    return scalbn(t, e_ref - 1075 - kFixBits);
+    const int n = e_ref - 1075 - kFixBits;
+    return n >= -1022 ? t * __longlong_as_double((long long)(n + 1023) << 52) : scalbn(t, n);
 }
 
 // Batched layout description shared by the host and the batched kernels.

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kSkipThreads, 1) ylt_skip_kernel(const OccGrou
                 uint32_t wi = uid[k] >> 5;
                 uint32_t w;
                 if constexpr (FOLD) {
-                    wi = wi >= (uint32_t)smem_words ? wi - (uint32_t)smem_words : wi;
+                    wi = min(wi, wi - (uint32_t)smem_words);  // wi - S wraps when wi < S
                     w = s_bits[wi];
                 } else {
                     w = wi < (uint32_t)smem_words ? s_bits[wi] : ld_bitmap(g.occ_bits + wi);

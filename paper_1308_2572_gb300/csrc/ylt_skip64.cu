@@ -56,16 +56,23 @@ __device__ __forceinline__ void note_max(unsigned long long* maxkey, unsigned lo
     if ((threadIdx.x & 31) == 0 && mk) atomicMax(maxkey, mk);
 }
 
-// Row id of X: LP doubles (LP = 1, 2, 4 or 8), 16-byte loads not kept in L1.
+// Row id of X: its LP FP64 entries as bit patterns, in one load of 8 * LP
+// bytes (a 32-byte row in one 256-bit load), not kept in L1. The table of
+// each group is its own allocation, so row id starts on an 8 * LP-byte
+// boundary. (Two 16-byte loads of FP64-typed registers per row made the
+// pass 3.6 times slower: c4, 627 against 173 ms.)
 template <int LP>
-__device__ __forceinline__ void ld_row64(const double* x, uint32_t id, double (&o)[LP]) {
+__device__ __forceinline__ void ld_row64(const double* x, uint32_t id, unsigned long long (&o)[LP]) {
+    static_assert(LP == 1 || LP == 2 || LP == 4, "FP64 groups hold 1, 2 or 4 layers");
     const double* p = x + (size_t)id * LP;
     if constexpr (LP == 1) {
-        asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(o[0]) : "l"(p));
+        asm("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(o[0]) : "l"(p));
+    } else if constexpr (LP == 2) {
+        asm("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(o[0]), "=l"(o[1]) : "l"(p));
     } else {
-#pragma unroll
-        for (int q = 0; q < LP / 2; ++q)
-            asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(o[2 * q]), "=d"(o[2 * q + 1]) : "l"(p + 2 * q));
+        asm("ld.global.nc.L1::no_allocate.v4.u64 {%0, %1, %2, %3}, [%4];"
+            : "=l"(o[0]), "=l"(o[1]), "=l"(o[2]), "=l"(o[3])
+            : "l"(p));
     }
 }
 
@@ -247,10 +254,10 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
 #pragma unroll
         for (int j = 0; j < LT; ++j) acc[j] = Fix{0, 0};
         auto add_row = [&](uint32_t id) {
-            double o[LT];
+            unsigned long long o[LT];  // the row's keys (bit patterns of FP64 values >= 0)
             ld_row64<LT>(g.occ64, id, o);
 #pragma unroll
-            for (int j = 0; j < LT; ++j) fix_add(acc[j], (unsigned long long)__double_as_longlong(o[j]), e_ref);
+            for (int j = 0; j < LT; ++j) fix_add(acc[j], o[j], e_ref);
         };
         // ids of a chunk of 32 * E events from c0; empty slots read as -1
         auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
                 uint32_t wi = uid[k] >> 5;
                 uint32_t w;
                 if constexpr (FOLD) {
-                    wi = wi >= (uint32_t)smem_words ? wi - (uint32_t)smem_words : wi;
+                    wi = min(wi, wi - (uint32_t)smem_words);  // wi - S wraps when wi < S
                     w = s_bits[wi];
                 } else {
                     w = wi < (uint32_t)smem_words ? s_bits[wi] : ld_bits_global(g.occ_bits + wi);
@@ -330,12 +337,15 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
         __syncwarp();
         if (lane < qn) add_row((uint32_t)q[lane]);
         __syncwarp();
-        double mine = 0.0;
+        // lane j keeps layer j's total and converts it: one FP64 conversion
+        // per lane rather than one per layer under a one-lane predicate
+        Fix mine_f{0, 0};
 #pragma unroll
         for (int j = 0; j < LT; ++j) {
             const Fix tot = fix_warp_sum(acc[j]);
-            if (lane == j) mine = fix_value(tot, e_ref);
+            if (lane == j) mine_f = tot;
         }
+        const double mine = fix_value(mine_f, e_ref);
         if (lane < g.n_layers) {
             const size_t wi = (size_t)my_layer * (size_t)y.n_trials + (size_t)t;
             ylt[wi] = capped_exit ? my_lim : xl_f64(mine, my_ret, my_lim);
