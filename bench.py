@@ -265,9 +265,9 @@ def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6):
         table = float((C + 1) * xb * lp)
         # FP64 operations of the all-FP64 variant: its CSR build costs an FMA
         # per non-zero loss and an add per (loss, layer holding it); the trial
-        # pass an add per slot of every queued event
+        # pass adds the FP64 occurrence losses as integers (no FP64 operation)
         nnz = float((port.elt_losses != 0).sum())
-        flops = 2.0 * nnz + nnz * elts_total / port.n_elt + sum(n_events * d * lp for d in dens)
+        flops = 2.0 * nnz + nnz * elts_total / port.n_elt
         out = {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
                "l2": n_groups * ids + build + reads, "table_bytes": table, "l2_resident": table <= l2_bytes,
                "lookups_performed": C * elts_total + gathered}
@@ -306,39 +306,42 @@ def roofline(ab: dict, secs: float, hbm_gbs: float, l2_gbs=None, fp64_gflops=Non
     """The bound a forward launch set runs against, from its accounting (see
     algorithmic_bytes) and its measured time.
 
-    A gathered table that fits L2 (the skip variant's occurrence tables):
-    t* = max(compulsory DRAM bytes / HBM peak, L2 sector bytes / probed L2
-    gather rate); the larger term names the bound ("hbm" or "l2") and gives
+    A gathered table that fits L2 (the skip and all-FP64 variants'
+    occurrence tables): t* = max(compulsory DRAM bytes / HBM peak, L2 sector
+    bytes / probed L2 gather rate); a table larger than L2: every sector read
+    counts as DRAM traffic, t* = per-unit bytes / HBM peak. Where the launch
+    set does FP64 arithmetic (the all-FP64 variant's build) and the probed
+    FP64 add rate is given, its FP64 operations / that rate is a third term.
+    The largest term names the bound ("hbm", "l2" or "alu") and gives
     achieved and peak, so frac = achieved / peak = t* / t. Without the L2
-    probe that case falls back to the DRAM term. A table larger than L2:
-    every sector read counts as DRAM traffic ("hbm", the per-unit bytes). The
-    all-FP64 variant, given the probed FP64 add rate: "alu". Beside the bound
-    the line keeps the HBM fraction by the compulsory DRAM bytes alone.
+    probe the L2 term is left out. Beside the bound the line keeps the HBM
+    fraction by the compulsory DRAM bytes alone.
     """
     gb = lambda b: b / secs / 1e9
     out = {"hbm_frac_by_dram_bytes": gb(ab["compulsory"]) / hbm_gbs,
            "algorithmic_bytes_per_launch": ab["s8d"], "compulsory_bytes_per_launch": ab["compulsory"],
            "l2_sector_bytes_per_launch": ab["l2"], "l2_sector_gbs": gb(ab["l2"]),
            "gathered_table_bytes": ab["table_bytes"], "gathered_table_fits_l2": bool(ab["l2_resident"])}
-    if "fp64_flops" in ab and fp64_gflops:
-        a = ab["fp64_flops"] / secs / 1e9
-        out.update(bound="alu", achieved=a, peak=fp64_gflops, unit="GFLOP/s", frac=a / fp64_gflops,
-                   peak_source="probed FP64 add rate (art_probe)", hbm_achieved_gbs=gb(ab["s8d"]))
-        return out
+    terms = {}
     if ab["l2_resident"]:
-        t_dram = ab["compulsory"] / (hbm_gbs * 1e9)
-        t_l2 = ab["l2"] / (l2_gbs * 1e9) if l2_gbs else 0.0
-        out["t_star_ms"] = max(t_dram, t_l2) * 1e3
-        if t_l2 > t_dram:
-            out.update(bound="l2", achieved=gb(ab["l2"]), peak=l2_gbs, unit="GB/s",
-                       peak_source="probed random 32-byte L2 gather rate (art_probe)")
-        else:
-            out.update(bound="hbm", achieved=gb(ab["compulsory"]), peak=hbm_gbs, unit="GB/s",
-                       peak_source="hbm_gbs (copy bandwidth)")
+        terms["hbm"] = (ab["compulsory"] / (hbm_gbs * 1e9),
+                        dict(achieved=gb(ab["compulsory"]), peak=hbm_gbs, unit="GB/s",
+                             peak_source="hbm_gbs (copy bandwidth)"))
+        if l2_gbs:
+            terms["l2"] = (ab["l2"] / (l2_gbs * 1e9),
+                           dict(achieved=gb(ab["l2"]), peak=l2_gbs, unit="GB/s",
+                                peak_source="probed random 32-byte L2 gather rate (art_probe)"))
     else:
-        out.update(bound="hbm", achieved=gb(ab["s8d"]), peak=hbm_gbs, unit="GB/s",
-                   peak_source="hbm_gbs (copy bandwidth)")
-        out["t_star_ms"] = ab["s8d"] / (hbm_gbs * 1e9) * 1e3
+        terms["hbm"] = (ab["s8d"] / (hbm_gbs * 1e9),
+                        dict(achieved=gb(ab["s8d"]), peak=hbm_gbs, unit="GB/s", peak_source="hbm_gbs (copy bandwidth)"))
+    if ab.get("fp64_flops") and fp64_gflops:
+        out["fp64_flops_per_launch"] = ab["fp64_flops"]
+        terms["alu"] = (ab["fp64_flops"] / (fp64_gflops * 1e9),
+                        dict(achieved=ab["fp64_flops"] / secs / 1e9, peak=fp64_gflops, unit="GFLOP/s",
+                             peak_source="probed FP64 add rate (art_probe)"))
+    bound = max(terms, key=lambda k: terms[k][0])
+    out["t_star_ms"] = terms[bound][0] * 1e3
+    out.update(bound=bound, **terms[bound][1])
     out["frac"] = out["achieved"] / out["peak"]
     return out
 

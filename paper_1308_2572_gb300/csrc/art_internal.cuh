@@ -107,19 +107,43 @@ struct Fix {
     unsigned long long lo, hi;
 };
 
-// The key's value in those units as two words. e_ref is at least the key's
-// exponent.
-__device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, unsigned long long& a0,
-                                          unsigned long long& a1) {
+// The key's value in those units as a mantissa m (< 2^53, already shifted
+// down where the key lies below the unit's range) and a left shift sh
+// (0 .. kFixBits). e_ref is at least the key's exponent.
+__device__ __forceinline__ void fix_split(unsigned long long key, int e_ref, unsigned long long& m, int& sh) {
     const int e = (int)(key >> 52);
-    unsigned long long m = (key & kMant) | (e ? (1ULL << 52) : 0ULL);
-    int sh = max(e, 1) - e_ref + kFixBits;  // <= kFixBits
+    m = (key & kMant) | (e ? (1ULL << 52) : 0ULL);
+    sh = max(e, 1) - e_ref + kFixBits;  // <= kFixBits
     if (sh < 0) {
         m = -sh < 64 ? m >> -sh : 0ULL;
         sh = 0;
     }
+}
+
+// m * 2^sh as two words (sh <= kFixBits, m < 2^53).
+__device__ __forceinline__ void fix_shift(unsigned long long m, int sh, unsigned long long& a0, unsigned long long& a1) {
     a0 = m << sh;
     a1 = sh > 11 ? m >> (64 - sh) : 0ULL;
+}
+
+// The key's value in those units as two words.
+__device__ __forceinline__ void fix_words(unsigned long long key, int e_ref, unsigned long long& a0,
+                                          unsigned long long& a1) {
+    unsigned long long m;
+    int sh;
+    fix_split(key, e_ref, m, sh);
+    fix_shift(m, sh, a0, a1);
+}
+
+// (m, sh) of fix_split in one word: m in bits 0-52, sh in bits 58-63; a
+// value of 0 (m = 0) packs to 0, so packing a zero entry again keeps it 0.
+// A table packed once per reference exponent spares each later add the
+// split.
+__device__ __forceinline__ unsigned long long fix_pack(unsigned long long key, int e_ref) {
+    unsigned long long m;
+    int sh;
+    fix_split(key, e_ref, m, sh);
+    return m ? m | ((unsigned long long)sh << 58) : 0ULL;
 }
 
 __device__ __forceinline__ void fix_add2(Fix& f, unsigned long long a0, unsigned long long a1) {
@@ -130,6 +154,14 @@ __device__ __forceinline__ void fix_add2(Fix& f, unsigned long long a0, unsigned
 __device__ __forceinline__ void fix_add(Fix& f, unsigned long long key, int e_ref) {
     unsigned long long a0, a1;
     fix_words(key, e_ref, a0, a1);
+    fix_add2(f, a0, a1);
+}
+
+// f += the value of a packed word (fix_pack): the same two words as fix_add
+// of the key it was packed from.
+__device__ __forceinline__ void fix_add_packed(Fix& f, unsigned long long w) {
+    unsigned long long a0, a1;
+    fix_shift(w & ((1ULL << 58) - 1), (int)(w >> 58), a0, a1);
     fix_add2(f, a0, a1);
 }
 
@@ -242,7 +274,7 @@ constexpr int kMaxOccLayers = 8;
 constexpr int kMaxOcc64Layers = 4;  // layers per FP64 occurrence group
 struct OccGroupArgs {
     const float* occ;          // [C + 1][lt_pad] FP32
-    const double* occ64;       // [C + 1][lt_pad] FP64 (the all-FP64 tables)
+    const double* occ64;       // [C + 1][lt_pad] the all-FP64 tables (FP64, then packed fixed point)
     const unsigned long long* maxkey;  // the FP64 table's largest entry (its key), written by the build
     const uint32_t* occ_bits;  // bits 0 .. C, zero-padded to whole 16-byte groups
     int32_t layer[kMaxOccLayers];

@@ -26,9 +26,11 @@
 // 128-bit fixed-point number whose unit is 2^-96 of the group table's largest
 // entry (the build records it), so the aggregate S is the exact sum of the
 // trial's FP64 occurrence losses up to one unit per event, rounded to FP64
-// once; the lanes' sums are reduced across the warp (xor shuffles: every lane
-// holds every layer's total) and lane j applies layer j's aggregate terms in
-// FP64. Integer adds replace the FP64 adds of a sequential sum, of which this
+// once. After the build each table entry is packed in place into the
+// mantissa and shift of its fixed-point value, so a pass adds an entry with
+// two shifts and a 128-bit add. The lanes' sums are reduced across the warp
+// (xor shuffles: every lane holds every layer's total) and lane j applies
+// layer j's aggregate terms in FP64. Integer adds replace the FP64 adds of a sequential sum, of which this
 // part has about 0.53 TFLOP/s.
 #include <algorithm>
 #include <limits>
@@ -199,6 +201,19 @@ __global__ void __launch_bounds__(256) build_occ64_csr_kernel(const uint32_t* __
     if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
 }
 
+// Packs every entry of group blockIdx.y's table in place (fix_pack against
+// the group's reference exponent, known once the build has recorded the
+// table's largest entry), so that the trial passes add each entry without
+// splitting it into mantissa and shift again.
+__global__ void __launch_bounds__(256) pack_occ64_kernel(double* const* __restrict__ occ64,
+                                                         const OccBuildGroup* __restrict__ groups, int64_t n_entries) {
+    const int e_ref = ref_exp(__ldcg(groups[blockIdx.y].maxkey));
+    unsigned long long* t = reinterpret_cast<unsigned long long*>(occ64[blockIdx.y]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_entries;
+         i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = fix_pack(t[i], e_ref);
+}
+
 template <int LT, bool VEC, bool FOLD>
 __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGroupArgs g, const YetArgs y,
                                                                   const int32_t smem_words, const bool early_exit,
@@ -254,10 +269,10 @@ __global__ void __launch_bounds__(k64Threads, 1) ylt_skip64_kernel(const OccGrou
 #pragma unroll
         for (int j = 0; j < LT; ++j) acc[j] = Fix{0, 0};
         auto add_row = [&](uint32_t id) {
-            unsigned long long o[LT];  // the row's keys (bit patterns of FP64 values >= 0)
+            unsigned long long o[LT];  // the row's packed entries
             ld_row64<LT>(g.occ64, id, o);
 #pragma unroll
-            for (int j = 0; j < LT; ++j) fix_add(acc[j], o[j], e_ref);
+            for (int j = 0; j < LT; ++j) fix_add_packed(acc[j], o[j]);
         };
         // ids of a chunk of 32 * E events from c0; empty slots read as -1
         auto load_ids = [&](int64_t c0, uint32_t (&v)[E]) {
@@ -408,7 +423,16 @@ cudaError_t launch_skip64(art_portfolio* p, const YetArgs& y, double* ylt, uint8
         }
     }
     cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || y.n_trials == 0) return err;
+    if (err != cudaSuccess) return err;
+    if (build) {
+        // the tables' entries packed against their groups' largest entries
+        const int64_t n_entries = ((int64_t)p->catalogue + 1) * p->og_lp64;
+        const int64_t blocks = std::min<int64_t>((n_entries + 255) / 256, (int64_t)p->num_sms * 8);
+        pack_occ64_kernel<<<dim3((unsigned)blocks, (unsigned)p->ogroups64.size()), 256, 0, s>>>(
+            p->d_occ64_ptrs, p->d_ogroups64, n_entries);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (y.n_trials == 0) return cudaSuccess;
     for (const OccGroupArgs& g : p->ogroups64) {
         switch (p->og_lp64) {
             case 1: err = launch_group64<1>(g, y, p->num_sms, p->catalogue, early, ylt, branch, p->d_flags, s); break;

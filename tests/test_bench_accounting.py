@@ -58,7 +58,11 @@ def test_each_variant_is_accounted_against_its_bound():
         assert {"s8d", "compulsory", "l2", "table_bytes", "l2_resident", "lookups_performed"} <= set(ab), v
         assert ab["s8d"] >= ab["compulsory"] > 0
     ab = bench.algorithmic_bytes(w, "fp64")
-    assert ab["fp64_flops"] > 0  # the all-FP64 variant is bound by the FP64 pipe
+    # the all-FP64 variant's FP64 operations are its build's: an FMA per
+    # non-zero loss and an add per (loss, layer holding it)
+    port = w.portfolio
+    nnz = float((port.elt_losses != 0).sum())
+    assert ab["fp64_flops"] == pytest.approx(2 * nnz + nnz * float(port.elts_per_layer().sum()) / port.n_elt)
 
 
 def test_skip_variant_counts_the_lookups_it_performs():
@@ -100,8 +104,16 @@ def test_roofline_of_a_table_larger_than_l2_and_of_fp64():
     ab = {"s8d": 68e9, "compulsory": 4.2e9, "l2": 68e9, "table_bytes": 128e6, "l2_resident": False}
     r = bench.roofline(ab, 11.2e-3, 6769.4, 6956.0)
     assert r["bound"] == "hbm" and r["frac"] == pytest.approx(68e9 / 11.2e-3 / 6769.4e9)
+    # FP64 work that takes longer than the traffic names the bound ...
     r = bench.roofline(dict(ab, fp64_flops=1e11), 0.69, 6769.4, 6956.0, fp64_gflops=528.0)
     assert r["bound"] == "alu" and r["unit"] == "GFLOP/s" and r["frac"] == pytest.approx(1e11 / 0.69 / 528e9)
+    assert r["t_star_ms"] == pytest.approx(1e11 / 528e9 * 1e3)
+    # ... and FP64 work that takes less does not
+    r = bench.roofline(dict(ab, fp64_flops=1e9), 11.2e-3, 6769.4, 6956.0, fp64_gflops=528.0)
+    assert r["bound"] == "hbm" and r["frac"] == pytest.approx(68e9 / 11.2e-3 / 6769.4e9)
+    res = dict(ab, l2_resident=True, compulsory=4.14e9, l2=7.01e9)
+    r = bench.roofline(dict(res, fp64_flops=1e8), 1.331e-3, 6769.4, 6956.0, fp64_gflops=528.0)
+    assert r["bound"] == "l2" and r["frac"] == pytest.approx(7.01e9 / 6956e9 / 1.331e-3)
 
 
 def test_traffic_comes_from_a_json_record_of_the_current_sources(tmp_path):

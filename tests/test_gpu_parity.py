@@ -372,6 +372,36 @@ def test_update_terms_and_rounding():
         p.close()
 
 
+def test_fp64_tables_rebuilt_and_repacked_keep_results():
+    """Every all-FP64 call builds its occurrence tables and packs their entries
+    in place. A catalogue past what shared memory holds folds the bitmap, and
+    with every event carrying a loss each folded word is all ones, so the
+    empty slots of partial chunks (mapped to the sentinel row C, which no
+    build rewrites) gather row C: it must stay zero however often the tables
+    are built and packed."""
+    w = workloads.random_case(211, catalogue=2_000_003, n_elt=4, n_layers=4, n_trials=2000, min_len=1,
+                              max_len=300, nnz_frac=1.0)
+    w.portfolio.elt_ded[:] = 0.0  # every loss gives a positive payout
+    w.portfolio.occ_ret[:] = 0.0  # every event with a loss has a positive occurrence loss
+    ref, gross, _ = oracle.ylt(w.oracle_problem())
+    p = art.portfolio_from_workload(w, layouts=OCC64_LAYOUTS)
+    try:
+        first, _ = run_ylt(p, w, art.ART_VARIANT_FP64)
+        y = first.cpu().numpy()
+        assert np.all(np.abs(y - ref) <= FP64_TOL * np.maximum(gross, 1.0))
+        for _ in range(2):
+            again, _ = run_ylt(p, w, art.ART_VARIANT_FP64)
+            assert torch.equal(again, first)
+        m, d, l, t = art.art_get_terms(p)
+        art.art_update_terms(p, terms=np.column_stack([t[:, 0], t[:, 1] * 0.5, t[:, 2], t[:, 3]]))
+        run_ylt(p, w, art.ART_VARIANT_FP64)
+        art.art_update_terms(p, terms=t)
+        back, _ = run_ylt(p, w, art.ART_VARIANT_FP64)
+        assert torch.equal(back, first)
+    finally:
+        p.close()
+
+
 @pytest.mark.parametrize("name,n_sample", [("c2", 5000), ("c4", 5000)])
 def test_multilayer_workloads_sampled(name, n_sample):
     """The batching (CSR, 64 layers over a 256-ELT pool) and precision
