@@ -47,9 +47,16 @@ namespace art {
 
 namespace {
 
-constexpr int kAgThreads = 512;
-constexpr int kAgWarps = kAgThreads / 32;
-constexpr int kAgIds = 8;    // ids per lane per chunk
+// Threads per CTA of the trial pass and ids per lane in flight, by the
+// group's column count. Up to 16 columns the pass needs about 80 registers
+// per thread, and 24 warps per SM with 4 ids each hide more of the gathers'
+// latency than 16 warps with 8 ids (c3 adjoint 3.88 against 4.18 ms; 1024
+// threads spill); wider groups keep 512 threads with 8 ids (128 registers,
+// no spills).
+template <int NP>
+constexpr int kAgThreadsFor = NP <= 16 ? 768 : 512;
+template <int NP>
+constexpr int kAgIdsFor = NP <= 16 ? 4 : 8;
 constexpr int kAgQueue = 64;  // per-warp queue entries
 
 __device__ __forceinline__ uint32_t ld_bits_global(const uint32_t* p) {
@@ -163,7 +170,7 @@ __device__ __forceinline__ void eval_event(const GroupArgs& g, const uint2* __re
 }
 
 template <int NP, int LT, bool VEC, bool FOLD>
-__global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const GroupArgs g, const YetArgs y,
+__global__ void __launch_bounds__(kAgThreadsFor<NP>, 1) adjoint_pass_kernel(const GroupArgs g, const YetArgs y,
                                                                      const uint2* __restrict__ masks,
                                                                      const uint32_t* __restrict__ gbits,
                                                                      const int32_t smem_words,
@@ -171,7 +178,8 @@ __global__ void __launch_bounds__(kAgThreads, 1) adjoint_pass_kernel(const Group
                                                                      const double* __restrict__ gw,
                                                                      double* __restrict__ partial) {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int E = kAgIds;
+    constexpr int E = kAgIdsFor<NP>;
+    constexpr int kAgWarps = kAgThreadsFor<NP> / 32;
     constexpr int NW = 1 << LT;      // entries of a warp's weight table
     constexpr int W = 4 * LT + NP;   // OccR[LT], OccL[LT], AggR[LT], AggL[LT], then the columns
     extern __shared__ __align__(16) uint32_t s_dyn[];
@@ -436,6 +444,7 @@ cudaError_t launch_one(const GroupArgs& g, const GroupIndex& gix, const YetArgs&
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
     constexpr int W = 4 * LT + NP;
+    constexpr int kAgWarps = kAgThreadsFor<NP> / 32;
     const int fixed = 4 * (512 + 2 * kAgWarps * W + 32 + kAgWarps * (1 << LT) + kAgWarps * kAgQueue);
     const int words = (C >> 5) + 1;  // bits 0 .. C (C: the sentinel)
     const int smem_words = std::max(4, std::min((words + 3) & ~3, (max_optin - fixed) / 4) & ~3);
@@ -446,7 +455,7 @@ cudaError_t launch_one(const GroupArgs& g, const GroupIndex& gix, const YetArgs&
                     : (fold ? adjoint_pass_kernel<NP, LT, false, true> : adjoint_pass_kernel<NP, LT, false, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms, (y.n_trials + kAgWarps - 1) / kAgWarps));
-    kern<<<nblk, kAgThreads, smem, s>>>(g, y, sc.masks, sc.bits, smem_words, branch, gw, sc.partial);
+    kern<<<nblk, kAgThreadsFor<NP>, smem, s>>>(g, y, sc.masks, sc.bits, smem_words, branch, gw, sc.partial);
     if ((e = cudaGetLastError())) return e;
     group_scatter_kernel<<<1, 128, 0, s>>>(sc.partial, nblk, LT, NP, gix, grad_terms, grad_mult);
     return cudaGetLastError();
