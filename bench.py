@@ -589,6 +589,10 @@ def extra_workload(name: str, dev, probes: dict, hbm: float, l2_size: float) -> 
             art.art_set_variant(p, art.ART_VARIANT_FP64)
             y64 = torch.empty_like(ylt)
             rec["fp64_forward_ms"] = time_forward(art, torch, p, T, ids, off, K, y64, stream, reps=2)
+            r64 = roofline(algorithmic_bytes(w, "fp64", l2_size), rec["fp64_forward_ms"] * 1e-3, hbm,
+                           probes.get("l2_gather32_gbs"), probes.get("fp64_add_gflops"))
+            rec["fp64_roofline"] = {k: r64.get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "t_star_ms",
+                                                           "hbm_frac_by_dram_bytes", "peak_source")}
             art.art_set_variant(p, vmap[chosen])
             art.art_run_ylt(p, T, ids, off, K, ylt, None, stream)
             # the gross loss G per (layer, trial): the all-FP64 forward with
