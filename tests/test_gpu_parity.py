@@ -429,9 +429,9 @@ def test_multilayer_workloads_sampled(name, n_sample):
 
 @pytest.mark.parametrize("name,n", [("c0", None), ("c0u", None), ("c1", 40000), ("c3", 8000)])
 def test_early_exit_keeps_results(name, n):
-    """The skip variant's optional early exit (stop reading a trial once it is
-    capped) gives the oracle's results; on the literal one-layer terms, where
-    every trial caps, exactly AggL."""
+    """The optional early exit of the skip and all-FP64 variants (stop
+    reading a trial once it is capped) gives the oracle's results; on the
+    literal one-layer terms, where every trial caps, exactly AggL."""
     w = workloads.make(name, n_trials=n)
     p = art.portfolio_from_workload(w)
     try:
@@ -447,5 +447,16 @@ def test_early_exit_keeps_results(name, n):
         assert torch.equal(fast[capped], full[capped])
         if name in ("c0", "c1"):
             assert torch.all(fast == 2e7)
+        # the all-FP64 pass decides the cap on its exact fixed-point sums
+        p64 = art.portfolio_from_workload(w, layouts=OCC64_LAYOUTS | art.ART_LAYOUT_SPARSE)
+        try:
+            art.art_set_flags(p64, art.ART_FLAG_EARLY_EXIT)
+            y64, _ = run_ylt(p64, w, art.ART_VARIANT_FP64, yet=yet)
+            y = y64[:, torch.from_numpy(trials).cuda()].cpu().numpy()
+            assert np.all(np.abs(y - ref) <= FP64_TOL * np.maximum(gross, 1.0)), f"{name} all-FP64 early exit"
+            if name in ("c0", "c1"):
+                assert torch.all(y64 == 2e7)
+        finally:
+            p64.close()
     finally:
         p.close()
