@@ -907,7 +907,9 @@ def main():
 
     extras = {}
     names = [] if args.workloads in ("", "none") else [n for n in args.workloads.split(",") if n != args.config]
-    if rank == 0 and not args.trials and not args.layers:
+    # the other workloads are single-GPU figures: timed at N = 1 only, so that
+    # the ranks of a scaling run are not held while rank 0 times them
+    if rank == 0 and world == 1 and not args.trials and not args.layers:
         for name in names:
             t0 = time.perf_counter()
             try:
