@@ -11,7 +11,8 @@ Metric: trial-events x ELTs per second (sum_t K_t * sum_j |E_j| per step /
 step time), plus ms per 1M-trial YLT and the roofline fraction of the
 forward kernel. After the headline line's timed region, the batching (c2),
 differentiation (c3) and precision (c4) workloads are timed too and reported
-in its `workloads` record (--workloads none skips them).
+in its `workloads` record (--workloads none skips them); they are
+single-GPU figures, timed at N = 1 only.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1]
                   [--variant auto|plain|batched|fp64|skip|sparse]
