@@ -863,7 +863,8 @@ def main():
                "step_h2d_gbs": h2d / e2e_s / 1e9, "h2d_link_rank0": link,
                "path": ("art_run_ylt_host per rank, the shard's YLT to the device, art_topk, all-gather, host "
                         "merge (art_merge_topk)") if sharded else
-                       ("art_run_ylt_host_metrics (pinned host YET in 64 MiB chunks, H2D overlapped with the "
+                       ("art_run_ylt_host_metrics (the pinned host YET read in place over the host link by a "
+                        "forward that reads every id once, else copied in 64 MiB chunks overlapped with the "
                         "forward; YLT kept on the device for art_metrics; YLT and metrics copied back)")}
         del ids_h, ylt_h
 

@@ -120,10 +120,13 @@ enum {
                                  that group's pass; the window is cleared afterwards) */
     ART_FLAG_GRAPH = 2,       /* art_run_ylt captures its launches (any variant) in a CUDA
                                  graph once per argument set and replays it            */
-    ART_FLAG_EARLY_EXIT = 4   /* skip variant: stop reading a trial once every layer of the
+    ART_FLAG_EARLY_EXIT = 4,  /* skip variant: stop reading a trial once every layer of the
                                  group has reached its aggregate cap (the aggregate never
                                  decreases, so the loss is AggL); same results within FP32
                                  rounding of the cap, far fewer lookups on capped trials  */
+    ART_FLAG_HOST_STAGED = 8  /* art_run_ylt_host*: always copy the YET to the device in
+                                 staged chunks, never read it in place (see
+                                 art_run_ylt_host)                                          */
 };
 
 typedef struct {
@@ -233,12 +236,21 @@ ART_API art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t
                        uint8_t* branch_dev, cudaStream_t stream);
 
 /*
- * art_run_ylt_host -- art_run_ylt from host buffers: the YET is copied to the
+ * art_run_ylt_host -- art_run_ylt from host buffers, two ways. (1) In
+ * place: when the YET buffers are page-locked host memory mapped into the
+ * current device (cudaHostAlloc, cudaHostRegister with mapping, a pinned
+ * buffer under unified addressing: cudaHostGetDevicePointer succeeds) and
+ * the variant reads every event id once per call (the skip and all-FP64
+ * variants with one occurrence group, the plain variant with one layer),
+ * the forward reads the ids from host memory over the host link, into a
+ * device YLT the portfolio keeps, which is then copied into ylt_host. (2)
+ * Staged, otherwise or with ART_FLAG_HOST_STAGED: the YET is copied to the
  * device in chunks of trials on the given stream, each chunk's YLT rows are
- * computed and copied back into ylt_host ([n_layers][T] FP64). The portfolio
- * owns the staging buffers (grown on demand, freed with the portfolio).
- * Blocks until the result is in ylt_host. Dense YETs only (trial_off NULL)
- * or CSR with host offsets. Pinned host memory gives full copy bandwidth.
+ * computed and copied back into ylt_host ([n_layers][T] FP64). The
+ * portfolio owns the device YLT and the staging buffers (grown on demand,
+ * freed with the portfolio). Both give the same results. Blocks until the
+ * result is in ylt_host. Dense YETs only (trial_off NULL) or CSR with host
+ * offsets. Pinned host memory gives full link bandwidth.
  * The chunks stand for the paper's chunked reads of the YET (Section III);
  * the result is that of art_run_ylt (Algorithm 1, Section II). Host offsets
  * are checked on the host (off[0] = 0, non-decreasing) before any copy.
@@ -253,9 +265,9 @@ ART_API art_status art_run_ylt_host(art_portfolio* p, int64_t n_trials, const in
  * art_run_ylt_host_metrics -- the simulation stage and the financial
  * functions from host buffers in one call (Section II, Algorithm 1 on a YET
  * read in chunks as in Section III; Section I, PML and TVaR of the YLT): the
- * YET goes to the device in chunks as in art_run_ylt_host, the whole YLT is
- * kept on the device, art_metrics runs on it there, and only the results
- * come back. The YLT never makes a device-host-device round trip.
+ * YET is read in place or staged in chunks as in art_run_ylt_host, the whole
+ * YLT is kept on the device, art_metrics runs on it there, and only the
+ * results come back. The YLT never makes a device-host-device round trip.
  *  ylt_host      NULL, or [n_layers][T] FP64 host output (the YLT as well).
  *  probs_host    [n_p] probabilities in (0, 1), 1 <= n_p <= 8.
  *  mean_host     [n_layers], pml_host and tvar_host [n_layers][n_p]: FP64

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libart.so")
 ART_OK, ART_EINVAL, ART_ENOMEM, ART_ECUDA, ART_EID_RANGE, ART_ETIMEOUT, ART_EUNSUPPORTED = range(7)
 ART_VARIANT_AUTO, ART_VARIANT_PLAIN, ART_VARIANT_BATCHED, ART_VARIANT_FP64, ART_VARIANT_SKIP, ART_VARIANT_SPARSE = range(6)
 ART_LAYOUT_LAYER, ART_LAYOUT_POOL, ART_LAYOUT_POOL64, ART_LAYOUT_GROUP, ART_LAYOUT_SPARSE, ART_LAYOUT_OCC64 = 1, 2, 4, 8, 16, 32
-ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH, ART_FLAG_EARLY_EXIT = 1, 2, 4
+ART_FLAG_L2_PERSIST, ART_FLAG_GRAPH, ART_FLAG_EARLY_EXIT, ART_FLAG_HOST_STAGED = 1, 2, 4, 8
 
 # Every entry point declared in include/art.h.
 EXPORTS = ("art_create_portfolio", "art_update_terms", "art_get_terms", "art_set_variant", "art_run_ylt",

@@ -760,7 +760,8 @@ art_status art_get_terms(const art_portfolio* p, float* elt_mult_host, float* el
 }
 
 art_status art_set_flags(art_portfolio* p, int32_t flags) {
-    if (!p || (flags & ~(ART_FLAG_L2_PERSIST | ART_FLAG_GRAPH | ART_FLAG_EARLY_EXIT))) return ART_EINVAL;
+    if (!p || (flags & ~(ART_FLAG_L2_PERSIST | ART_FLAG_GRAPH | ART_FLAG_EARLY_EXIT | ART_FLAG_HOST_STAGED)))
+        return ART_EINVAL;
     p->flags = flags;
     if (p->graph_exec) {
         cudaGraphExecDestroy(p->graph_exec);
@@ -843,11 +844,53 @@ art_status art_run_ylt(art_portfolio* p, int64_t n_trials, const int32_t* event_
 
 namespace {
 
-// The host-buffer forward: the YET goes to the device in chunks of trials on
-// `stream` (copies on the portfolio's copy stream, double-buffered), each
-// chunk's YLT rows go to ylt_host (if not NULL) and into columns t0.. of the
-// device array ylt_dev ([n_layers][n_trials], if not NULL). Blocks until the
-// last copy is done. Arguments validated by the caller.
+// A device buffer of at least `need` doubles, kept by the portfolio between
+// calls (reallocated, after the stream's work, only when it grows).
+cudaError_t ensure_dev(double** buf, int64_t* cap, int64_t need, cudaStream_t stream) {
+    if (need <= *cap) return cudaSuccess;
+    cudaStreamSynchronize(stream);
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    const cudaError_t e = cudaMalloc(buf, sizeof(double) * (size_t)need);
+    if (e == cudaSuccess) *cap = need;
+    return e;
+}
+
+// The current device's address of a host buffer that is page-locked and
+// mapped into it (cudaHostAlloc, cudaHostRegister with mapping, a pinned
+// tensor under unified addressing); NULL for any other buffer (the failed
+// query's error is cleared).
+template <typename T>
+const T* device_alias(const T* host) {
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, const_cast<T*>(host), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<const T*>(d);
+}
+
+// True when the variant's forward reads every event id once per call: the
+// skip and all-FP64 variants with one occurrence group, the plain variant
+// with one layer.
+bool one_pass_over_ids(const art_portfolio* p, int variant) {
+    if (variant == ART_VARIANT_SKIP) return p->ogroups.size() == 1;
+    if (variant == ART_VARIANT_FP64) return p->ogroups64.size() == 1;
+    if (variant == ART_VARIANT_PLAIN) return p->n_layers == 1;
+    return false;
+}
+
+// The host-buffer forward. When the YET buffers are mapped page-locked host
+// memory and the variant reads every id once, the forward reads them in
+// place over the host link (no staging copies; ART_FLAG_HOST_STAGED turns
+// this off) into ylt_dev, or a device YLT the portfolio keeps, and the YLT
+// is copied to ylt_host. Otherwise the YET goes to the device in chunks of
+// trials on `stream` (copies on the portfolio's copy stream,
+// double-buffered), each chunk's YLT rows go to ylt_host (if not NULL) and
+// into columns t0.. of the device array ylt_dev ([n_layers][n_trials], if
+// not NULL). Blocks until the last copy is done. Arguments validated by the
+// caller.
 art_status host_run(art_portfolio* p, int64_t n_trials, const int32_t* event_ids_host, const int64_t* trial_off_host,
                     int32_t events_per_trial, double* ylt_host, double* ylt_dev, cudaStream_t stream) {
     if (trial_off_host) {
@@ -857,6 +900,27 @@ art_status host_run(art_portfolio* p, int64_t n_trials, const int32_t* event_ids
     }
     const int variant = resolve_variant(p);
     if (!variant_available(p, variant)) return ART_EUNSUPPORTED;
+    if (!(p->flags & ART_FLAG_HOST_STAGED) && one_pass_over_ids(p, variant)) {
+        const int32_t* d_ids = device_alias(event_ids_host);
+        const int64_t* d_off = trial_off_host ? device_alias(trial_off_host) : nullptr;
+        if (d_ids && (!trial_off_host || d_off)) {
+            cudaError_t e = cudaSuccess;
+            double* yd = ylt_dev;
+            if (!yd) {
+                if ((e = ensure_dev(&p->host_ylt, &p->host_ylt_cap, (int64_t)p->n_layers * n_trials, stream)))
+                    return fail(e);
+                yd = p->host_ylt;
+            }
+            const YetArgs y{d_ids, d_off, n_trials, trial_off_host ? 0 : events_per_trial, p->catalogue};
+            e = run_forward(p, variant, y, yd, nullptr, stream, true);
+            if (!e && ylt_host)
+                e = cudaMemcpyAsync(ylt_host, yd, sizeof(double) * (size_t)p->n_layers * (size_t)n_trials,
+                                    cudaMemcpyDeviceToHost, stream);
+            const cudaError_t e2 = cudaStreamSynchronize(stream);
+            if (e || e2) return fail(e ? e : e2);
+            return ART_OK;
+        }
+    }
     // chunk of trials per stage: about 64 MiB of ids
     const int64_t avg = trial_off_host ? std::max<int64_t>(1, trial_off_host[n_trials] / std::max<int64_t>(1, n_trials))
                                        : std::max<int64_t>(1, events_per_trial);
@@ -978,17 +1042,8 @@ art_status art_run_ylt_host_metrics(art_portfolio* p, int64_t n_trials, const in
     const int64_t L = p->n_layers;
     const int64_t need_ylt = L * n_trials, need_out = L * (1 + 2 * (int64_t)n_p);
     cudaError_t e = cudaSuccess;
-    if (need_ylt > p->host_ylt_cap || need_out > p->host_out_cap) {
-        cudaStreamSynchronize(stream);
-        cudaFree(p->host_ylt);
-        cudaFree(p->host_out);
-        p->host_ylt = p->host_out = nullptr;
-        p->host_ylt_cap = p->host_out_cap = 0;
-        if ((e = cudaMalloc(&p->host_ylt, sizeof(double) * need_ylt))) return fail(e);
-        if ((e = cudaMalloc(&p->host_out, sizeof(double) * need_out))) return fail(e);
-        p->host_ylt_cap = need_ylt;
-        p->host_out_cap = need_out;
-    }
+    if ((e = ensure_dev(&p->host_ylt, &p->host_ylt_cap, need_ylt, stream))) return fail(e);
+    if ((e = ensure_dev(&p->host_out, &p->host_out_cap, need_out, stream))) return fail(e);
     // the metrics' scratch too, so that repeated calls allocate nothing
     const size_t need_scratch = metrics_scratch_bytes(n_trials, (int32_t)L, n_p);
     if (need_scratch > p->host_scratch_cap) {

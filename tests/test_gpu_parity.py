@@ -252,6 +252,42 @@ def test_host_buffers_match_device_path():
                 p.close()
 
 
+def test_host_buffers_in_place_and_staged():
+    """The host-buffer calls read a mapped page-locked YET in place when the
+    variant reads every id once (one occurrence group, or one layer for the
+    plain variant), and stage it otherwise: pinned ids and offsets, the
+    same with ART_FLAG_HOST_STAGED, and pageable buffers all give the device
+    path's bits, with and without the metrics."""
+    cases = (workloads.make("c0u"), workloads.random_case(208, n_trials=6000, max_len=90, n_layers=3))
+    probs = [0.99]
+    for w in cases:
+        for v, layouts in ((art.ART_VARIANT_SKIP, art.ART_LAYOUT_LAYER),
+                           (art.ART_VARIANT_FP64, OCC64_LAYOUTS | art.ART_LAYOUT_SPARSE),
+                           (art.ART_VARIANT_PLAIN, art.ART_LAYOUT_LAYER)):
+            p = art.portfolio_from_workload(w, layouts=layouts)
+            try:
+                dev, _ = run_ylt(p, w, v)
+                mean, pml, tvar = gpu_metrics(dev, probs)
+                L, T, K = w.portfolio.n_layers, w.yet.n_trials, w.yet.events_per_trial
+                ids = torch.from_numpy(w.yet.event_ids)
+                off = None if w.yet.trial_off is None else torch.from_numpy(w.yet.trial_off)
+                for pinned, flags in ((True, 0), (True, art.ART_FLAG_HOST_STAGED), (False, 0)):
+                    art.art_set_flags(p, flags)
+                    i_h = ids.pin_memory() if pinned else ids.clone()
+                    o_h = None if off is None else (off.pin_memory() if pinned else off.clone())
+                    out = torch.zeros((L, T), dtype=torch.float64).pin_memory()
+                    art.art_run_ylt_host(p, T, i_h, o_h, K, out)
+                    assert torch.equal(out, dev.cpu()), (w.name, v, pinned, flags)
+                    m, pm, tv = np.zeros(L), np.zeros((L, 1)), np.zeros((L, 1))
+                    out.zero_()
+                    art.art_run_ylt_host_metrics(p, T, i_h, o_h, K, probs, ylt=out, mean=m, pml=pm, tvar=tv)
+                    assert torch.equal(out, dev.cpu()), (w.name, v, pinned, flags)
+                    assert np.array_equal(m, mean) and np.array_equal(pm, pml) and np.array_equal(tv, tvar)
+                assert art.art_get_device_status(p) == art.ART_OK
+            finally:
+                p.close()
+
+
 def test_host_buffers_with_metrics_match_device_path():
     """art_run_ylt_host_metrics (YET from host memory, YLT kept on the device
     for the metrics) gives the bits of art_run_ylt followed by art_metrics,
