@@ -106,10 +106,11 @@ enum {
     ART_LAYOUT_SPARSE = 16,   /* all ELTs: event-major CSR of the non-zero losses
                                  (C + 1 offsets, 8 bytes per non-zero loss)                */
     ART_LAYOUT_OCC64 = 32     /* with ART_LAYOUT_LAYER: FP64 occurrence-loss tables
-                                 ([C + 1][<= 8] FP64 per run of <= 8 layers) and bitmaps,
-                                 written by the all-FP64 variant on every call; that
-                                 variant then uses them instead of the FP64 pool
-                                 (counted with the pool64 bytes)                           */
+                                 ([C + 1][<= 4] 8-byte entries per run of <= 4 layers) and
+                                 bitmaps, written by the all-FP64 variant on every call
+                                 (FP64 values, then packed in place into fixed-point
+                                 words); that variant then uses them instead of the
+                                 FP64 pool (counted with the pool64 bytes)                 */
 };
 
 /* Flags. */
