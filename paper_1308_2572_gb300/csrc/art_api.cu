@@ -365,6 +365,24 @@ cudaError_t build_occ_groups(art_portfolio* p) {
         }
     }
     if (e) return e;
+    // the tables X can be built from the CSR of the non-zero losses when
+    // every layer lists its ELTs in ascending id order: the CSR's entry order
+    // is then each layer's order, and the absent (zero) losses add exactly 0,
+    // so the sums are those of the per-layer tables bit for bit
+    bool ascending = true;
+    for (int32_t j = 0; j < L && ascending; ++j)
+        for (int32_t c = p->loff[j] + 1; c < p->loff[j + 1]; ++c) ascending = ascending && p->lids[c - 1] < p->lids[c];
+    if (ascending && p->pool_np > 0 && p->sp_ptr) {
+        std::vector<uint8_t> sm((size_t)ng * p->pool_np, 0);
+        for (int32_t gi = 0; gi < ng; ++gi)
+            for (int s = 0; s < p->ogroups[gi].n_layers; ++s) {
+                const int32_t j = p->ogroups[gi].layer[s];
+                for (int c = p->loff[j]; c < p->loff[j + 1]; ++c)
+                    sm[(size_t)gi * p->pool_np + p->lids[c]] |= (uint8_t)(1u << s);
+            }
+        if ((e = cudaMalloc(&p->d_slotmask, sm.size()))) return e;
+        if ((e = cudaMemcpy(p->d_slotmask, sm.data(), sm.size(), cudaMemcpyHostToDevice))) return e;
+    }
     if ((e = cudaMalloc(&p->d_lbuild, sizeof(LayerBuildArgs) * L))) return e;
     if ((e = cudaMalloc(&p->d_ogroups, sizeof(OccBuildGroup) * ng))) return e;
     if ((e = cudaMemcpy(p->d_ogroups, bg.data(), sizeof(OccBuildGroup) * ng, cudaMemcpyHostToDevice))) return e;
@@ -490,6 +508,7 @@ void free_portfolio(art_portfolio* p) {
     cudaFree(p->d_ogroups64);
     cudaFree(p->d_occ64_ptrs);
     cudaFree(p->d_occ64_max);
+    cudaFree(p->d_slotmask);
     cudaFree(p->d_slotmask64);
     cudaFree(p->pool);
     cudaFree(p->pool64);

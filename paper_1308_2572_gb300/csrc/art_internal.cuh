@@ -354,6 +354,8 @@ struct art_portfolio {
     double** d_occ64_ptrs = nullptr;            // [n_ogroups64]
     unsigned long long* d_occ64_max = nullptr;  // [n_ogroups64]: each FP64 table's largest entry
     int32_t og_lp64 = 0;                        // slots per row of the FP64 tables (1, 2 or 4)
+    uint8_t* d_slotmask = nullptr;              // [n_ogroups][pool_np]: slots of the skip group holding the ELT
+                                                // (only when every layer lists its ELTs in ascending id order)
     uint8_t* d_slotmask64 = nullptr;            // [n_ogroups64][pool_np]: slots of the group holding the ELT
     int64_t occ64_bytes = 0;
     int64_t group_bytes = 0;

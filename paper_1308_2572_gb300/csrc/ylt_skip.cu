@@ -490,6 +490,61 @@ __global__ void __launch_bounds__(256) build_occ_kernel(const LayerBuildArgs* __
     if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
 }
 
+// The same tables from the event-major CSR of the non-zero losses (every
+// layer's ELTs in ascending id order): thread i walks event i's entries (in
+// ELT id order, which is each layer's order) and adds F_e in FP32 to the
+// slots of the group's layers that hold ELT e. The absent losses, zeros,
+// would add exactly 0, so the sums are the per-layer tables' bit for bit,
+// while the reads are the event's non-zero entries instead of its full rows.
+template <int LP>
+__global__ void __launch_bounds__(256) build_occ_csr_kernel(const uint32_t* __restrict__ ptr,
+                                                            const SparseEntry* __restrict__ entries,
+                                                            const float* __restrict__ terms, int32_t np,
+                                                            const uint8_t* __restrict__ slotmask,
+                                                            const float* __restrict__ occ_terms,
+                                                            const OccBuildGroup* __restrict__ groups, int32_t catalogue,
+                                                            int32_t words) {
+    const OccBuildGroup& grp = groups[blockIdx.y];
+    const uint8_t* sm = slotmask + (size_t)blockIdx.y * np;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool nz = false;
+    if (i < catalogue) {
+        float x[LP];
+#pragma unroll
+        for (int s = 0; s < LP; ++s) x[s] = 0.0f;
+        const uint32_t k1 = ptr[i + 1];
+        for (uint32_t k = ptr[i]; k < k1; ++k) {
+            const SparseEntry en = entries[k];
+            const uint32_t mask = sm[en.elt];
+            if (!mask) continue;
+            const float f = fin_f32(en.loss, terms[en.elt], terms[np + en.elt], terms[2 * np + en.elt]);
+#pragma unroll
+            for (int s = 0; s < LP; ++s)
+                if ((mask >> s) & 1u) x[s] += f;
+        }
+        float o[LP];
+#pragma unroll
+        for (int s = 0; s < LP; ++s) {
+            o[s] = 0.0f;
+            if (s < grp.n_layers) {
+                const int32_t j = grp.layer[s];
+                o[s] = xl_f32(x[s], occ_terms[2 * j], occ_terms[2 * j + 1]);
+                nz |= o[s] > 0.0f;
+            }
+        }
+        float* dst = grp.occ + i * LP;
+        if constexpr (LP == 1) dst[0] = o[0];
+        else if constexpr (LP == 2) *reinterpret_cast<float2*>(dst) = make_float2(o[0], o[1]);
+        else {
+#pragma unroll
+            for (int q = 0; q < LP / 4; ++q)
+                reinterpret_cast<float4*>(dst)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
+}
+
 template <int LT, int LP>
 cudaError_t launch_group(const OccGroupArgs& g, const YetArgs& y, int num_sms, int32_t catalogue, bool early,
                          double* ylt, uint8_t* branch, int* flags, cudaStream_t s) {
@@ -538,6 +593,19 @@ cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np
 cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s) {
     const int32_t words = (int32_t)(((int64_t)p->catalogue + 31) / 32);
     const dim3 grid((unsigned)(((int64_t)words * 32 + 255) / 256), (unsigned)p->ogroups.size());
+    // from the CSR of the non-zero losses where it can stand in for the
+    // per-layer tables (see build_occ_csr_kernel)
+    if (p->d_slotmask && p->sp_ptr && p->d_elt_terms && p->d_occ) {
+        const SparseEntry* en = reinterpret_cast<const SparseEntry*>(p->sp_entries);
+        switch (p->og_lp) {
+            case 1: build_occ_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
+            case 2: build_occ_csr_kernel<2><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
+            case 4: build_occ_csr_kernel<4><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
+            case 8: build_occ_csr_kernel<8><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (p->og_lp) {
         case 1: build_occ_kernel<1><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
         case 2: build_occ_kernel<2><<<grid, 256, 0, s>>>(p->d_lbuild, p->d_ogroups, p->catalogue, words); break;

@@ -252,6 +252,47 @@ def test_host_buffers_match_device_path():
                 p.close()
 
 
+def test_occurrence_tables_from_csr_match_dense_build():
+    """With the CSR of the non-zero losses and every layer's ELTs in
+    ascending id order, the skip variant builds its occurrence tables from
+    the CSR; the YLT is that of the build from the per-layer tables, bit for
+    bit. A portfolio with a layer listed out of order keeps the per-layer
+    build and matches the oracle."""
+    cases = (workloads.make("c0u"), workloads.random_case(209, n_trials=4000, max_len=90, n_layers=11, n_elt=20,
+                                                          max_elts_per_layer=12),
+             workloads.random_case(210, n_trials=3000, dense_k=200, n_layers=3, n_elt=9))
+    for w in cases:
+        ys = []
+        for layouts in (art.ART_LAYOUT_LAYER, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE):
+            p = art.portfolio_from_workload(w, layouts=layouts)
+            try:
+                y, _ = run_ylt(p, w, art.ART_VARIANT_SKIP)
+                ys.append(y)
+            finally:
+                p.close()
+        assert torch.equal(ys[0], ys[1]), w.name
+        ref, gross, _ = oracle.ylt(w.oracle_problem())
+        assert_ylt_close(ys[1].cpu().numpy(), ref, gross, f"{w.name} CSR build")
+    # a layer whose ELTs are listed in descending order
+    w = cases[1]
+    port = w.portfolio
+    ids = port.layer_elt_ids.copy()
+    for j in range(port.n_layers):
+        a, b = port.layer_elt_off[j], port.layer_elt_off[j + 1]
+        ids[a:b] = ids[a:b][::-1]
+    tab = torch.from_numpy(port.elt_losses).cuda()
+    terms = np.stack([port.occ_ret, port.occ_lim, port.agg_ret, port.agg_lim], axis=1)
+    p = art.art_create_portfolio(port.catalogue_size, tab, port.elt_mult, port.elt_ded, port.elt_lim,
+                                 port.layer_elt_off, ids, terms, layouts=art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE)
+    try:
+        y, _ = run_ylt(p, w, art.ART_VARIANT_SKIP)
+        prob = dict(w.oracle_problem(), layer_elt_ids=ids)
+        ref, gross, _ = oracle.ylt(prob)
+        assert_ylt_close(y.cpu().numpy(), ref, gross, "descending layer lists")
+    finally:
+        p.close()
+
+
 def test_host_buffers_in_place_and_staged():
     """The host-buffer calls read a mapped page-locked YET in place when the
     variant reads every id once (one occurrence group, or one layer for the
