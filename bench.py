@@ -218,7 +218,31 @@ def _sec(nbytes) -> int:
     return 32 * -(-int(nbytes) // 32)
 
 
-def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6):
+def csr_build_used(port, layouts: int) -> bool:
+    """Whether the library builds the occurrence tables from the CSR of the
+    non-zero losses: with ART_LAYOUT_SPARSE and every layer's ELTs in
+    ascending id order (else from the per-layer tables)."""
+    from paper_1308_2572_gb300 import art
+    if not layouts & art.ART_LAYOUT_SPARSE:
+        return False
+    for j in range(port.n_layers):
+        e = port.layer_elt_ids[port.layer_elt_off[j]:port.layer_elt_off[j + 1]]
+        if np.any(np.diff(e) <= 0):
+            return False
+    return True
+
+
+def builds_from_csr(port, layouts: int, variant: str) -> bool:
+    """Whether this variant's occurrence tables come from the CSR: the
+    all-FP64 build whenever the CSR exists, the skip build as
+    csr_build_used says."""
+    from paper_1308_2572_gb300 import art
+    if variant == "fp64":
+        return bool(layouts & art.ART_LAYOUT_SPARSE)
+    return variant == "skip" and csr_build_used(port, layouts)
+
+
+def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6, csr_build: bool = False):
     """What one forward launch set moves and reads, for the roofline.
 
     s8d: the per-unit figure -- 4 B per event id (plus 8 B per CSR offset)
@@ -239,6 +263,9 @@ def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6):
     lookups_performed: table entries the kernels read per launch set (the
       skip and all-FP64 variants: one per (catalogue event, layer ELT) in the
       build plus one X row per gathered event; the others: per occurrence).
+    csr_build: the skip and all-FP64 builds read the CSR of the non-zero
+      losses (per group: the C + 1 offsets and every 8-byte entry) instead of
+      the per-layer tables; the lookups of the build are then its entries.
     """
     port, yet = w.portfolio, w.yet
     n_events = yet.n_events
@@ -260,18 +287,23 @@ def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6):
         dens = [occurrence_density(port, lays) for lays in groups]
         gathered = sum(n_events * d for d in dens)
         reads = sum(n_events * d * _sec(xb * lp) for d in dens)
-        build = float(sum(4 * _pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (
-            (C + 1) * xb * lp + C / 8)
+        nnz = float((port.elt_losses != 0).sum())
+        if csr_build:
+            build = len(groups) * (4.0 * (C + 1) + 8.0 * nnz + (C + 1) * xb * lp + C / 8)
+            build_lookups = len(groups) * nnz
+        else:
+            build = float(sum(4 * _pad(int(n)) for n in port.elts_per_layer())) * C + len(groups) * (
+                (C + 1) * xb * lp + C / 8)
+            build_lookups = C * elts_total
         n_groups = len(groups)
         table = float((C + 1) * xb * lp)
         # FP64 operations of the all-FP64 variant: its CSR build costs an FMA
         # per non-zero loss and an add per (loss, layer holding it); the trial
         # pass adds the FP64 occurrence losses as integers (no FP64 operation)
-        nnz = float((port.elt_losses != 0).sum())
         flops = 2.0 * nnz + nnz * elts_total / port.n_elt
         out = {"s8d": n_groups * ids + ylt + build + reads, "compulsory": n_groups * ids + ylt + build,
                "l2": n_groups * ids + build + reads, "table_bytes": table, "l2_resident": table <= l2_bytes,
-               "lookups_performed": C * elts_total + gathered}
+               "lookups_performed": build_lookups + gathered}
         if variant == "fp64":
             out["fp64_flops"] = flops
         return out
@@ -542,7 +574,7 @@ def extra_workload(name: str, dev, probes: dict, hbm: float, l2_size: float) -> 
         rec.update(variant=chosen, autotune=tune, forward_ms=ms, ms_per_1M_trial_ylt=ms * 1e6 / T,
                    trial_events_elts_per_s=w.lookups() / (ms * 1e-3),
                    vs_plain_one_layer_per_launch=fwd["plain"] / ms)
-        ab = algorithmic_bytes(w, chosen, l2_size)
+        ab = algorithmic_bytes(w, chosen, l2_size, builds_from_csr(port, layouts, chosen))
         roof = roofline(ab, ms * 1e-3, hbm, probes.get("l2_gather32_gbs"),
                         probes.get("fp64_add_gflops") if chosen == "fp64" else None)
         roof.update(kernel=VARIANT_KERNEL[chosen], traffic=recorded_traffic(VARIANT_KERNEL[chosen], name))
@@ -594,7 +626,8 @@ def extra_workload(name: str, dev, probes: dict, hbm: float, l2_size: float) -> 
             art.art_set_variant(p, art.ART_VARIANT_FP64)
             y64 = torch.empty_like(ylt)
             rec["fp64_forward_ms"] = time_forward(art, torch, p, T, ids, off, K, y64, stream, reps=2)
-            r64 = roofline(algorithmic_bytes(w, "fp64", l2_size), rec["fp64_forward_ms"] * 1e-3, hbm,
+            r64 = roofline(algorithmic_bytes(w, "fp64", l2_size, builds_from_csr(port, layouts, "fp64")),
+                           rec["fp64_forward_ms"] * 1e-3, hbm,
                            probes.get("l2_gather32_gbs"), probes.get("fp64_add_gflops"))
             rec["fp64_roofline"] = {k: r64.get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "t_star_ms",
                                                            "hbm_frac_by_dram_bytes", "peak_source")}
@@ -808,7 +841,7 @@ def main():
                   "fp64_add_gflops": art.art_probe(art.ART_PROBE_FP64ADD, 0, 3)}
     # roofline of the dominant kernel (the forward)
     peak, peak_kind = measured_peaks()
-    ab = algorithmic_bytes(w, variant, l2_size)
+    ab = algorithmic_bytes(w, variant, l2_size, builds_from_csr(port, layouts, variant))
     roof = roofline(ab, fwd_mean / 1e3, peak, probes.get("l2_gather32_gbs"),
                     probes.get("fp64_add_gflops") if variant == "fp64" else None)
     kernel_name = VARIANT_KERNEL[variant]

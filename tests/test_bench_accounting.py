@@ -2,6 +2,7 @@
 the library's rules, and each variant is accounted against the right
 bound."""
 import json
+import types
 import os
 import sys
 
@@ -135,3 +136,31 @@ def test_first_layers_keeps_a_consistent_prefix_of_the_portfolio():
     assert np.array_equal(sub.layer_elt_ids, port.layer_elt_ids[:port.layer_elt_off[4]])
     assert np.array_equal(sub.agg_lim, port.agg_lim[:4]) and sub.elt_losses is port.elt_losses
     assert bench.first_layers(w, 5).portfolio.n_layers == 1  # at most the layers there are
+
+
+def test_csr_build_accounting():
+    """With ART_LAYOUT_SPARSE and every layer's ELTs ascending the skip
+    variant's build reads the CSR (per group: the offsets and every 8-byte
+    entry) instead of the per-layer tables; a layer listed out of order
+    keeps the per-layer build; the all-FP64 build uses the CSR whenever it
+    exists."""
+    from paper_1308_2572_gb300 import art
+    w = workloads.make("c0", n_trials=200)
+    port = w.portfolio
+    sparse = art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE
+    assert bench.csr_build_used(port, sparse)
+    assert not bench.csr_build_used(port, art.ART_LAYOUT_LAYER)
+    assert bench.builds_from_csr(port, sparse, "fp64") and not bench.builds_from_csr(port, sparse, "plain")
+    dense = bench.algorithmic_bytes(w, "skip")
+    csr = bench.algorithmic_bytes(w, "skip", csr_build=True)
+    C = port.catalogue_size
+    nnz = float((port.elt_losses != 0).sum())
+    x_and_bits = (C + 1) * 4 + C / 8  # one layer: LP = 1, 4-byte entries
+    assert csr["compulsory"] - (dense["compulsory"] - (4 * 4 * C + x_and_bits)) == pytest.approx(
+        4.0 * (C + 1) + 8.0 * nnz + x_and_bits)
+    assert csr["lookups_performed"] - dense["lookups_performed"] == pytest.approx(nnz - C * 3)
+    rev = types.SimpleNamespace(**{k: getattr(port, k) for k in ("n_layers", "layer_elt_off")})
+    ids = port.layer_elt_ids.copy()
+    ids[port.layer_elt_off[0]:port.layer_elt_off[1]] = ids[port.layer_elt_off[0]:port.layer_elt_off[1]][::-1]
+    rev.layer_elt_ids = ids
+    assert not bench.csr_build_used(rev, sparse)
