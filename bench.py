@@ -219,27 +219,19 @@ def _sec(nbytes) -> int:
 
 
 def csr_build_used(port, layouts: int) -> bool:
-    """Whether the library builds the occurrence tables from the CSR of the
-    non-zero losses: with ART_LAYOUT_SPARSE and every layer's ELTs in
-    ascending id order (else from the per-layer tables)."""
+    """Whether the library builds the skip variant's occurrence tables from
+    the CSR of the non-zero losses: whenever the portfolio holds it
+    (ART_LAYOUT_SPARSE). A layer listed out of ascending ELT order has the
+    events with three or more of its entries re-summed from its per-layer
+    row; the accounting leaves those rare rows out."""
     from paper_1308_2572_gb300 import art
-    if not layouts & art.ART_LAYOUT_SPARSE:
-        return False
-    for j in range(port.n_layers):
-        e = port.layer_elt_ids[port.layer_elt_off[j]:port.layer_elt_off[j + 1]]
-        if np.any(np.diff(e) <= 0):
-            return False
-    return True
+    return bool(layouts & art.ART_LAYOUT_SPARSE)
 
 
 def builds_from_csr(port, layouts: int, variant: str) -> bool:
-    """Whether this variant's occurrence tables come from the CSR: the
-    all-FP64 build whenever the CSR exists, the skip build as
-    csr_build_used says."""
-    from paper_1308_2572_gb300 import art
-    if variant == "fp64":
-        return bool(layouts & art.ART_LAYOUT_SPARSE)
-    return variant == "skip" and csr_build_used(port, layouts)
+    """Whether this variant's occurrence tables come from the CSR (the skip
+    and all-FP64 builds, whenever the portfolio holds it)."""
+    return variant in ("skip", "fp64") and csr_build_used(port, layouts)
 
 
 def algorithmic_bytes(w, variant: str, l2_bytes: float = 126e6, csr_build: bool = False):

@@ -365,14 +365,19 @@ cudaError_t build_occ_groups(art_portfolio* p) {
         }
     }
     if (e) return e;
-    // the tables X can be built from the CSR of the non-zero losses when
-    // every layer lists its ELTs in ascending id order: the CSR's entry order
-    // is then each layer's order, and the absent (zero) losses add exactly 0,
-    // so the sums are those of the per-layer tables bit for bit
-    bool ascending = true;
-    for (int32_t j = 0; j < L && ascending; ++j)
-        for (int32_t c = p->loff[j] + 1; c < p->loff[j + 1]; ++c) ascending = ascending && p->lids[c - 1] < p->lids[c];
-    if (ascending && p->pool_np > 0 && p->sp_ptr) {
+    // the tables X are built from the CSR of the non-zero losses where it
+    // exists: each event's entries come in ELT id order, so a layer that
+    // lists its ELTs in ascending order sums them in its own order (the
+    // absent zeros add exactly 0); for a layer listed out of order the build
+    // re-sums the events with three or more of its entries from its
+    // per-layer row (one or two terms give the same bits in any order)
+    for (int32_t gi = 0; gi < ng; ++gi)
+        for (int s = 0; s < p->ogroups[gi].n_layers; ++s) {
+            const int32_t j = p->ogroups[gi].layer[s];
+            for (int32_t c = p->loff[j] + 1; c < p->loff[j + 1]; ++c)
+                if (!(p->lids[c - 1] < p->lids[c])) bg[gi].unsorted |= 1 << s;
+        }
+    if (p->pool_np > 0 && p->sp_ptr) {
         std::vector<uint8_t> sm((size_t)ng * p->pool_np, 0);
         for (int32_t gi = 0; gi < ng; ++gi)
             for (int s = 0; s < p->ogroups[gi].n_layers; ++s) {

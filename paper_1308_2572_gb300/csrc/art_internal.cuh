@@ -301,6 +301,7 @@ struct OccBuildGroup {
     unsigned long long* maxkey;  // FP64 groups: the table's largest entry (atomic maximum of keys)
     int32_t layer[kMaxOccLayers];
     int32_t n_layers;
+    int32_t unsorted;            // skip groups: bit s set when layer s lists its ELTs out of ascending id order
 };
 
 }  // namespace art
@@ -355,7 +356,6 @@ struct art_portfolio {
     unsigned long long* d_occ64_max = nullptr;  // [n_ogroups64]: each FP64 table's largest entry
     int32_t og_lp64 = 0;                        // slots per row of the FP64 tables (1, 2 or 4)
     uint8_t* d_slotmask = nullptr;              // [n_ogroups][pool_np]: slots of the skip group holding the ELT
-                                                // (only when every layer lists its ELTs in ascending id order)
     uint8_t* d_slotmask64 = nullptr;            // [n_ogroups64][pool_np]: slots of the group holding the ELT
     int64_t occ64_bytes = 0;
     int64_t group_bytes = 0;

@@ -490,18 +490,22 @@ __global__ void __launch_bounds__(256) build_occ_kernel(const LayerBuildArgs* __
     if ((threadIdx.x & 31) == 0 && (i >> 5) < words) grp.occ_bits[i >> 5] = m;
 }
 
-// The same tables from the event-major CSR of the non-zero losses (every
-// layer's ELTs in ascending id order): thread i walks event i's entries (in
-// ELT id order, which is each layer's order) and adds F_e in FP32 to the
-// slots of the group's layers that hold ELT e. The absent losses, zeros,
-// would add exactly 0, so the sums are the per-layer tables' bit for bit,
-// while the reads are the event's non-zero entries instead of its full rows.
+// The same tables from the event-major CSR of the non-zero losses: thread i
+// walks event i's entries (in ELT id order) and adds F_e in FP32 to the
+// slots of the group's layers that hold ELT e. For a layer that lists its
+// ELTs in ascending id order that is the layer's own order, and the absent
+// losses, zeros, would add exactly 0, so the sum is the per-layer build's
+// bit for bit. For a layer listed out of order the same holds while the
+// event has at most two of its entries (one or two terms give the same bits
+// in either order); with three or more the thread re-sums that layer from
+// its per-layer row, in the layer's order, as the per-layer build does.
 template <int LP>
 __global__ void __launch_bounds__(256) build_occ_csr_kernel(const uint32_t* __restrict__ ptr,
                                                             const SparseEntry* __restrict__ entries,
                                                             const float* __restrict__ terms, int32_t np,
                                                             const uint8_t* __restrict__ slotmask,
                                                             const float* __restrict__ occ_terms,
+                                                            const LayerBuildArgs* __restrict__ lbuild,
                                                             const OccBuildGroup* __restrict__ groups, int32_t catalogue,
                                                             int32_t words) {
     const OccBuildGroup& grp = groups[blockIdx.y];
@@ -509,9 +513,14 @@ __global__ void __launch_bounds__(256) build_occ_csr_kernel(const uint32_t* __re
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool nz = false;
     if (i < catalogue) {
+        const int unsorted = grp.unsorted;
         float x[LP];
+        int cnt[LP];
 #pragma unroll
-        for (int s = 0; s < LP; ++s) x[s] = 0.0f;
+        for (int s = 0; s < LP; ++s) {
+            x[s] = 0.0f;
+            cnt[s] = 0;
+        }
         const uint32_t k1 = ptr[i + 1];
         for (uint32_t k = ptr[i]; k < k1; ++k) {
             const SparseEntry en = entries[k];
@@ -520,7 +529,10 @@ __global__ void __launch_bounds__(256) build_occ_csr_kernel(const uint32_t* __re
             const float f = fin_f32(en.loss, terms[en.elt], terms[np + en.elt], terms[2 * np + en.elt]);
 #pragma unroll
             for (int s = 0; s < LP; ++s)
-                if ((mask >> s) & 1u) x[s] += f;
+                if ((mask >> s) & 1u) {
+                    x[s] += f;
+                    ++cnt[s];
+                }
         }
         float o[LP];
 #pragma unroll
@@ -528,6 +540,13 @@ __global__ void __launch_bounds__(256) build_occ_csr_kernel(const uint32_t* __re
             o[s] = 0.0f;
             if (s < grp.n_layers) {
                 const int32_t j = grp.layer[s];
+                if (((unsorted >> s) & 1) && cnt[s] >= 3) {
+                    const LayerBuildArgs& a = lbuild[j];
+                    const float* row = a.table + i * a.np;
+                    float xs = 0.0f;
+                    for (int c = 0; c < a.np; ++c) xs += fin_f32(row[c], a.m[c], a.d[c], a.lim[c]);
+                    x[s] = xs;
+                }
                 o[s] = xl_f32(x[s], occ_terms[2 * j], occ_terms[2 * j + 1]);
                 nz |= o[s] > 0.0f;
             }
@@ -593,15 +612,15 @@ cudaError_t build_group_bitmap(const float* table, int32_t catalogue, int32_t np
 cudaError_t build_occurrence(art_portfolio* p, cudaStream_t s) {
     const int32_t words = (int32_t)(((int64_t)p->catalogue + 31) / 32);
     const dim3 grid((unsigned)(((int64_t)words * 32 + 255) / 256), (unsigned)p->ogroups.size());
-    // from the CSR of the non-zero losses where it can stand in for the
-    // per-layer tables (see build_occ_csr_kernel)
-    if (p->d_slotmask && p->sp_ptr && p->d_elt_terms && p->d_occ) {
+    // from the CSR of the non-zero losses where the portfolio holds it (see
+    // build_occ_csr_kernel)
+    if (p->d_slotmask && p->sp_ptr && p->d_elt_terms && p->d_occ && p->d_lbuild) {
         const SparseEntry* en = reinterpret_cast<const SparseEntry*>(p->sp_entries);
         switch (p->og_lp) {
-            case 1: build_occ_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
-            case 2: build_occ_csr_kernel<2><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
-            case 4: build_occ_csr_kernel<4><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
-            case 8: build_occ_csr_kernel<8><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_ogroups, p->catalogue, words); break;
+            case 1: build_occ_csr_kernel<1><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+            case 2: build_occ_csr_kernel<2><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+            case 4: build_occ_csr_kernel<4><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
+            case 8: build_occ_csr_kernel<8><<<grid, 256, 0, s>>>(p->sp_ptr, en, p->d_elt_terms, p->pool_np, p->d_slotmask, p->d_occ, p->d_lbuild, p->d_ogroups, p->catalogue, words); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

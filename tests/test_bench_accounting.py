@@ -139,11 +139,9 @@ def test_first_layers_keeps_a_consistent_prefix_of_the_portfolio():
 
 
 def test_csr_build_accounting():
-    """With ART_LAYOUT_SPARSE and every layer's ELTs ascending the skip
-    variant's build reads the CSR (per group: the offsets and every 8-byte
-    entry) instead of the per-layer tables; a layer listed out of order
-    keeps the per-layer build; the all-FP64 build uses the CSR whenever it
-    exists."""
+    """With ART_LAYOUT_SPARSE the skip and all-FP64 builds read the CSR (per
+    group: the offsets and every 8-byte entry) instead of the per-layer
+    tables, whatever the order the layers list their ELTs in."""
     from paper_1308_2572_gb300 import art
     w = workloads.make("c0", n_trials=200)
     port = w.portfolio
@@ -163,4 +161,4 @@ def test_csr_build_accounting():
     ids = port.layer_elt_ids.copy()
     ids[port.layer_elt_off[0]:port.layer_elt_off[1]] = ids[port.layer_elt_off[0]:port.layer_elt_off[1]][::-1]
     rev.layer_elt_ids = ids
-    assert not bench.csr_build_used(rev, sparse)
+    assert bench.csr_build_used(rev, sparse)

@@ -252,45 +252,51 @@ def test_host_buffers_match_device_path():
                 p.close()
 
 
-def test_occurrence_tables_from_csr_match_dense_build():
-    """With the CSR of the non-zero losses and every layer's ELTs in
-    ascending id order, the skip variant builds its occurrence tables from
-    the CSR; the YLT is that of the build from the per-layer tables, bit for
-    bit. A portfolio with a layer listed out of order keeps the per-layer
-    build and matches the oracle."""
-    cases = (workloads.make("c0u"), workloads.random_case(209, n_trials=4000, max_len=90, n_layers=11, n_elt=20,
-                                                          max_elts_per_layer=12),
-             workloads.random_case(210, n_trials=3000, dense_k=200, n_layers=3, n_elt=9))
-    for w in cases:
-        ys = []
-        for layouts in (art.ART_LAYOUT_LAYER, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE):
-            p = art.portfolio_from_workload(w, layouts=layouts)
-            try:
-                y, _ = run_ylt(p, w, art.ART_VARIANT_SKIP)
-                ys.append(y)
-            finally:
-                p.close()
-        assert torch.equal(ys[0], ys[1]), w.name
-        ref, gross, _ = oracle.ylt(w.oracle_problem())
-        assert_ylt_close(ys[1].cpu().numpy(), ref, gross, f"{w.name} CSR build")
-    # a layer whose ELTs are listed in descending order
-    w = cases[1]
+def _skip_ylt(w, layouts, layer_elt_ids=None):
     port = w.portfolio
-    ids = port.layer_elt_ids.copy()
-    for j in range(port.n_layers):
-        a, b = port.layer_elt_off[j], port.layer_elt_off[j + 1]
-        ids[a:b] = ids[a:b][::-1]
+    ids = port.layer_elt_ids if layer_elt_ids is None else layer_elt_ids
     tab = torch.from_numpy(port.elt_losses).cuda()
     terms = np.stack([port.occ_ret, port.occ_lim, port.agg_ret, port.agg_lim], axis=1)
     p = art.art_create_portfolio(port.catalogue_size, tab, port.elt_mult, port.elt_ded, port.elt_lim,
-                                 port.layer_elt_off, ids, terms, layouts=art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE)
+                                 port.layer_elt_off, ids, terms, layouts=layouts)
     try:
         y, _ = run_ylt(p, w, art.ART_VARIANT_SKIP)
-        prob = dict(w.oracle_problem(), layer_elt_ids=ids)
-        ref, gross, _ = oracle.ylt(prob)
-        assert_ylt_close(y.cpu().numpy(), ref, gross, "descending layer lists")
+        return y
     finally:
         p.close()
+
+
+def test_occurrence_tables_from_csr_match_dense_build():
+    """With the CSR of the non-zero losses the skip variant builds its
+    occurrence tables from it; the YLT is that of the build from the
+    per-layer tables, bit for bit, for layers listed in ascending ELT order,
+    in descending order (events with three or more of a layer's entries
+    re-summed from its per-layer row) and in c3's rotated order."""
+    dense, csr = art.ART_LAYOUT_LAYER, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE
+    cases = [(workloads.make("c0u"), None),
+             (workloads.random_case(209, n_trials=4000, max_len=90, n_layers=11, n_elt=20, max_elts_per_layer=12,
+                                    nnz_frac=0.6), None),
+             (workloads.random_case(210, n_trials=3000, dense_k=200, n_layers=3, n_elt=9, nnz_frac=0.8), None),
+             (workloads.make("c3", n_trials=3000), None)]
+    w = cases[1][0]
+    rev = w.portfolio.layer_elt_ids.copy()
+    for j in range(w.portfolio.n_layers):
+        a, b = w.portfolio.layer_elt_off[j], w.portfolio.layer_elt_off[j + 1]
+        rev[a:b] = rev[a:b][::-1]
+    cases.append((w, rev))
+    w2 = cases[2][0]
+    rev2 = w2.portfolio.layer_elt_ids.copy()
+    for j in range(w2.portfolio.n_layers):
+        a, b = w2.portfolio.layer_elt_off[j], w2.portfolio.layer_elt_off[j + 1]
+        rev2[a:b] = np.roll(rev2[a:b], 1)
+    cases.append((w2, rev2))
+    for w, ids in cases:
+        y_dense = _skip_ylt(w, dense, ids)
+        y_csr = _skip_ylt(w, csr, ids)
+        assert torch.equal(y_dense, y_csr), w.name
+        prob = w.oracle_problem() if ids is None else dict(w.oracle_problem(), layer_elt_ids=ids)
+        ref, gross, _ = oracle.ylt(prob)
+        assert_ylt_close(y_csr.cpu().numpy(), ref, gross, f"{w.name} CSR build")
 
 
 def test_host_buffers_in_place_and_staged():
