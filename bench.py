@@ -727,8 +727,10 @@ def main():
     log(f"[bench] rank {rank}: generated {args.config} in {time.perf_counter() - t_gen:.1f} s")
     port, yet = w.portfolio, w.yet
     L, T, K = port.n_layers, yet.n_trials, yet.events_per_trial
-    # a named variant builds only its own layout (keeps profiling runs small)
-    layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_LAYER, "batched": art.ART_LAYOUT_POOL,
+    # a named variant builds only the layouts it reads (keeps profiling runs
+    # small); the skip variant's tables are built from the CSR
+    layouts = {"plain": art.ART_LAYOUT_LAYER, "skip": art.ART_LAYOUT_LAYER | art.ART_LAYOUT_SPARSE,
+               "batched": art.ART_LAYOUT_POOL,
                "fp64": art.ART_LAYOUT_LAYER | art.ART_LAYOUT_OCC64 | art.ART_LAYOUT_SPARSE,
                "sparse": art.ART_LAYOUT_SPARSE}.get(
         args.variant, art.ART_LAYOUT_LAYER | art.ART_LAYOUT_POOL | art.ART_LAYOUT_GROUP | art.ART_LAYOUT_SPARSE)
