@@ -687,7 +687,7 @@ def main():
                     help="ART_FLAG_GRAPH: the forward's launches replay from a captured CUDA graph")
     ap.add_argument("--no-l2-persist", action="store_true",
                     help="no persisting L2 access-policy window over the gathered table (ART_FLAG_L2_PERSIST is "
-                         "set by default: 5% off the one-layer forward)")
+                         "set by default: 5%% off the one-layer forward)")
     ap.add_argument("--trials", type=int, default=0,
                     help="keep only the first N trials (small cases for profiling; 0 = the full workload)")
     ap.add_argument("--layers", type=int, default=0,

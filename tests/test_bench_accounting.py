@@ -162,3 +162,13 @@ def test_csr_build_accounting():
     ids[port.layer_elt_off[0]:port.layer_elt_off[1]] = ids[port.layer_elt_off[0]:port.layer_elt_off[1]][::-1]
     rev.layer_elt_ids = ids
     assert bench.csr_build_used(rev, sparse)
+
+
+def test_bench_help_renders():
+    """Every help string of bench.py formats (argparse expands % in them)."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                     "bench.py"), "--help"], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr[-500:]
+    assert "--no-l2-persist" in r.stdout
