@@ -85,9 +85,11 @@ enum {
                                  terms in FP64 (ART_LAYOUT_OCC64); else batched over the
                                  FP64 pool with FP64 sums (ART_LAYOUT_POOL64)             */
     ART_VARIANT_SKIP = 4,     /* per call, the occurrence loss of every catalogue event
-                                 for every layer (one build launch from the per-layer
-                                 tables), then one trial pass per run of <= 8 layers that
-                                 skips events with zero occurrence loss (bitmap)         */
+                                 for every layer (one build launch, from the CSR of the
+                                 non-zero losses when ART_LAYOUT_SPARSE is present, else
+                                 from the per-layer tables; the same values bit for bit),
+                                 then one trial pass per run of <= 8 layers that skips
+                                 events with zero occurrence loss (bitmap)               */
     ART_VARIANT_SPARSE = 5    /* one persistent launch over all layers, reading an
                                  event-major CSR of the non-zero losses (compressed ELTs) */
 };
@@ -104,7 +106,9 @@ enum {
                                  [C][n_pad] FP32 over the group's ELTs plus a C-bit
                                  occupancy bitmap; read by art_run_ylt_backward           */
     ART_LAYOUT_SPARSE = 16,   /* all ELTs: event-major CSR of the non-zero losses
-                                 (C + 1 offsets, 8 bytes per non-zero loss)                */
+                                 (C + 1 offsets, 8 bytes per non-zero loss); also the
+                                 source of the skip and all-FP64 variants' per-call
+                                 occurrence tables                                         */
     ART_LAYOUT_OCC64 = 32     /* with ART_LAYOUT_LAYER: FP64 occurrence-loss tables
                                  ([C + 1][<= 4] 8-byte entries per run of <= 4 layers) and
                                  bitmaps, written by the all-FP64 variant on every call
